@@ -1,0 +1,379 @@
+"""Pins of the CPU oracle to what the paper and the mathematics fix.
+
+None of these checks re-types the oracle's own formulas: each compares it
+with an independent statement (the textbook polynomial equilibrium, the
+printed Psi of section 2.3, the printed tables, closed-form limits of
+section 4.1, numpy's roll/FFT/eig).  A dropped term, a wrong sign, a swapped
+moment row or a transposed operand in the oracle fails at least one.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import lbm_inputs as inp
+import oracle as orc
+from oracle import vn
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def feq_poly(rho, ux, uy, cx, cy):
+    """Textbook second-order D2Q9 equilibrium, written independently."""
+    cu = cx * ux + cy * uy
+    return W * rho * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy))
+
+
+@pytest.fixture(scope="module")
+def vel():
+    return orc.velocities()
+
+
+def test_velocity_set_is_d2q9(vel):
+    cx, cy = vel
+    assert cx[0] == 0 and cy[0] == 0
+    pairs = {(int(a), int(b)) for a, b in zip(cx, cy)}
+    assert pairs == {(a, b) for a in (-1, 0, 1) for b in (-1, 0, 1)}
+    # the opposite of every velocity is in the set
+    for a, b in pairs:
+        assert (-a, -b) in pairs
+
+
+def test_moment_matrix_conditions_and_orthogonality(vel):
+    """M_0j = 1, M_aj = v_j^a (section 2.1); rows orthogonal with the
+    Lallemand-Luo norms."""
+    cx, cy = vel
+    M, Mi = orc.matrices()
+    assert np.array_equal(M[0], np.ones(9))
+    assert np.array_equal(M[1], cx)
+    assert np.array_equal(M[2], cy)
+    G = M @ M.T
+    assert np.array_equal(G, np.diag([9, 6, 6, 36, 36, 12, 12, 4, 4]).astype(float))
+    assert np.max(np.abs(M @ Mi - np.eye(9))) < 1e-15
+    # same matrix as the polynomial basis built independently in oracle.vn
+    assert np.array_equal(M, vn.moment_matrix())
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_equilibrium_moments_give_polynomial_equilibrium(vel, seed):
+    """M^-1 m^eq(rho, j) of section 2.3 equals the textbook f^eq."""
+    cx, cy = vel
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.8, 1.2)
+    ux, uy = rng.uniform(-0.2, 0.2, 2)
+    _, Mi = orc.matrices()
+    f = Mi @ orc.meq(rho, rho * ux, rho * uy)
+    assert np.max(np.abs(f - feq_poly(rho, ux, uy, cx, cy))) < 2e-16 * 8
+    # and the oracle's lattice init agrees
+    fl = orc.init_eq(np.full((1, 1), rho), np.full((1, 1), ux), np.full((1, 1), uy))
+    assert np.max(np.abs(fl[:, 0, 0] - feq_poly(rho, ux, uy, cx, cy))) < 2e-15
+
+
+@pytest.mark.parametrize("U,V", [(0.0, 0.0), (0.1, 0.0), (0.07, -0.05)])
+def test_meq_jacobian_matches_printed_psi(U, V):
+    """Linearizing the oracle's m^eq about (rho=1, U, V) and relaxing with S
+    reproduces every entry of the Psi printed in section 2.3."""
+    s = inp.s_paper(dict(s_e=1.3, s_eps=1.7, s_q=0.6, s_nu=1.9))
+    h = 1e-6
+    J = np.zeros((9, 3))
+    w0 = np.array([1.0, U, V])
+    for c in range(3):
+        d = np.zeros(3)
+        d[c] = h
+        J[:, c] = (orc.meq(*(w0 + d)) - orc.meq(*(w0 - d))) / (2 * h)
+    S = np.diag(s)
+    Psi = np.eye(9) - S
+    Psi[3:, :3] += S[3:, 3:] @ J[3:, :]
+    assert np.max(np.abs(Psi - vn.psi(U, V, s))) < 1e-9
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_collision_conserves_mass_and_momentum(vel, seed):
+    cx, cy = vel
+    rng = np.random.default_rng(seed)
+    s = inp.s_paper(dict(s_e=rng.uniform(0.2, 2), s_eps=rng.uniform(0.2, 2),
+                         s_q=rng.uniform(0.2, 2), s_nu=rng.uniform(0.2, 2)))
+    f = W * (1 + 0.05 * rng.standard_normal(9))
+    g = orc.collide(s, f)
+    for row in (np.ones(9), cx, cy):
+        assert abs(row @ g - row @ f) < 4e-16
+    # the collision really moves the non-conserved moments
+    assert np.max(np.abs(g - f)) > 1e-4
+
+
+def test_equilibrium_is_fixed_point(vel):
+    cx, cy = vel
+    s = inp.s_paper(inp.rates("OPT"))
+    f = feq_poly(1.02, 0.08, -0.03, cx, cy)
+    assert np.max(np.abs(orc.collide(s, f) - f)) < 1e-16 * 4
+    rho = np.full((6, 7), 1.02)
+    f = orc.init_eq(rho, np.full((6, 7), 0.08), np.full((6, 7), -0.03))
+    g = orc.run(f, s, 10)
+    assert np.max(np.abs(g - f)) < 1e-15
+
+
+def test_bgk_special_case(vel):
+    """All rates equal s: Lambda = s I (section 2.1, Eq. eq_BGK_LBM_R)."""
+    cx, cy = vel
+    rng = np.random.default_rng(3)
+    sv = 1.0 / 0.53
+    f = W * (1 + 0.05 * rng.standard_normal(9))
+    rho = f.sum()
+    ux, uy = (cx @ f) / rho, (cy @ f) / rho
+    bgk = f - sv * (f - feq_poly(rho, ux, uy, cx, cy))
+    g = orc.collide(np.full(9, sv), f)
+    assert np.max(np.abs(g - bgk)) < 1e-15
+
+
+@pytest.mark.parametrize("nx,ny", [(2, 2), (3, 5), (7, 2), (5, 3)])
+def test_streaming_by_brute_force(vel, nx, ny):
+    """With S = 0 the step is pure streaming f_i(x + c_i) <- f_i(x) on the
+    periodic lattice, compared with numpy.roll."""
+    cx, cy = vel
+    rng = np.random.default_rng(nx * 10 + ny)
+    f = rng.standard_normal((9, ny, nx))
+    g = f.copy()
+    for t in range(1, 4):
+        g = np.stack([np.roll(g[i], (cy[i], cx[i]), axis=(0, 1)) for i in range(9)])
+        assert np.array_equal(orc.run(f, np.zeros(9), t), g)
+
+
+def test_translation_invariance():
+    s = inp.s_paper(inp.rates("LL", nu=1e-3))
+    f = inp.random_populations(9, 6, 11, amp=1e-2)
+    a = orc.run(np.roll(f, (2, 3), axis=(1, 2)), s, 7)
+    b = np.roll(orc.run(f, s, 7), (2, 3), axis=(1, 2))
+    assert np.array_equal(a, b)
+
+
+def test_scaling_commutes_with_step():
+    """m^eq is homogeneous of degree 1 in (rho, j), so stepping 2f gives
+    exactly 2 step(f) (powers of two scale without rounding)."""
+    s = inp.s_paper(inp.rates("OPT"))
+    f = inp.random_populations(8, 5, 12, amp=1e-2)
+    assert np.array_equal(orc.run(2.0 * f, s, 5), 2.0 * orc.run(f, s, 5))
+
+
+def test_vn_reference_state_is_oracle_equilibrium():
+    for U, V in [(0.0, 0.0), (0.1, 0.0), (0.05, 0.02)]:
+        a = vn.equilibrium(1.0, U, V)
+        b = orc.init_eq(np.ones((1, 1)), np.full((1, 1), U), np.full((1, 1), V))[:, 0, 0]
+        assert np.max(np.abs(a - b)) < 1e-15
+
+
+# ------------------------------------------------------- von Neumann pins
+def sig(r, key):
+    return 1.0 / r[key] - 0.5
+
+
+@pytest.mark.parametrize("name", ["LL", "OPT", "LL*"])
+def test_vn_small_k_limits(name):
+    """As k -> 0 the eigenvalues of G(k) reproduce the L-NSE modes of
+    section 4.1 with nu = sigma_nu/3 and bulk eta = sigma_e/3 (the delta-t
+    matrix of section 2.3): acoustic phase speed c_s, acoustic damping
+    k^2 (sigma_e + sigma_nu)/6, shear damping k^2 sigma_nu/3."""
+    r = inp.rates(name, nu=1e-3)
+    s = inp.s_paper(r)
+    se, sn = sig(r, "s_e"), sig(r, "s_nu")
+    for k in (0.02, 0.04):
+        for theta in (0.0, math.pi / 6, math.pi / 4):
+            lam = vn.eigs(k * math.cos(theta), k * math.sin(theta), 0.0, 0.0, s)
+            damp, c = vn.mode_rates(lam, k)
+            ac = np.argsort(-np.abs(lam))[:3]  # the three hydrodynamic modes
+            speeds = np.sort(c[ac])
+            assert abs(speeds[2] - vn.CS) < 5 * k * k
+            assert abs(speeds[0] + vn.CS) < 5 * k * k
+            assert abs(speeds[1]) < 1e-6
+            i_sh = ac[np.argmin(np.abs(c[ac]))]
+            i_ac = ac[np.argmax(c[ac])]
+            gam_ac = k * k * (se + sn) / 6
+            gam_sh = k * k * sn / 3
+            assert abs(damp[i_ac] - gam_ac) < 0.05 * gam_ac + 2 * k ** 4
+            assert abs(damp[i_sh] - gam_sh) < 0.05 * gam_sh + 2 * k ** 4
+
+
+@pytest.mark.parametrize("U", [0.1, -0.05])
+def test_vn_mean_flow_convection(U):
+    """With a uniform flow the acoustic speeds are c_s +- U (the delta-t^0
+    matrix of the uniform-flow case, section 2.3)."""
+    s = inp.s_paper(inp.rates("OPT"))
+    k = 0.02
+    lam = vn.acoustic_modes(k, 0.0, U, 0.0, s)
+    _, c = vn.mode_rates(lam, k)
+    assert abs(c[0] - (U + vn.CS)) < 1e-3
+    assert abs(c[1] - (U - vn.CS)) < 1e-3
+
+
+def test_vn_unstable_band_claim():
+    """Section 4.2 (Fig. 4-2 discussion): at sigma_e = sigma_nu = 0.0025 one
+    mode grows for 0.75 < k < 1.75 off the axes and none along them.  Read
+    here as a statement on the original scheme (Lallemand-Luo s_eps, s_q),
+    whose unstable band the optimized Table 1 group A rates remove."""
+    t = inp.TABLE1["A"]
+    opt = {k_: 1.0 / (t["sigma_" + k_[2:]] + 0.5) for k_ in ("s_e", "s_eps", "s_q", "s_nu")}
+    orig = dict(opt, s_eps=inp.LL["s_eps"], s_q=inp.LL["s_q"])
+    band = np.linspace(0.8, 1.7, 10)
+    for th in (math.pi / 6, math.pi / 4, 2 * math.pi / 3, 3 * math.pi / 4):
+        g_orig = [np.max(np.abs(vn.eigs(k * math.cos(th), k * math.sin(th), 0, 0,
+                                        inp.s_paper(orig)))) for k in band]
+        g_opt = [np.max(np.abs(vn.eigs(k * math.cos(th), k * math.sin(th), 0, 0,
+                                       inp.s_paper(opt)))) for k in band]
+        assert max(g_orig) > 1.005          # a growing mode inside the band
+        assert g_orig[4] > 1.001            # k = 1.2, mid-band
+        assert max(g_opt) < 1.0 + 1e-12
+        # outside the band the original scheme is stable again
+        for k in (0.4, 2.2):
+            lam = vn.eigs(k * math.cos(th), k * math.sin(th), 0, 0, inp.s_paper(orig))
+            assert np.max(np.abs(lam)) < 1.0 + 1e-12
+    for th in (0.0, math.pi / 2):
+        for k in np.linspace(0.05, 3.0, 40):
+            for r in (opt, orig):
+                lam = vn.eigs(k * math.cos(th), k * math.sin(th), 0, 0, inp.s_paper(r))
+                assert np.max(np.abs(lam)) < 1.0 + 1e-9
+
+
+@pytest.mark.parametrize("U,name", [(0.0, "LL"), (0.1, "OPT"), (0.0, "OPT-Z")])
+def test_step_matches_linear_propagation(U, name):
+    """At amplitude 1e-7 the nonlinear oracle equals the exact linear
+    evolution (every Fourier mode times G(k)^T built from the printed Psi)
+    up to O(amplitude^2): pins the oracle's streaming and collision against
+    section 2.3's Psi and section 4.1's amplification matrix."""
+    nx, ny, T = 24, 16, 40
+    r = inp.rates(name, nu=1e-3)
+    s = inp.s_paper(r)
+    rng = np.random.default_rng(5)
+    base = orc.init_eq(np.ones((ny, nx)), np.full((ny, nx), U), np.zeros((ny, nx)))
+    fp = 1e-7 * rng.standard_normal((9, ny, nx)) * base
+    got = orc.run(base + fp, s, T) - base
+    want = vn.propagate_linear(fp, T, U, 0.0, s)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err < 1e-6
+
+
+def test_plane_wave_eigenmode_rate():
+    """A small-amplitude acoustic eigenmode of G(k) put on the lattice by the
+    oracle decays and turns by exactly lambda per step."""
+    nx, ny, m, T = 32, 4, 3, 25
+    s = inp.s_paper(inp.rates("LL", nu=2e-3))
+    k = 2 * math.pi * m / nx
+    G = vn.amplification(k, 0.0, 0.0, 0.0, s)
+    lam, vec = np.linalg.eig(G)
+    j = np.argmax(np.abs(lam) - 10 * (np.abs(vn.mode_rates(lam, k)[1] - vn.CS) > 0.1))
+    x = np.arange(nx)
+    mode = vec[:, j][:, None, None] * np.exp(1j * k * x)[None, None, :] * np.ones((1, ny, 1))
+    base = orc.init_eq(np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)))
+    A = 1e-8
+    f = base + A * np.real(mode)
+    g = orc.run(f, s, T) - base
+    want = A * np.real(lam[j] ** T * mode)
+    assert np.linalg.norm(g - want) / np.linalg.norm(want) < 1e-6
+
+
+# ----------------------------------------------------------- pulse pins
+def test_pulse_integral_at_t0_is_gaussian():
+    """Eq. exactpules at t = 0: the Hankel transform of the Gaussian returns
+    the initial pulse eps exp(-alpha eta^2)."""
+    from oracle import pulse
+    eta = np.linspace(0, 30, 61)
+    eps, b = 1e-3, 4.0
+    got = pulse.bessel(eta, 0.0, eps, b)
+    want = eps * np.exp(-pulse.alpha_of(b) * eta ** 2)
+    assert np.max(np.abs(got - want)) < 1e-12 * eps * 1e3
+
+
+def test_pulse_periodic_equals_free_space_before_images_arrive():
+    from oracle import pulse
+    n, eps, b, t = 256, 1e-3, 4.0, 40.0
+    rho = pulse.periodic(n, n, 128.0, 128.0, t, eps, b)
+    x = np.arange(100, 160)
+    eta = np.abs(x - 128.0)
+    want = pulse.bessel(eta, t, eps, b)
+    assert np.max(np.abs(rho[128, 100:160] - want)) < 1e-9 * eps * 1e3
+    # a ring: the wave front sits near c_s t
+    r_peak = eta[np.argmax(want)]
+    assert abs(r_peak - vn.CS * t) < 3 * b
+
+
+def test_pulse_mass_is_conserved():
+    from oracle import pulse
+    eps, b = 1e-3, 4.0
+    for t in (0.0, 17.0, 200.0):
+        rho = pulse.periodic(64, 64, 32.0, 32.0, t, eps, b)
+        assert abs(rho.sum() - math.pi * eps / pulse.alpha_of(b)) < 1e-12
+
+
+def test_oracle_pulse_follows_linear_acoustics():
+    """The oracle's Gaussian pulse against the continuum solution with
+    viscous damping k^2 (sigma_e + sigma_nu)/6: the two differ only by the
+    scheme's dispersion error, which is small for a well-resolved pulse."""
+    from oracle import pulse
+    n, eps, b, T = 96, 1e-6, 6.0, 60
+    r = inp.rates("LL", nu=1e-3)
+    s = inp.s_paper(r)
+    rho, ux, uy = inp.gaussian_pulse(n, n, eps, b, 48.0, 48.0)
+    f = orc.run(orc.init_eq(rho, ux, uy), s, T)
+    got = orc.moments(f)[0] - 1.0
+    se, sn = sig(r, "s_e"), sig(r, "s_nu")
+    want = pulse.periodic(n, n, 48.0, 48.0, T, eps, b,
+                          gamma=lambda k: k * k * (se + sn) / 6)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err < 0.03
+    # without the damping the continuum model is clearly worse
+    free = pulse.periodic(n, n, 48.0, 48.0, T, eps, b)
+    assert np.linalg.norm(got - free) / np.linalg.norm(free) > err
+
+
+# ----------------------------------------------------- printed parameters
+@pytest.fixture(scope="module")
+def golden():
+    with open(os.path.join(HERE, "golden", "paper_tables.json")) as fh:
+        return json.load(fh)
+
+
+def test_input_tables_match_the_paper(golden):
+    for tab, mine in (("table1", inp.TABLE1), ("table2", inp.TABLE2),
+                      ("table3", inp.TABLE3), ("table4", inp.TABLE4),
+                      ("table5", inp.TABLE5)):
+        for grp, vals in mine.items():
+            for key, v in vals.items():
+                assert golden[tab][grp][key] == v, (tab, grp, key)
+    assert golden["lallemand_luo"]["s_e"] == inp.LL["s_e"]
+    assert golden["lallemand_luo"]["s_eps"] == inp.LL["s_eps"]
+    assert golden["lallemand_luo"]["s_q"] == inp.LL["s_q"]
+
+
+def test_table3_and_table5_agree_through_sigma(golden):
+    """sigma = 1/s - 1/2 (section 2.3) maps Table 5 onto Table 3."""
+    for grp in ("A", "B"):
+        t3, t5 = golden["table3"][grp], golden["table5"][grp]
+        for key in ("e", "nu", "eps", "q"):
+            s_from_sigma = 1.0 / (t3["sigma_" + key] + 0.5)
+            assert abs(s_from_sigma - t5["s_" + key]) < 2e-9
+
+
+def test_table4_viscosity_column(golden):
+    """Table 4's nu equals sigma_nu / 3 = (1/s_nu - 1/2)/3 to printed digits."""
+    for grp in ("A", "B"):
+        t = golden["table4"][grp]
+        nu = (1.0 / t["s_nu"] - 0.5) / 3.0
+        assert abs(nu - t["nu"]) / t["nu"] < 2e-5
+
+
+def test_sound_speed(golden):
+    assert abs(vn.CS - golden["sound_speed"]["cs"]) < 5e-6
+
+
+def test_ll_order_is_the_c_abi_vector():
+    """The Lallemand-Luo vector s = (0, 1.64, 1.54, 0, 1.9, 0, 1.9, 1/tau,
+    1/tau), tau = 1/2 + 3 nu, is the ABI's order; the paper's order puts
+    s_e at index 3 (section 2.3)."""
+    r = inp.rates("LL", nu=1e-3)
+    tau = 0.5 + 3e-3
+    assert np.allclose(inp.s_ll(r), [0, 1.64, 1.54, 0, 1.9, 0, 1.9, 1 / tau, 1 / tau],
+                       rtol=0, atol=1e-15)
+    sp = inp.s_paper(r)
+    assert sp[3] == 1.64 and sp[4] == 1.54 and sp[5] == sp[6] == 1.9
+    assert sp[7] == sp[8] == 1 / tau and not sp[:3].any()
