@@ -1,0 +1,251 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) D2Q9 multi-relaxation-time lattice
+ * Boltzmann library (liblbm.so).
+ *
+ * The scheme is the one of Xu & Sagaut, "Optimal low-dispersion
+ * low-dissipation LBM schemes for computational aeroacoustics"
+ * (arXiv 1107.4543):
+ *   - evolution f_i(x + c_i, t + 1) = f_i + Lambda_ij (f_j^eq - f_j)
+ *     (section 2.1, Eq. blbs) on a periodic nx x ny lattice, dt = dx = 1;
+ *   - Lambda = M^-1 S M, conserved moments rho, jx, jy kept, the others
+ *     relaxed m_i <- m_i - s_i (m_i - m_i^eq) (section 2.1,
+ *     Eqs. eq_conservative, eq_noconservative, q-macro);
+ *   - D2Q9 equilibrium moments {rho, jx, jy, -2rho + 3|j|^2/rho,
+ *     rho - 3|j|^2/rho, -jx, -jy, (jx^2 - jy^2)/rho, jx jy/rho} and
+ *     S = diag(0,0,0,s_e,s_eps,s_q,s_q,s_nu,s_nu) (section 2.3).
+ * The paper prints neither the velocity order nor M; this library uses
+ * c_0..c_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1)
+ * and the Lallemand-Luo D2Q9 moment matrix.
+ *
+ * Conventions (all entry points):
+ *   - return LBM_OK (0) on success, LBM_PENDING (> 0) for an unfinished
+ *     request, or a negative LBM_E* code; lbm_strerror() names a code and
+ *     lbm_last_error() gives the calling thread's last detailed message;
+ *   - host arrays are owned by the caller and are row-major ny x nx
+ *     (index y * nx + x) float64, populations 9 x ny x nx (index
+ *     (i * ny + y) * nx + x);
+ *   - device memory of a lattice is owned by its handle; arguments named
+ *     *_dev are device pointers owned by the caller;
+ *   - a handle is not thread-safe; the server (lbm_server_*) is;
+ *   - every call runs on the GPU that was current at lbm_create; work is
+ *     enqueued on the handle's stream (lbm_set_stream), and the calls that
+ *     return host data synchronize that stream.
+ * No entry point falls back to the CPU: without a usable GPU they fail
+ * with LBM_ECUDA.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ codes */
+#define LBM_OK 0
+#define LBM_PENDING 1
+#define LBM_EINVAL (-1)    /* bad argument (sizes, rates, null pointer)    */
+#define LBM_ENOMEM (-2)    /* device or host allocation failed / budget    */
+#define LBM_ECUDA (-3)     /* a CUDA call failed                           */
+#define LBM_EUNSTABLE (-4) /* non-finite populations detected              */
+#define LBM_ETIMEOUT (-5)  /* a bounded wait ran out                       */
+#define LBM_ENOTFOUND (-6) /* unknown request id                           */
+#define LBM_ECLOSED (-7)   /* server shutting down                         */
+
+/* storage types of the populations.  The *DEV types store the deviation
+ * f' = f - f^eq(rho0, u0) and collide in FP32; LBM_F64 stores the full
+ * populations and computes in FP64 with the operation order of a plain
+ * matrix-vector implementation of section 2.1. */
+#define LBM_F64 0
+#define LBM_F32DEV 1
+#define LBM_F16DEV 2  /* FP16, scaled by a power of two fixed at init */
+#define LBM_BF16DEV 3
+
+typedef struct lbm_ctx *lbm_handle;
+
+/* lbm_create -- allocate a periodic nx x ny lattice (section 2.1).
+ *   S[9]   relaxation rates in Lallemand-Luo order
+ *          (rho, e, eps, jx, qx, jy, qy, pxx, pxy), e.g. the original
+ *          scheme's (0, 1.64, 1.54, 0, 1.9, 0, 1.9, 1/tau, 1/tau) of
+ *          section 2.3; the library maps them to the paper's order
+ *          (rho, jx, jy, e, eps, qx, qy, pxx, pxy).  Entries of the conserved
+ *          slots (rho, jx, jy) are ignored but must be finite; the others
+ *          must lie in (0, 2].  The two q entries may differ, as may the two
+ *          p entries.
+ *   rho0, u0[2]  reference state: the base f^eq(rho0, u0) of the
+ *          deviation storage types and the initial uniform state.
+ *   storage_dtype  LBM_F64 / LBM_F32DEV / LBM_F16DEV / LBM_BF16DEV.
+ * The lattice starts as the uniform equilibrium f^eq(rho0, u0).
+ * Errors: LBM_EINVAL (nx or ny < 2, rates out of range, rho0 <= 0, null
+ * out), LBM_ENOMEM, LBM_ECUDA (no GPU).  *out is set only on success. */
+int lbm_create(int nx, int ny, const double S[9], double rho0,
+               const double u0[2], int storage_dtype, lbm_handle *out);
+
+/* lbm_init_field -- set f = f^eq(rho, u) at every node from host fields
+ * rho, ux, uy (ny x nx each); t is reset to 0.  Initialisation by the
+ * equilibrium of the prescribed macroscopic fields (section 5.2 gives only
+ * rho and u).  For LBM_F16DEV the power-of-two storage scale is chosen here
+ * from the largest |f'|.  Copies host->device and synchronizes.
+ * Errors: LBM_EINVAL (null pointer, rho <= 0 somewhere), LBM_ECUDA. */
+int lbm_init_field(lbm_handle h, const double *rho, const double *ux,
+                   const double *uy);
+
+/* lbm_init_field_dev -- as lbm_init_field with device fields (float64,
+ * ny x nx, row-major, caller-owned); enqueued, no host copy.  For
+ * LBM_F16DEV it synchronizes once to read the largest |f'|. */
+int lbm_init_field_dev(lbm_handle h, const double *rho_dev,
+                       const double *ux_dev, const double *uy_dev);
+
+/* lbm_init_analytic -- f = f^eq(rho, u) of an analytic field computed on
+ * the device (no host arrays):
+ *   kind LBM_INIT_GAUSSIAN: rho = rho0 + p[0] exp(-ln2 |x - (p[2],p[3])|^2
+ *        / p[1]^2) with the minimum-image distance, u = u0 (section 5.2);
+ *   kind LBM_INIT_PLANE: rho = rho0 + p[0] cos(2 pi p[1] x / nx),
+ *        ux = u0x + p[0] cos(...) / (sqrt(3) rho0), uy = u0y (a right-running
+ *        acoustic wave with p[1] wavelengths in the period). */
+#define LBM_INIT_GAUSSIAN 1
+#define LBM_INIT_PLANE 2
+int lbm_init_analytic(lbm_handle h, int kind, const double params[8]);
+
+/* lbm_step -- enqueue n >= 0 time steps (one fused pull-stream + collide
+ * kernel per step, replayed from a captured CUDA graph in chunks) on the
+ * handle's stream and return without waiting.  Errors: LBM_EINVAL (n < 0),
+ * LBM_ECUDA (launch failure). */
+int lbm_step(lbm_handle h, long n);
+
+/* lbm_moments -- rho, ux, uy (host, ny x nx) at the current time: the
+ * moments of the pre-collision populations, u = j / rho.  Synchronizes. */
+int lbm_moments(lbm_handle h, double *rho, double *ux, double *uy);
+
+/* lbm_moments_dev -- as lbm_moments into caller-owned device arrays;
+ * enqueued, does not synchronize. */
+int lbm_moments_dev(lbm_handle h, double *rho_dev, double *ux_dev,
+                    double *uy_dev);
+
+/* lbm_destroy -- synchronize the handle's stream and free its memory. */
+int lbm_destroy(lbm_handle h);
+
+/* ---------------------------------------------------------- extensions */
+/* Full populations f (host, 9 x ny x nx, float64) at the current time:
+ * checkpoint (get) and restore / arbitrary initial state (set).  For the
+ * deviation types the base f^eq(rho0, u0) is added / subtracted in FP64;
+ * set() on LBM_F16DEV re-chooses the storage scale.  Both synchronize. */
+int lbm_get_populations(lbm_handle h, double *f);
+int lbm_set_populations(lbm_handle h, const double *f);
+
+/* Use `stream` (a cudaStream_t, e.g. torch.cuda.current_stream()) for all
+ * further work of the handle; NULL restores the handle's own stream. */
+int lbm_set_stream(lbm_handle h, void *stream);
+
+/* Wait for the handle's stream. */
+int lbm_sync(lbm_handle h);
+
+/* Global sums over the lattice in FP64, by a deterministic two-stage
+ * reduction on the device: out[0] = sum rho', out[1] = sum jx',
+ * out[2] = sum jy' (deviations from rho0, rho0 u0), out[3] = number of
+ * non-finite stored populations.  The collision conserves mass and
+ * momentum exactly in exact arithmetic (section 2.1,
+ * Eq. eq_conservative), so out[0..2] measure rounding drift.
+ * Synchronizes; returns LBM_EUNSTABLE when out[3] > 0. */
+int lbm_drift(lbm_handle h, double out[4]);
+
+/* Static description of a lattice. */
+typedef struct {
+  int nx, ny;
+  int pitch;          /* elements per stored row (>= nx)                */
+  int dtype;          /* LBM_F64 ... LBM_BF16DEV                         */
+  int elem_bytes;     /* bytes per stored population                     */
+  long t;             /* time steps taken since the last init/set        */
+  double qscale;      /* LBM_F16DEV: stored value = f' * qscale          */
+  double S_paper[9];  /* rates in the paper's moment order               */
+  size_t device_bytes;/* device memory held by the handle                */
+} lbm_info_t;
+int lbm_info(lbm_handle h, lbm_info_t *out);
+
+/* Device allocator used for all later allocations of the library
+ * (e.g. a caching allocator).  alloc returns NULL on failure.  Passing
+ * NULL functions restores cudaMalloc / cudaFree.  Not thread-safe with
+ * respect to concurrent lbm_create calls. */
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*lbm_free_fn)(void *ptr, void *ctx);
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void *ctx);
+
+const char *lbm_strerror(int code);
+const char *lbm_last_error(void);
+
+/* ------------------------------------------------------------- batches */
+/* Many independent lattices advanced together: every time step is ONE
+ * kernel launch per storage type over a flattened (lattice, row group,
+ * segment) work list of all members, and chunks of 64 steps are replayed
+ * from a captured CUDA graph.  Members must be deviation-storage lattices
+ * (LBM_F32DEV, LBM_F16DEV or LBM_BF16DEV) created on the current device,
+ * none of them in another batch; they keep their own memory, rates and
+ * reference state, and each advances with exactly the arithmetic of
+ * lbm_step.  While in the batch a member's work runs on the batch stream
+ * (its first member's); lbm_moments, lbm_get_populations and lbm_drift on a
+ * member work as usual between batch steps, while lbm_step, init and
+ * set_populations on a member are rejected (LBM_EINVAL).  lbm_batch_destroy
+ * releases the members, which stay valid. */
+typedef struct lbm_batch_ctx *lbm_batch;
+int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out);
+int lbm_batch_step(lbm_batch b, long n);
+int lbm_batch_destroy(lbm_batch b);
+
+/* ------------------------------------------------------------- serving */
+/* A request: one lattice solve.  init_kind is LBM_INIT_GAUSSIAN or
+ * LBM_INIT_PLANE (params as for lbm_init_analytic) or LBM_INIT_FIELDS (the
+ * host fields rho/ux/uy, ny x nx, copied at submit time). */
+#define LBM_INIT_FIELDS 0
+typedef struct {
+  int nx, ny;
+  double S[9];            /* Lallemand-Luo order, as for lbm_create        */
+  double rho0, u0[2];
+  int dtype;              /* LBM_F32DEV, LBM_F16DEV or LBM_BF16DEV          */
+  long steps;
+  int init_kind;
+  double init_params[8];
+  const double *rho, *ux, *uy; /* LBM_INIT_FIELDS only                     */
+} lbm_request;
+
+typedef struct lbm_server_ctx *lbm_server;
+
+/* A continuous-batching server on the current device: a host scheduler
+ * thread admits queued requests while their device bytes fit in
+ * hbm_budget_bytes, steps all admitted lattices together in generations of
+ * at most chunk_steps steps (one batched launch per step), retires finished
+ * lattices (moments copied to host, memory freed) and admits newcomers
+ * between generations.  Thread-safe. */
+int lbm_server_create(size_t hbm_budget_bytes, long chunk_steps,
+                      lbm_server *out);
+
+/* Queue a request; never waits for the GPU.  *id identifies it.
+ * Errors: LBM_EINVAL (bad request), LBM_ENOMEM (the request alone exceeds
+ * the budget), LBM_ECLOSED. */
+int lbm_submit(lbm_server s, const lbm_request *req, long long *id);
+
+/* LBM_PENDING while the request runs; LBM_OK once finished: copies its
+ * rho, ux, uy (host, ny x nx; any may be NULL) and the latency from submit
+ * to results-on-host in seconds, then forgets the request.  A request that
+ * failed returns its error code (and is forgotten). */
+int lbm_poll(lbm_server s, long long id, double *rho, double *ux, double *uy,
+             double *latency_s);
+
+typedef struct {
+  long long submitted, admitted, completed, failed;
+  long long generations;    /* batched step chunks run                    */
+  int resident;             /* lattices on the device now                 */
+  int peak_resident;
+  size_t resident_bytes, peak_bytes;
+  double lattice_updates;   /* node-steps done                            */
+  double busy_s;            /* wall time with work on the device          */
+} lbm_server_stats_t;
+int lbm_server_stats(lbm_server s, lbm_server_stats_t *out);
+
+/* Stop admitting, wait for admitted work, free everything. */
+int lbm_server_destroy(lbm_server s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

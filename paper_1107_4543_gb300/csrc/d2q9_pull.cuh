@@ -1,0 +1,222 @@
+// D2Q9 pull streaming with 128-bit vector I/O (device helpers).
+//
+// Storage: populations as 9 planes f[i][y][x] of `pitch` elements per row
+// (pitch >= nx, a multiple of the vector width), periodic in x and y.  The
+// buffer holds the post-collision populations of the previous step, so the
+// pre-collision population at node (x, y) is f_i(x, y) = P_i(x - cx_i,
+// y - cy_i): the collide-then-stream of section 2.1 (Eq. blbs) written as a
+// pull.
+//
+// Work unit ("task"): one warp covers R = 32 / L rows; in each row L lanes
+// cover L consecutive chunks of V nodes (V * sizeof(T) = 16 bytes).  Every
+// plane is read with aligned 16-byte loads; the +-1 x-shifts are formed from
+// the neighbouring lane's chunk by a warp shuffle (width L), and only the two
+// chunks at a segment's ends make one extra scalar load (a cache hit: the
+// neighbouring warp loads the same line).  Periodic wrap is folded into the
+// row index (y) and into those edge loads (x).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// velocities c_0..c_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1)
+__host__ __device__ constexpr int CXd(int i) {
+  return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int CYd(int i) {
+  return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+}
+
+// ---------------------------------------------------------- element I/O
+template <typename T> struct Elem;
+
+template <> struct Elem<float> {
+  static constexpr int V = 4;
+  using C = float;  // compute type
+  static __device__ __forceinline__ void unpack(const uint4 &r, float *o) {
+    o[0] = __uint_as_float(r.x); o[1] = __uint_as_float(r.y);
+    o[2] = __uint_as_float(r.z); o[3] = __uint_as_float(r.w);
+  }
+  static __device__ __forceinline__ uint4 pack(const float *v) {
+    return make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]),
+                      __float_as_uint(v[2]), __float_as_uint(v[3]));
+  }
+  static __device__ __forceinline__ float one(const float *p) { return __ldg(p); }
+};
+
+template <> struct Elem<__half> {
+  static constexpr int V = 8;
+  using C = float;
+  static __device__ __forceinline__ void unpack(const uint4 &r, float *o) {
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      __half2 h = *reinterpret_cast<const __half2 *>(&w[k]);
+      float2 f = __half22float2(h);
+      o[2 * k] = f.x; o[2 * k + 1] = f.y;
+    }
+  }
+  static __device__ __forceinline__ uint4 pack(const float *v) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      __half2 h = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
+      w[k] = *reinterpret_cast<uint32_t *>(&h);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  static __device__ __forceinline__ float one(const __half *p) {
+    return __half2float(__ldg(p));
+  }
+};
+
+template <> struct Elem<__nv_bfloat16> {
+  static constexpr int V = 8;
+  using C = float;
+  static __device__ __forceinline__ void unpack(const uint4 &r, float *o) {
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      // bf16 -> f32 is exact: the bf16 bits are the high half of the f32
+      o[2 * k] = __uint_as_float(w[k] << 16);
+      o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+  }
+  static __device__ __forceinline__ uint4 pack(const float *v) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+      w[k] = *reinterpret_cast<uint32_t *>(&h);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  static __device__ __forceinline__ float one(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ldg(p));
+  }
+};
+
+template <> struct Elem<double> {
+  static constexpr int V = 2;
+  using C = double;
+  static __device__ __forceinline__ void unpack(const uint4 &r, double *o) {
+    o[0] = __hiloint2double((int)r.y, (int)r.x);
+    o[1] = __hiloint2double((int)r.w, (int)r.z);
+  }
+  static __device__ __forceinline__ uint4 pack(const double *v) {
+    return make_uint4((unsigned)__double2loint(v[0]), (unsigned)__double2hiint(v[0]),
+                      (unsigned)__double2loint(v[1]), (unsigned)__double2hiint(v[1]));
+  }
+  static __device__ __forceinline__ double one(const double *p) { return __ldg(p); }
+};
+
+// geometry of one lattice as the step kernels see it
+struct Geom {
+  int nx, ny, pitch;
+  int L;       // lanes per row segment (4, 8, 16 or 32)
+  int nseg;    // segments per row: ceil(ceil(nx / V) / L)
+  int rgroups; // row groups: ceil(ny / (32 / L))
+  long long plane;  // pitch * ny
+};
+
+// Position of this lane for task `task` of a lattice.
+struct LanePos {
+  int y, x0, lseg;  // row, first node of the chunk, lane index in segment
+  bool active;      // chunk holds at least one real node of a real row
+};
+
+template <int V>
+__device__ __forceinline__ LanePos lane_pos(const Geom &g, long long task, int lane) {
+  LanePos p;
+  int rows_per_warp = 32 / g.L;
+  int seg = (int)(task % g.nseg);
+  int rg = (int)(task / g.nseg);
+  p.lseg = lane & (g.L - 1);
+  p.y = rg * rows_per_warp + lane / g.L;
+  p.x0 = (seg * g.L + p.lseg) * V;
+  p.active = (p.y < g.ny) && (p.x0 < g.nx);
+  return p;
+}
+
+// Pull the 9 pre-collision populations of the V nodes of this lane's chunk
+// into out[i][e] (compute type C; storage value times inv_scale when
+// SCALED).  All 32 lanes must call it (it shuffles); inactive lanes get
+// zeros.  Elements of padding columns (x >= nx) get unspecified values that
+// never reach a real node.
+template <typename T, bool SCALED>
+__device__ __forceinline__ void pull9(const T *__restrict__ src, const Geom &g,
+                                      const LanePos &p,
+                                      typename Elem<T>::C inv_scale,
+                                      typename Elem<T>::C (&out)[9][Elem<T>::V]) {
+  using C = typename Elem<T>::C;
+  constexpr int V = Elem<T>::V;
+  const int L = g.L;
+  const int last = g.nx - 1;
+  // which element of this chunk is the last real node (or -1)
+  const int e_last = (p.x0 <= last && last < p.x0 + V) ? last - p.x0 : -1;
+  auto sc = [&](C a) -> C { return SCALED ? a * inv_scale : a; };
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int cx = CXd(i), cy = CYd(i);
+    int ys = p.y - cy;
+    ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
+    const T *row = src + (long long)i * g.plane + (long long)ys * g.pitch;
+    C v[V];
+    if (p.active) {
+      uint4 r = __ldg(reinterpret_cast<const uint4 *>(row + p.x0));
+      Elem<T>::unpack(r, v);
+    } else {
+#pragma unroll
+      for (int e = 0; e < V; ++e) v[e] = C(0);
+    }
+    if (cx == 0) {
+#pragma unroll
+      for (int e = 0; e < V; ++e) out[i][e] = sc(v[e]);
+    } else if (cx == 1) {
+      // node x pulls from x - 1
+      C prev = __shfl_up_sync(0xffffffffu, v[V - 1], 1, L);
+      if (p.active && (p.lseg == 0 || p.x0 == 0))
+        prev = Elem<T>::one(row + (p.x0 == 0 ? last : p.x0 - 1));
+      out[i][0] = sc(prev);
+#pragma unroll
+      for (int e = 1; e < V; ++e) out[i][e] = sc(v[e - 1]);
+    } else {
+      // node x pulls from x + 1 (column 0 for the last real node)
+      C next = __shfl_down_sync(0xffffffffu, v[0], 1, L);
+      if (p.active && p.lseg == L - 1 && p.x0 + V <= last)
+        next = Elem<T>::one(row + p.x0 + V);
+#pragma unroll
+      for (int e = 0; e < V - 1; ++e) out[i][e] = sc(v[e + 1]);
+      out[i][V - 1] = sc(next);
+      if (e_last >= 0) {
+        C w = sc(Elem<T>::one(row));
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+          if (e == e_last) out[i][e] = w;
+      }
+    }
+  }
+}
+
+// Store the 9 post-collision populations of this lane's chunk (aligned
+// 16-byte stores; padding columns x >= nx receive unspecified values).
+template <typename T, bool SCALED>
+__device__ __forceinline__ void store9(T *__restrict__ dst, const Geom &g, const LanePos &p,
+                                       typename Elem<T>::C scale,
+                                       typename Elem<T>::C (&in)[9][Elem<T>::V]) {
+  using C = typename Elem<T>::C;
+  constexpr int V = Elem<T>::V;
+  if (!p.active) return;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    C v[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) v[e] = SCALED ? in[i][e] * scale : in[i][e];
+    T *row = dst + (long long)i * g.plane + (long long)p.y * g.pitch;
+    *reinterpret_cast<uint4 *>(row + p.x0) = Elem<T>::pack(v);
+  }
+}
+
+}  // namespace lbm

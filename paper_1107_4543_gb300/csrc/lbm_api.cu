@@ -1,0 +1,780 @@
+// C ABI of liblbm.so (declared in include/lbm.h): lattice handles, the step
+// loop (graph-captured chunks of fused step launches), initialisation,
+// moments, checkpoints, drift, batches.  The serving scheduler lives in
+// serve.cu.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+static std::mutex g_alloc_mu;
+static lbm_alloc_fn g_alloc = nullptr;
+static lbm_free_fn g_free = nullptr;
+static void *g_alloc_ctx = nullptr;
+
+void *dev_alloc(size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  lbm_alloc_fn a;
+  void *ctx;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    a = g_alloc;
+    ctx = g_alloc_ctx;
+  }
+  if (a) return a(bytes, ctx);
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(void *p) {
+  if (!p) return;
+  lbm_free_fn f;
+  void *ctx;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    f = g_free;
+    ctx = g_alloc_ctx;
+  }
+  if (f)
+    f(p, ctx);
+  else
+    cudaFree(p);
+}
+
+int sm_count() {
+  int d = 0, n = 0;
+  if (cudaGetDevice(&d) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return 148;
+  }
+  return n;
+}
+
+// Lanes per row segment: the smallest power of two covering the row's
+// 16-byte chunks, at most a warp.
+static int lanes_for(int nchunks) {
+  int L = 1;
+  while (L < nchunks && L < 32) L <<= 1;
+  return L;
+}
+
+static Geom make_geom(int nx, int ny, int V, int esize) {
+  Geom g;
+  g.nx = nx;
+  g.ny = ny;
+  const int align = std::max(V, 128 / esize);  // rows start on 128-byte lines
+  g.pitch = (nx + align - 1) / align * align;
+  const int nchunks = (nx + V - 1) / V;
+  g.L = lanes_for(nchunks);
+  g.nseg = (nchunks + g.L - 1) / g.L;
+  const int rows_per_warp = 32 / g.L;
+  g.rgroups = (ny + rows_per_warp - 1) / rows_per_warp;
+  g.plane = (long long)g.pitch * ny;
+  return g;
+}
+
+struct DevGuard {
+  int prev = -1, want;
+  explicit DevGuard(int d) : want(d) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != d) cudaSetDevice(d);
+  }
+  ~DevGuard() {
+    if (prev >= 0 && prev != want) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_ctx {
+  Lattice L;
+  int device = 0;
+  double S_paper[9];
+  double rho0 = 1.0, u0[2] = {0, 0};
+  double f0[9];
+  double qscale = 1.0;
+  cudaStream_t own_stream = nullptr, stream = nullptr;
+  long t = 0;
+  double *partials = nullptr, *drift_out = nullptr;
+  unsigned int *maxbits = nullptr;
+  double *stage = nullptr;  // 3 * N doubles, lazily allocated
+  size_t bytes = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  int block = 256;
+  int grid_cap = 0;
+  lbm_batch_ctx *batch = nullptr;
+};
+
+#define CK(call)                                                            \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess) {                                                \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));        \
+      cudaGetLastError();                                                   \
+      return LBM_ECUDA;                                                     \
+    }                                                                       \
+  } while (0)
+
+#define REQUIRE(cond, msg)         \
+  do {                             \
+    if (!(cond)) {                 \
+      set_error(msg);              \
+      return LBM_EINVAL;           \
+    }                              \
+  } while (0)
+
+static AuxView aux_view(const lbm_ctx *h) {
+  AuxView a;
+  a.g = h->L.g;
+  a.dtype = h->L.dtype;
+  a.buf = h->L.buf[h->L.cur];
+  a.rho0 = h->rho0;
+  a.jx0 = h->rho0 * h->u0[0];
+  a.jy0 = h->rho0 * h->u0[1];
+  for (int i = 0; i < 9; ++i) a.f0[i] = h->f0[i];
+  a.scale = h->qscale;
+  return a;
+}
+
+static void set_qscale(lbm_ctx *h, double maxabs) {
+  // stored |f'| * qscale stays near 2^14: 11-bit FP16 mantissas with 4x
+  // headroom below the largest finite FP16 (65504), and no subnormals for
+  // values down to 2^-10 of the largest
+  double s = 1.0;
+  if (maxabs > 0 && isfinite(maxabs)) {
+    int k = 14 - (int)ceil(log2(maxabs));
+    k = std::max(-100, std::min(100, k));
+    s = ldexp(1.0, k);
+  }
+  h->qscale = s;
+  h->L.dp.scale = (float)s;
+  h->L.dp.inv_scale = (float)(1.0 / s);
+}
+
+static int free_graph(lbm_ctx *h) {
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_steps = 0;
+  }
+  return LBM_OK;
+}
+
+static cudaError_t launch_one(lbm_ctx *h, int from, cudaStream_t st) {
+  const void *src = h->L.buf[from];
+  void *dst = h->L.buf[from ^ 1];
+  if (h->L.dtype == LBM_F64) return launch_step_f64(h->L, src, dst, st, h->block, h->grid_cap);
+  return launch_step_dev(h->L, src, dst, st, h->block, h->grid_cap);
+}
+
+// capture `steps` (even) launches starting from buffer 0 into a graph
+static int capture_graph(lbm_ctx *h, int steps) {
+  free_graph(h);
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) e = launch_one(h, k & 1, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    h->graph = nullptr;
+    set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+    cudaGetLastError();
+    return LBM_ECUDA;
+  }
+  h->graph_steps = steps;
+  return LBM_OK;
+}
+
+static int ensure_stage(lbm_ctx *h) {
+  if (h->stage) return LBM_OK;
+  const size_t n = (size_t)h->L.g.nx * h->L.g.ny;
+  h->stage = (double *)dev_alloc(3 * n * sizeof(double));
+  if (!h->stage) {
+    set_error("cannot allocate the field staging buffer");
+    return LBM_ENOMEM;
+  }
+  h->bytes += 3 * n * sizeof(double);
+  return LBM_OK;
+}
+
+static int check_rates(const double S[9]) {
+  static const int conserved[3] = {0, 3, 5};  // rho, jx, jy in LL order
+  for (int k = 0; k < 9; ++k) {
+    bool cons = (k == conserved[0] || k == conserved[1] || k == conserved[2]);
+    if (!isfinite(S[k])) return 0;
+    if (!cons && !(S[k] > 0.0 && S[k] <= 2.0)) return 0;
+  }
+  return 1;
+}
+
+// init f = f^eq(field) (kind 0: device arrays; else analytic)
+static int do_init(lbm_ctx *h, const double *rho, const double *ux, const double *uy, int kind,
+                   const double *params) {
+  if (h->batch) {
+    set_error("lattice is a batch member");
+    return LBM_EINVAL;
+  }
+  h->L.cur = 0;
+  AuxView a = aux_view(h);
+  if (h->L.dtype == LBM_F16DEV) {
+    CK(launch_maxdev_eq(a, rho, ux, uy, kind, params, h->maxbits, h->stream));
+    unsigned int bits = 0;
+    CK(cudaMemcpyAsync(&bits, h->maxbits, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    float m;
+    memcpy(&m, &bits, sizeof(m));
+    set_qscale(h, (double)m);
+    a = aux_view(h);
+  }
+  CK(launch_init_eq(a, rho, ux, uy, kind, params, h->stream));
+  h->t = 0;
+  return LBM_OK;
+}
+
+extern "C" {
+
+const char *lbm_strerror(int code) {
+  switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_PENDING: return "pending";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "out of memory";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_EUNSTABLE: return "non-finite populations";
+    case LBM_ETIMEOUT: return "timed out";
+    case LBM_ENOTFOUND: return "unknown request";
+    case LBM_ECLOSED: return "server closed";
+    default: return "unknown error";
+  }
+}
+
+const char *lbm_last_error(void) { return g_last_error.c_str(); }
+
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void *ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) {
+    set_error("allocator and free must both be set or both be NULL");
+    return LBM_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = alloc ? ctx : nullptr;
+  return LBM_OK;
+}
+
+int lbm_create(int nx, int ny, const double S[9], double rho0, const double u0[2],
+               int storage_dtype, lbm_handle *out) {
+  REQUIRE(out != nullptr && S != nullptr && u0 != nullptr, "null argument");
+  REQUIRE(nx >= 2 && ny >= 2, "nx and ny must be >= 2");
+  REQUIRE((long long)nx * ny <= (1LL << 40), "lattice too large");
+  REQUIRE(rho0 > 0.0 && isfinite(rho0), "rho0 must be positive");
+  REQUIRE(isfinite(u0[0]) && isfinite(u0[1]), "u0 must be finite");
+  REQUIRE(check_rates(S), "rates: non-conserved entries must lie in (0, 2], all finite");
+  int esize, V;
+  switch (storage_dtype) {
+    case LBM_F64: esize = 8; V = 2; break;
+    case LBM_F32DEV: esize = 4; V = 4; break;
+    case LBM_F16DEV:
+    case LBM_BF16DEV: esize = 2; V = 8; break;
+    default: REQUIRE(false, "unknown storage dtype");
+  }
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  lbm_ctx *h = new (std::nothrow) lbm_ctx();
+  if (!h) return LBM_ENOMEM;
+  h->device = dev;
+  h->L.g = make_geom(nx, ny, V, esize);
+  h->L.dtype = storage_dtype;
+  h->L.V = V;
+  h->L.esize = esize;
+  h->L.cur = 0;
+  // Lallemand-Luo order (rho, e, eps, jx, qx, jy, qy, pxx, pxy) -> paper
+  // order (rho, jx, jy, e, eps, qx, qy, pxx, pxy)
+  const int ll_of_paper[9] = {0, 3, 5, 1, 2, 4, 6, 7, 8};
+  for (int k = 0; k < 9; ++k) h->S_paper[k] = S[ll_of_paper[k]];
+  h->rho0 = rho0;
+  h->u0[0] = u0[0];
+  h->u0[1] = u0[1];
+  host_feq(rho0, u0[0], u0[1], h->f0);
+  DevParams &dp = h->L.dp;
+  dp.rho0 = (float)rho0;
+  dp.jx0 = (float)(rho0 * u0[0]);
+  dp.jy0 = (float)(rho0 * u0[1]);
+  dp.k3 = (float)(h->S_paper[3] / 36.0);
+  dp.k4 = (float)(h->S_paper[4] / 36.0);
+  dp.k5 = (float)(h->S_paper[5] / 12.0);
+  dp.k6 = (float)(h->S_paper[6] / 12.0);
+  dp.k7 = (float)(h->S_paper[7] / 4.0);
+  dp.k8 = (float)(h->S_paper[8] / 4.0);
+  dp.scale = 1.0f;
+  dp.inv_scale = 1.0f;
+  F64Params &fp = h->L.fp;
+  fp.s3 = h->S_paper[3];
+  fp.s4 = h->S_paper[4];
+  fp.s5 = h->S_paper[5];
+  fp.s6 = h->S_paper[6];
+  fp.s7 = h->S_paper[7];
+  fp.s8 = h->S_paper[8];
+
+  const size_t buf_bytes = (size_t)h->L.g.plane * 9 * esize;
+  h->L.buf[0] = dev_alloc(buf_bytes);
+  h->L.buf[1] = dev_alloc(buf_bytes);
+  h->partials = (double *)dev_alloc(sizeof(double) * 4 * drift_blocks());
+  h->drift_out = (double *)dev_alloc(sizeof(double) * 4);
+  h->maxbits = (unsigned int *)dev_alloc(sizeof(unsigned int));
+  if (!h->L.buf[0] || !h->L.buf[1] || !h->partials || !h->drift_out || !h->maxbits) {
+    lbm_destroy(h);
+    set_error("device allocation failed");
+    return LBM_ENOMEM;
+  }
+  h->bytes = 2 * buf_bytes + sizeof(double) * (4 * drift_blocks() + 4) + sizeof(unsigned int);
+  if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    lbm_destroy(h);
+    set_error("cannot create a stream");
+    return LBM_ECUDA;
+  }
+  h->stream = h->own_stream;
+  // start from the uniform equilibrium f^eq(rho0, u0)
+  if (cudaMemsetAsync(h->L.buf[0], 0, buf_bytes, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->L.buf[1], 0, buf_bytes, h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    lbm_destroy(h);
+    set_error("memset failed");
+    return LBM_ECUDA;
+  }
+  if (storage_dtype == LBM_F64) {
+    const double p[8] = {0, 1, 0, 0, 0, 0, 0, 0};  // zero-amplitude Gaussian
+    int rc = do_init(h, nullptr, nullptr, nullptr, LBM_INIT_GAUSSIAN, p);
+    if (rc != LBM_OK) {
+      lbm_destroy(h);
+      return rc;
+    }
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    set_error(std::string("create: ") + cudaGetErrorString(cudaGetLastError()));
+    lbm_destroy(h);
+    return LBM_ECUDA;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_destroy(lbm_handle h) {
+  if (!h) return LBM_EINVAL;
+  DevGuard g(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_graph(h);
+  dev_free(h->L.buf[0]);
+  dev_free(h->L.buf[1]);
+  dev_free(h->partials);
+  dev_free(h->drift_out);
+  dev_free(h->maxbits);
+  dev_free(h->stage);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  cudaGetLastError();
+  delete h;
+  return LBM_OK;
+}
+
+int lbm_set_stream(lbm_handle h, void *stream) {
+  REQUIRE(h != nullptr, "null handle");
+  DevGuard g(h->device);
+  CK(cudaStreamSynchronize(h->stream));
+  h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+  return LBM_OK;
+}
+
+int lbm_sync(lbm_handle h) {
+  REQUIRE(h != nullptr, "null handle");
+  DevGuard g(h->device);
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_init_field_dev(lbm_handle h, const double *rho, const double *ux, const double *uy) {
+  REQUIRE(h && rho && ux && uy, "null argument");
+  DevGuard g(h->device);
+  return do_init(h, rho, ux, uy, 0, nullptr);
+}
+
+int lbm_init_field(lbm_handle h, const double *rho, const double *ux, const double *uy) {
+  REQUIRE(h && rho && ux && uy, "null argument");
+  DevGuard g(h->device);
+  const size_t n = (size_t)h->L.g.nx * h->L.g.ny;
+  for (size_t k = 0; k < n; ++k)
+    REQUIRE(rho[k] > 0.0 && isfinite(rho[k]) && isfinite(ux[k]) && isfinite(uy[k]),
+            "fields must be finite with rho > 0");
+  int rc = ensure_stage(h);
+  if (rc != LBM_OK) return rc;
+  CK(cudaMemcpyAsync(h->stage, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->stage + n, ux, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->stage + 2 * n, uy, n * sizeof(double), cudaMemcpyHostToDevice,
+                     h->stream));
+  rc = do_init(h, h->stage, h->stage + n, h->stage + 2 * n, 0, nullptr);
+  if (rc != LBM_OK) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_init_analytic(lbm_handle h, int kind, const double params[8]) {
+  REQUIRE(h && params, "null argument");
+  REQUIRE(kind == LBM_INIT_GAUSSIAN || kind == LBM_INIT_PLANE, "unknown init kind");
+  for (int k = 0; k < 8; ++k) REQUIRE(isfinite(params[k]), "params must be finite");
+  if (kind == LBM_INIT_GAUSSIAN) REQUIRE(params[1] > 0.0, "half-width must be positive");
+  DevGuard g(h->device);
+  return do_init(h, nullptr, nullptr, nullptr, kind, params);
+}
+
+int lbm_step(lbm_handle h, long n) {
+  REQUIRE(h != nullptr, "null handle");
+  REQUIRE(n >= 0, "negative step count");
+  REQUIRE(h->batch == nullptr, "lattice is a batch member; step the batch");
+  DevGuard g(h->device);
+  const int G = 64;  // steps per captured graph (even)
+  while (n > 0) {
+    if (h->L.cur == 0 && n >= G) {
+      if (!h->graph || h->graph_steps != G) {
+        int rc = capture_graph(h, G);
+        if (rc != LBM_OK) return rc;
+      }
+      CK(cudaGraphLaunch(h->graph, h->stream));
+      n -= G;
+      h->t += G;
+    } else {
+      CK(launch_one(h, h->L.cur, h->stream));
+      h->L.cur ^= 1;
+      n -= 1;
+      h->t += 1;
+    }
+  }
+  return LBM_OK;
+}
+
+int lbm_moments_dev(lbm_handle h, double *rho, double *ux, double *uy) {
+  REQUIRE(h && rho && ux && uy, "null argument");
+  DevGuard g(h->device);
+  CK(launch_moments(aux_view(h), rho, ux, uy, h->stream));
+  return LBM_OK;
+}
+
+int lbm_moments(lbm_handle h, double *rho, double *ux, double *uy) {
+  REQUIRE(h && rho && ux && uy, "null argument");
+  DevGuard g(h->device);
+  int rc = ensure_stage(h);
+  if (rc != LBM_OK) return rc;
+  const size_t n = (size_t)h->L.g.nx * h->L.g.ny;
+  CK(launch_moments(aux_view(h), h->stage, h->stage + n, h->stage + 2 * n, h->stream));
+  CK(cudaMemcpyAsync(rho, h->stage, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(ux, h->stage + n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(uy, h->stage + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_get_populations(lbm_handle h, double *f) {
+  REQUIRE(h && f, "null argument");
+  DevGuard g(h->device);
+  const size_t n = (size_t)h->L.g.nx * h->L.g.ny;
+  double *tmp = (double *)dev_alloc(9 * n * sizeof(double));
+  if (!tmp) {
+    set_error("cannot allocate population staging");
+    return LBM_ENOMEM;
+  }
+  cudaError_t e = launch_get_pop(aux_view(h), tmp, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(f, tmp, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dev_free(tmp);
+  if (e != cudaSuccess) {
+    set_error(std::string("get_populations: ") + cudaGetErrorString(e));
+    cudaGetLastError();
+    return LBM_ECUDA;
+  }
+  return LBM_OK;
+}
+
+int lbm_set_populations(lbm_handle h, const double *f) {
+  REQUIRE(h && f, "null argument");
+  REQUIRE(h->batch == nullptr, "lattice is a batch member");
+  DevGuard g(h->device);
+  const size_t n = (size_t)h->L.g.nx * h->L.g.ny;
+  for (size_t k = 0; k < 9 * n; ++k) REQUIRE(isfinite(f[k]), "populations must be finite");
+  double *tmp = (double *)dev_alloc(9 * n * sizeof(double));
+  if (!tmp) {
+    set_error("cannot allocate population staging");
+    return LBM_ENOMEM;
+  }
+  h->L.cur = 0;
+  cudaError_t e =
+      cudaMemcpyAsync(tmp, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && h->L.dtype == LBM_F16DEV) {
+    e = launch_maxdev_pop(aux_view(h), tmp, h->maxbits, h->stream);
+    unsigned int bits = 0;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&bits, h->maxbits, sizeof(bits), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    float m;
+    memcpy(&m, &bits, sizeof(m));
+    if (e == cudaSuccess) set_qscale(h, (double)m);
+  }
+  if (e == cudaSuccess) e = launch_set_pop(aux_view(h), tmp, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dev_free(tmp);
+  if (e != cudaSuccess) {
+    set_error(std::string("set_populations: ") + cudaGetErrorString(e));
+    cudaGetLastError();
+    return LBM_ECUDA;
+  }
+  h->t = 0;
+  return LBM_OK;
+}
+
+int lbm_drift(lbm_handle h, double out[4]) {
+  REQUIRE(h && out, "null argument");
+  DevGuard g(h->device);
+  CK(launch_drift(aux_view(h), h->partials, h->drift_out, h->stream));
+  CK(cudaMemcpyAsync(out, h->drift_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return out[3] > 0 ? LBM_EUNSTABLE : LBM_OK;
+}
+
+int lbm_info(lbm_handle h, lbm_info_t *out) {
+  REQUIRE(h && out, "null argument");
+  out->nx = h->L.g.nx;
+  out->ny = h->L.g.ny;
+  out->pitch = h->L.g.pitch;
+  out->dtype = h->L.dtype;
+  out->elem_bytes = h->L.esize;
+  out->t = h->t;
+  out->qscale = h->qscale;
+  for (int k = 0; k < 9; ++k) out->S_paper[k] = h->S_paper[k];
+  out->device_bytes = h->bytes;
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batch
+struct lbm_batch_ctx {
+  std::vector<lbm_ctx *> members;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  struct Group {
+    int dtype;
+    int n;
+    long long ntasks;
+    BatchEntry *ents = nullptr;
+    int *block_first = nullptr;
+  };
+  std::vector<Group> groups;
+  std::vector<int> offs;                 // member buffer index at creation
+  std::vector<cudaStream_t> saved_streams;
+  int parity = 0;                        // steps taken mod 2
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  int block = 256;
+};
+
+static cudaError_t batch_launch_all(lbm_batch_ctx *b, int parity, cudaStream_t st) {
+  for (auto &gr : b->groups) {
+    cudaError_t e = launch_step_batch(gr.dtype, gr.ents, gr.n, gr.block_first, gr.ntasks, parity,
+                                      st, b->block);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static void batch_free(lbm_batch_ctx *b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (auto &gr : b->groups) {
+    dev_free(gr.ents);
+    dev_free(gr.block_first);
+  }
+  for (size_t k = 0; k < b->members.size(); ++k) {
+    auto *m = b->members[k];
+    if (m->batch == b) m->batch = nullptr;
+    if (k < b->saved_streams.size()) m->stream = b->saved_streams[k];
+  }
+  cudaGetLastError();
+  delete b;
+}
+
+extern "C" {
+
+int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
+  REQUIRE(n >= 1 && members && out, "bad batch arguments");
+  int dev = members[0] ? members[0]->device : 0;
+  for (int k = 0; k < n; ++k) {
+    REQUIRE(members[k] != nullptr, "null member");
+    REQUIRE(members[k]->L.dtype != LBM_F64, "batches take deviation-storage lattices only");
+    REQUIRE(members[k]->batch == nullptr, "lattice already in a batch");
+    REQUIRE(members[k]->device == dev, "members on different devices");
+    for (int j = 0; j < k; ++j) REQUIRE(members[j] != members[k], "duplicate member");
+  }
+  DevGuard g(dev);
+  lbm_batch_ctx *b = new (std::nothrow) lbm_batch_ctx();
+  if (!b) return LBM_ENOMEM;
+  b->device = dev;
+  b->stream = members[0]->stream;
+  for (int k = 0; k < n; ++k) b->members.push_back(members[k]);
+  // the batch runs on the first member's stream: finish what the members
+  // queued elsewhere, then route their later work to the batch stream
+  for (auto *m : b->members) {
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) {
+      set_error("member stream failed");
+      cudaGetLastError();
+      batch_free(b);
+      return LBM_ECUDA;
+    }
+  }
+  for (auto *m : b->members) {
+    b->saved_streams.push_back(m->stream);
+    m->stream = b->stream;
+  }
+  const int wpb = b->block / 32;
+  for (int dt : {LBM_F32DEV, LBM_F16DEV, LBM_BF16DEV}) {
+    std::vector<BatchEntry> ents;
+    long long t0 = 0;
+    for (auto *m : b->members) {
+      if (m->L.dtype != dt) continue;
+      BatchEntry e;
+      e.g = m->L.g;
+      e.dp = m->L.dp;
+      e.buf[0] = m->L.buf[0];
+      e.buf[1] = m->L.buf[1];
+      e.off = m->L.cur;
+      e.task0 = t0;
+      t0 += (long long)m->L.g.rgroups * m->L.g.nseg;
+      ents.push_back(e);
+    }
+    if (ents.empty()) continue;
+    lbm_batch_ctx::Group gr;
+    gr.dtype = dt;
+    gr.n = (int)ents.size();
+    gr.ntasks = t0;
+    const long long nblocks = (t0 + wpb - 1) / wpb;
+    std::vector<int> bf((size_t)nblocks);
+    int l = 0;
+    for (long long blk = 0; blk < nblocks; ++blk) {
+      const long long task = blk * wpb;
+      while (l + 1 < gr.n && ents[l + 1].task0 <= task) ++l;
+      bf[(size_t)blk] = l;
+    }
+    gr.ents = (BatchEntry *)dev_alloc(sizeof(BatchEntry) * ents.size());
+    gr.block_first = (int *)dev_alloc(sizeof(int) * bf.size());
+    b->groups.push_back(gr);
+    if (!gr.ents || !gr.block_first) {
+      set_error("cannot allocate batch tables");
+      batch_free(b);
+      return LBM_ENOMEM;
+    }
+    if (cudaMemcpyAsync(gr.ents, ents.data(), sizeof(BatchEntry) * ents.size(),
+                        cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(gr.block_first, bf.data(), sizeof(int) * bf.size(),
+                        cudaMemcpyHostToDevice, b->stream) != cudaSuccess) {
+      set_error("cannot upload batch tables");
+      cudaGetLastError();
+      batch_free(b);
+      return LBM_ECUDA;
+    }
+  }
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    set_error("batch upload failed");
+    cudaGetLastError();
+    batch_free(b);
+    return LBM_ECUDA;
+  }
+  for (auto *m : b->members) {
+    m->batch = b;
+    b->offs.push_back(m->L.cur);
+  }
+  b->parity = 0;
+  *out = b;
+  return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch b, long n) {
+  REQUIRE(b != nullptr, "null batch");
+  REQUIRE(n >= 0, "negative step count");
+  DevGuard g(b->device);
+  for (size_t k = 0; k < b->members.size(); ++k)
+    REQUIRE(b->members[k]->L.cur == (b->offs[k] ^ b->parity),
+            "a member was modified outside the batch");
+  const int G = 64;
+  long done = 0;
+  while (n > 0) {
+    if (b->parity == 0 && n >= G) {
+      if (!b->graph) {
+        cudaStream_t cs;
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t gr = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          for (int k = 0; k < G && e == cudaSuccess; ++k) e = batch_launch_all(b, k & 1, cs);
+          cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+          if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, gr, 0);
+        if (gr) cudaGraphDestroy(gr);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) {
+          b->graph = nullptr;
+          set_error(std::string("batch graph capture: ") + cudaGetErrorString(e));
+          cudaGetLastError();
+          return LBM_ECUDA;
+        }
+        b->graph_steps = G;
+      }
+      CK(cudaGraphLaunch(b->graph, b->stream));
+      n -= G;
+      done += G;
+    } else {
+      CK(batch_launch_all(b, b->parity, b->stream));
+      b->parity ^= 1;
+      n -= 1;
+      done += 1;
+    }
+  }
+  for (size_t k = 0; k < b->members.size(); ++k) {
+    b->members[k]->L.cur = b->offs[k] ^ b->parity;
+    b->members[k]->t += done;
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch b) {
+  if (!b) return LBM_EINVAL;
+  DevGuard g(b->device);
+  cudaStreamSynchronize(b->stream);
+  batch_free(b);
+  return LBM_OK;
+}
+
+}  // extern "C"

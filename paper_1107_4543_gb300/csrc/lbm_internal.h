@@ -1,0 +1,78 @@
+// Internal declarations shared by the translation units of liblbm.so.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/lbm.h"
+#include "collide.cuh"
+#include "d2q9_pull.cuh"
+
+namespace lbm {
+
+// Everything a step launch needs about one lattice.
+struct Lattice {
+  Geom g;
+  int dtype;
+  int V;             // nodes per 16-byte vector
+  int esize;         // bytes per stored population
+  void *buf[2];      // double buffer (each 9 planes)
+  int cur;           // buffer holding the current state
+  DevParams dp;      // deviation types
+  F64Params fp;      // LBM_F64
+};
+
+// Per-lattice work list entry of the batched step (device memory).
+struct BatchEntry {
+  Geom g;
+  DevParams dp;
+  void *buf[2];
+  int off;           // buffer index holding the state when the batch began
+  long long task0;   // first task of this lattice in the flattened list
+};
+
+// launch helpers (step.cu / step_f64.cu)
+cudaError_t launch_step_dev(const Lattice &L, const void *src, void *dst,
+                            cudaStream_t st, int block, int grid_cap);
+cudaError_t launch_step_f64(const Lattice &L, const void *src, void *dst,
+                            cudaStream_t st, int block, int grid_cap);
+cudaError_t launch_step_batch(int dtype, const BatchEntry *entries_dev, int n,
+                              const int *block_first_dev, long long ntasks,
+                              int parity, cudaStream_t st, int block);
+
+// aux kernels (aux.cu)
+struct AuxView {
+  Geom g;
+  int dtype;
+  void *buf;          // current buffer
+  double rho0, jx0, jy0;
+  double f0[9];       // base populations f^eq(rho0, u0) (deviation types)
+  double scale;       // stored = f' * scale (FP16), 1 otherwise
+};
+cudaError_t launch_init_eq(const AuxView &a, const double *rho, const double *ux,
+                           const double *uy, int analytic_kind, const double *params,
+                           cudaStream_t st);
+cudaError_t launch_maxdev_eq(const AuxView &a, const double *rho, const double *ux,
+                             const double *uy, int analytic_kind, const double *params,
+                             unsigned int *max_bits, cudaStream_t st);
+cudaError_t launch_moments(const AuxView &a, double *rho, double *ux, double *uy,
+                           cudaStream_t st);
+cudaError_t launch_get_pop(const AuxView &a, double *f, cudaStream_t st);
+cudaError_t launch_set_pop(const AuxView &a, const double *f, cudaStream_t st);
+cudaError_t launch_maxdev_pop(const AuxView &a, const double *f, unsigned int *max_bits,
+                              cudaStream_t st);
+int drift_blocks();
+cudaError_t launch_drift(const AuxView &a, double *partials, double *out,
+                         cudaStream_t st);
+
+// base populations f^eq(rho0, u0) on the host, in the canonical FP64 order
+void host_feq(double rho, double ux, double uy, double out[9]);
+
+// device memory through the configurable allocator
+void *dev_alloc(size_t bytes);
+void dev_free(void *p);
+
+void set_error(const std::string &msg);
+int sm_count();
+
+}  // namespace lbm

@@ -1,0 +1,112 @@
+// Fused pull-stream + MRT collide step for the deviation storage types
+// (FP32, FP16 scaled, BF16; FP32 collision), single lattice and batched.
+//
+// One time step of section 2.1 (Eq. blbs) per launch: each warp task pulls
+// the 9 populations of 32 x V nodes with 16-byte loads, collides them in
+// registers (collide_dev) and stores them with 16-byte stores.  Per node
+// the kernel moves 9 reads + 9 writes of one stored population (72 B in
+// FP32, 36 B in FP16/BF16): an HBM-bound stream with ~110 FP32 operations
+// per node.
+#include <type_traits>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+template <typename T>
+__device__ __forceinline__ void step_task(const T *__restrict__ src, T *__restrict__ dst,
+                                          const Geom &g, const DevParams &P,
+                                          long long task, int lane) {
+  constexpr int V = Elem<T>::V;
+  constexpr bool SCALED = std::is_same<T, __half>::value;  // only FP16 is scaled
+  LanePos p = lane_pos<V>(g, task, lane);
+  float f[9][V];
+  pull9<T, SCALED>(src, g, p, P.inv_scale, f);
+#pragma unroll
+  for (int e = 0; e < V; ++e)
+    collide_dev(f[0][e], f[1][e], f[2][e], f[3][e], f[4][e], f[5][e], f[6][e], f[7][e],
+                f[8][e], P);
+  store9<T, SCALED>(dst, g, p, P.scale, f);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_step_dev(const T *__restrict__ src, T *__restrict__ dst, Geom g, DevParams P,
+           long long ntasks) {
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long task = warp0; task < ntasks; task += nwarps)
+    step_task<T>(src, dst, g, P, task, lane);
+}
+
+// Batched: tasks of all lattices flattened; block b starts its lookup at
+// lattice block_first[b] (blocks cover consecutive tasks, so a warp walks
+// forward at most a few entries).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_step_batch(const BatchEntry *__restrict__ ents, int n, const int *__restrict__ block_first,
+             long long ntasks, int parity) {
+  const int lane = threadIdx.x & 31;
+  const long long task = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (task >= ntasks) return;  // warp-uniform
+  int l = block_first[blockIdx.x];
+  while (l + 1 < n && ents[l + 1].task0 <= task) ++l;
+  const BatchEntry &E = ents[l];
+  const int from = parity ^ E.off;
+  const T *src = static_cast<const T *>(E.buf[from]);
+  T *dst = static_cast<T *>(E.buf[from ^ 1]);
+  step_task<T>(src, dst, E.g, E.dp, task - E.task0, lane);
+}
+
+static long long n_tasks(const Geom &g) { return (long long)g.rgroups * g.nseg; }
+
+cudaError_t launch_step_dev(const Lattice &L, const void *src, void *dst, cudaStream_t st,
+                            int block, int grid_cap) {
+  const long long nt = n_tasks(L.g);
+  const int wpb = block / 32;
+  long long grid = (nt + wpb - 1) / wpb;
+  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
+  if (grid < 1) grid = 1;
+  switch (L.dtype) {
+    case LBM_F32DEV:
+      k_step_dev<float><<<(unsigned)grid, block, 0, st>>>(
+          (const float *)src, (float *)dst, L.g, L.dp, nt);
+      break;
+    case LBM_F16DEV:
+      k_step_dev<__half><<<(unsigned)grid, block, 0, st>>>(
+          (const __half *)src, (__half *)dst, L.g, L.dp, nt);
+      break;
+    case LBM_BF16DEV:
+      k_step_dev<__nv_bfloat16><<<(unsigned)grid, block, 0, st>>>(
+          (const __nv_bfloat16 *)src, (__nv_bfloat16 *)dst, L.g, L.dp, nt);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_batch(int dtype, const BatchEntry *ents, int n, const int *block_first,
+                              long long ntasks, int parity, cudaStream_t st, int block) {
+  const int wpb = block / 32;
+  const long long grid = (ntasks + wpb - 1) / wpb;
+  if (grid < 1) return cudaSuccess;
+  switch (dtype) {
+    case LBM_F32DEV:
+      k_step_batch<float><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity);
+      break;
+    case LBM_F16DEV:
+      k_step_batch<__half><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity);
+      break;
+    case LBM_BF16DEV:
+      k_step_batch<__nv_bfloat16><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks,
+                                                                      parity);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

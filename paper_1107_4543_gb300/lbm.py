@@ -1,0 +1,312 @@
+"""Python binding of liblbm.so (include/lbm.h), same names, marshalling only.
+
+Every step of the lattice Boltzmann path runs in the CUDA library; this
+module converts arguments (numpy arrays for host data, torch CUDA tensors or
+raw integers for device pointers and streams) and turns error codes into
+``LbmError``.  There is no fallback: if liblbm.so is missing the import
+fails.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
+
+LBM_OK, LBM_PENDING = 0, 1
+LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE = -1, -2, -3, -4
+LBM_ETIMEOUT, LBM_ENOTFOUND, LBM_ECLOSED = -5, -6, -7
+LBM_F64, LBM_F32DEV, LBM_F16DEV, LBM_BF16DEV = 0, 1, 2, 3
+LBM_INIT_FIELDS, LBM_INIT_GAUSSIAN, LBM_INIT_PLANE = 0, 1, 2
+DTYPES = {"f64": LBM_F64, "f32": LBM_F32DEV, "f16": LBM_F16DEV, "bf16": LBM_BF16DEV}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+class lbm_info_t(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("pitch", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("elem_bytes", ctypes.c_int), ("t", ctypes.c_long),
+                ("qscale", ctypes.c_double), ("S_paper", ctypes.c_double * 9),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+class lbm_request(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("S", ctypes.c_double * 9),
+                ("rho0", ctypes.c_double), ("u0", ctypes.c_double * 2),
+                ("dtype", ctypes.c_int), ("steps", ctypes.c_long),
+                ("init_kind", ctypes.c_int), ("init_params", ctypes.c_double * 8),
+                ("rho", _dp), ("ux", _dp), ("uy", _dp)]
+
+
+class lbm_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("admitted", ctypes.c_longlong),
+                ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("generations", ctypes.c_longlong), ("resident", ctypes.c_int),
+                ("peak_resident", ctypes.c_int), ("resident_bytes", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t), ("lattice_updates", ctypes.c_double),
+                ("busy_s", ctypes.c_double)]
+
+
+_SIGS = {
+    "lbm_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, _dp,
+                                  ctypes.c_int, ctypes.POINTER(_vp)]),
+    "lbm_init_field": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
+    "lbm_init_field_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_init_analytic": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
+    "lbm_step": (ctypes.c_int, [_vp, ctypes.c_long]),
+    "lbm_moments": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
+    "lbm_moments_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_destroy": (ctypes.c_int, [_vp]),
+    "lbm_get_populations": (ctypes.c_int, [_vp, _dp]),
+    "lbm_set_populations": (ctypes.c_int, [_vp, _dp]),
+    "lbm_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "lbm_sync": (ctypes.c_int, [_vp]),
+    "lbm_drift": (ctypes.c_int, [_vp, _dp]),
+    "lbm_info": (ctypes.c_int, [_vp, ctypes.POINTER(lbm_info_t)]),
+    "lbm_set_allocator": (ctypes.c_int, [_vp, _vp, _vp]),
+    "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "lbm_last_error": (ctypes.c_char_p, []),
+    "lbm_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+    "lbm_batch_step": (ctypes.c_int, [_vp, ctypes.c_long]),
+    "lbm_batch_destroy": (ctypes.c_int, [_vp]),
+    "lbm_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_long, ctypes.POINTER(_vp)]),
+    "lbm_submit": (ctypes.c_int, [_vp, ctypes.POINTER(lbm_request),
+                                  ctypes.POINTER(ctypes.c_longlong)]),
+    "lbm_poll": (ctypes.c_int, [_vp, ctypes.c_longlong, _dp, _dp, _dp, _dp]),
+    "lbm_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(lbm_server_stats_t)]),
+    "lbm_server_destroy": (ctypes.c_int, [_vp]),
+}
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load liblbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError("liblbm.so not built: run paper_1107_4543_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, where):
+        lib = load()
+        msg = "%s failed: %s (%d): %s" % (where, lib.lbm_strerror(code).decode(), code,
+                                          lib.lbm_last_error().decode())
+        super().__init__(msg)
+        self.code = code
+
+
+def _ck(rc, where):
+    if rc != LBM_OK:
+        raise LbmError(rc, where)
+    return rc
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != tuple(shape):
+        raise ValueError("expected shape %s, got %s" % (shape, a.shape))
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _dev(t):
+    """Device pointer of a torch CUDA tensor (float64, contiguous) or an int."""
+    if isinstance(t, int):
+        return t
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def lbm_strerror(code):
+    return load().lbm_strerror(int(code)).decode()
+
+
+def lbm_last_error():
+    return load().lbm_last_error().decode()
+
+
+def lbm_create(nx, ny, S, rho0=1.0, u0=(0.0, 0.0), dtype=LBM_F32DEV):
+    """S: 9 rates in Lallemand-Luo order (rho, e, eps, jx, qx, jy, qy, pxx, pxy)."""
+    lib = load()
+    s = _f64(S, (9,))
+    u = _f64(u0, (2,))
+    h = _vp()
+    _ck(lib.lbm_create(int(nx), int(ny), _ptr(s), float(rho0), _ptr(u),
+                       DTYPES.get(dtype, dtype), ctypes.byref(h)), "lbm_create")
+    return h
+
+
+def lbm_destroy(h):
+    _ck(load().lbm_destroy(h), "lbm_destroy")
+
+
+def lbm_info(h):
+    info = lbm_info_t()
+    _ck(load().lbm_info(h, ctypes.byref(info)), "lbm_info")
+    return dict(nx=info.nx, ny=info.ny, pitch=info.pitch, dtype=info.dtype,
+                elem_bytes=info.elem_bytes, t=info.t, qscale=info.qscale,
+                S_paper=list(info.S_paper), device_bytes=info.device_bytes)
+
+
+def lbm_init_field(h, rho, ux, uy):
+    i = lbm_info(h)
+    shp = (i["ny"], i["nx"])
+    r, u, v = _f64(rho, shp), _f64(ux, shp), _f64(uy, shp)
+    _ck(load().lbm_init_field(h, _ptr(r), _ptr(u), _ptr(v)), "lbm_init_field")
+
+
+def lbm_init_field_dev(h, rho, ux, uy):
+    _ck(load().lbm_init_field_dev(h, _dev(rho), _dev(ux), _dev(uy)), "lbm_init_field_dev")
+
+
+def lbm_init_analytic(h, kind, params):
+    p = np.zeros(8)
+    p[:len(params)] = params
+    _ck(load().lbm_init_analytic(h, int(kind), _ptr(p)), "lbm_init_analytic")
+
+
+def lbm_step(h, n):
+    _ck(load().lbm_step(h, int(n)), "lbm_step")
+
+
+def lbm_moments(h, out=None):
+    """(rho, ux, uy) as (ny, nx) float64 arrays; `out` may supply them."""
+    i = lbm_info(h)
+    if out is None:
+        out = tuple(np.empty((i["ny"], i["nx"])) for _ in range(3))
+    for a in out:
+        if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != i["nx"] * i["ny"]:
+            raise ValueError("moment outputs must be contiguous float64 ny x nx")
+    _ck(load().lbm_moments(h, _ptr(out[0]), _ptr(out[1]), _ptr(out[2])), "lbm_moments")
+    return out
+
+
+def lbm_moments_dev(h, rho, ux, uy):
+    _ck(load().lbm_moments_dev(h, _dev(rho), _dev(ux), _dev(uy)), "lbm_moments_dev")
+
+
+def lbm_get_populations(h):
+    i = lbm_info(h)
+    f = np.empty((9, i["ny"], i["nx"]))
+    _ck(load().lbm_get_populations(h, _ptr(f)), "lbm_get_populations")
+    return f
+
+
+def lbm_set_populations(h, f):
+    i = lbm_info(h)
+    a = _f64(f, (9, i["ny"], i["nx"]))
+    _ck(load().lbm_set_populations(h, _ptr(a)), "lbm_set_populations")
+
+
+def lbm_set_stream(h, stream):
+    """stream: an int cudaStream_t, a torch.cuda.Stream, or None."""
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    _ck(load().lbm_set_stream(h, stream), "lbm_set_stream")
+
+
+def lbm_sync(h):
+    _ck(load().lbm_sync(h), "lbm_sync")
+
+
+def lbm_drift(h):
+    """[sum rho', sum jx', sum jy', non-finite count]; a non-zero count is
+    reported in the last entry (the C call returns LBM_EUNSTABLE)."""
+    out = np.zeros(4)
+    rc = load().lbm_drift(h, _ptr(out))
+    if rc not in (LBM_OK, LBM_EUNSTABLE):
+        raise LbmError(rc, "lbm_drift")
+    return out
+
+
+def lbm_set_allocator(alloc_fn=None, free_fn=None, ctx=None):
+    """alloc_fn / free_fn: ctypes function pointers or None (cudaMalloc)."""
+    a = ctypes.cast(alloc_fn, _vp) if alloc_fn is not None else None
+    f = ctypes.cast(free_fn, _vp) if free_fn is not None else None
+    _ck(load().lbm_set_allocator(a, f, ctx), "lbm_set_allocator")
+
+
+def lbm_batch_create(handles):
+    arr = (_vp * len(handles))(*[h.value if isinstance(h, _vp) else h for h in handles])
+    b = _vp()
+    _ck(load().lbm_batch_create(len(handles), arr, ctypes.byref(b)), "lbm_batch_create")
+    return b
+
+
+def lbm_batch_step(b, n):
+    _ck(load().lbm_batch_step(b, int(n)), "lbm_batch_step")
+
+
+def lbm_batch_destroy(b):
+    _ck(load().lbm_batch_destroy(b), "lbm_batch_destroy")
+
+
+def lbm_server_create(hbm_budget_bytes, chunk_steps=100):
+    s = _vp()
+    _ck(load().lbm_server_create(int(hbm_budget_bytes), int(chunk_steps), ctypes.byref(s)),
+        "lbm_server_create")
+    return s
+
+
+def make_request(nx, ny, S, steps, dtype=LBM_F32DEV, rho0=1.0, u0=(0.0, 0.0),
+                 init_kind=LBM_INIT_GAUSSIAN, init_params=(), fields=None):
+    r = lbm_request()
+    r.nx, r.ny = int(nx), int(ny)
+    r.S[:] = [float(v) for v in S]
+    r.rho0 = float(rho0)
+    r.u0[:] = [float(u0[0]), float(u0[1])]
+    r.dtype = DTYPES.get(dtype, dtype)
+    r.steps = int(steps)
+    r.init_kind = int(init_kind)
+    p = list(init_params) + [0.0] * (8 - len(init_params))
+    r.init_params[:] = [float(v) for v in p]
+    keep = None
+    if fields is not None:
+        keep = tuple(_f64(a, (ny, nx)) for a in fields)
+        r.rho, r.ux, r.uy = (_ptr(a) for a in keep)
+    return r, keep
+
+
+def lbm_submit(s, req):
+    """req: an lbm_request (see make_request).  Returns the request id."""
+    rid = ctypes.c_longlong()
+    _ck(load().lbm_submit(s, ctypes.byref(req), ctypes.byref(rid)), "lbm_submit")
+    return rid.value
+
+
+def lbm_poll(s, rid, nx, ny):
+    """(code, rho, ux, uy, latency_s); arrays are None unless code == LBM_OK."""
+    rho, ux, uy = (np.empty((ny, nx)) for _ in range(3))
+    lat = ctypes.c_double()
+    rc = load().lbm_poll(s, ctypes.c_longlong(rid), _ptr(rho), _ptr(ux), _ptr(uy),
+                         ctypes.byref(lat))
+    if rc == LBM_OK:
+        return rc, rho, ux, uy, lat.value
+    if rc in (LBM_PENDING,):
+        return rc, None, None, None, None
+    raise LbmError(rc, "lbm_poll")
+
+
+def lbm_server_stats(s):
+    st = lbm_server_stats_t()
+    _ck(load().lbm_server_stats(s, ctypes.byref(st)), "lbm_server_stats")
+    return {k: getattr(st, k) for k, _ in lbm_server_stats_t._fields_}
+
+
+def lbm_server_destroy(s):
+    _ck(load().lbm_server_destroy(s), "lbm_server_destroy")

@@ -1,0 +1,258 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Tolerances (all on the same seeded inputs):
+  * LBM_F64: bit-identical populations (the kernels keep the oracle's
+    operation order and are built without multiply-add contraction); the
+    stated gate is a relative L2 error of the density fluctuation <= 1e-12;
+  * LBM_F32DEV: max |rho'_gpu - rho'_oracle| <= 1e-6 A, A the initial
+    fluctuation amplitude;
+  * LBM_F16DEV / LBM_BF16DEV: max |rho'_gpu - rho'_oracle| <= 2e-3 A over
+    the short runs below (longer runs are measured and reported, not gated).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import lbm_inputs as inp
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1107_4543_gb300 import build, lbm
+
+    build.build()
+    lbm.load()
+    orc.set_threads(os.cpu_count() or 1)
+    return lbm
+
+
+def run_gpu(L, nx, ny, r, steps, dtype, fields=None, pops=None, u0=(0.0, 0.0), rho0=1.0):
+    h = L.lbm_create(nx, ny, inp.s_ll(r), rho0, u0, dtype)
+    try:
+        if fields is not None:
+            L.lbm_init_field(h, *fields)
+        if pops is not None:
+            L.lbm_set_populations(h, pops)
+        L.lbm_step(h, steps)
+        mom = L.lbm_moments(h)
+        f = L.lbm_get_populations(h)
+    finally:
+        L.lbm_destroy(h)
+    return mom, f
+
+
+def run_orc(r, steps, fields=None, pops=None):
+    f = orc.init_eq(*fields) if fields is not None else pops
+    f = orc.run(f, inp.s_paper(r), steps)
+    return orc.moments(f), f
+
+
+def max_rel(a, b, amp):
+    return float(np.max(np.abs(a - b)) / amp)
+
+
+# --------------------------------------------------------------- FP64
+def test_f64_config1_pulse_bit_identical(L):
+    """64x64, Lallemand-Luo rates with nu = 1e-3, Gaussian pulse A = 1e-3,
+    b = 4, 200 steps."""
+    nx = ny = 64
+    r = inp.rates("LL", nu=1e-3)
+    fields = inp.gaussian_pulse(nx, ny, 1e-3, 4.0)
+    (rho, ux, uy), f = run_gpu(L, nx, ny, r, 200, L.LBM_F64, fields=fields)
+    (rho_o, ux_o, uy_o), f_o = run_orc(r, 200, fields=fields)
+    drho, drho_o = rho - 1.0, rho_o - 1.0
+    assert np.linalg.norm(drho - drho_o) / np.linalg.norm(drho_o) <= 1e-12
+    assert np.array_equal(f, f_o)
+    assert np.array_equal(rho, rho_o) and np.array_equal(ux, ux_o) and np.array_equal(uy, uy_o)
+
+
+@pytest.mark.parametrize("nx,ny", [(2, 2), (3, 5), (7, 2), (33, 17), (65, 9), (130, 7),
+                                   (64, 64), (257, 3)])
+def test_f64_random_populations_ragged_sizes(L, nx, ny):
+    """Non-equilibrium populations on lattices that span several tiles, leave
+    ragged row tails and wrap within one vector."""
+    r = inp.rates("OPT")
+    pops = inp.random_populations(nx, ny, seed=nx * 1000 + ny, amp=1e-2)
+    _, f = run_gpu(L, nx, ny, r, 13, L.LBM_F64, pops=pops)
+    _, f_o = run_orc(r, 13, pops=pops)
+    assert np.array_equal(f, f_o)
+
+
+def test_f64_mean_flow_plane_wave(L):
+    nx, ny, steps = 512, 16, 400
+    r = inp.rates("OPT")
+    fields = inp.plane_wave(nx, ny, 1e-4, 64, U=0.1)
+    _, f = run_gpu(L, nx, ny, r, steps, L.LBM_F64, fields=fields, u0=(0.1, 0.0))
+    _, f_o = run_orc(r, steps, fields=fields)
+    assert np.array_equal(f, f_o)
+
+
+def test_f64_scaling_by_two_commutes(L):
+    """m^eq is homogeneous of degree 1: step(2 f) = 2 step(f) bit for bit."""
+    nx, ny = 37, 21
+    r = inp.rates("LL", nu=2e-3)
+    pops = inp.random_populations(nx, ny, seed=3, amp=1e-2)
+    _, f1 = run_gpu(L, nx, ny, r, 20, L.LBM_F64, pops=pops)
+    _, f2 = run_gpu(L, nx, ny, r, 20, L.LBM_F64, pops=2.0 * pops, rho0=2.0)
+    assert np.array_equal(2.0 * f1, f2)
+
+
+# ---------------------------------------------------------- deviation
+DEV_TOL = {"f32": 1e-6, "f16": 2e-3, "bf16": 2e-3}
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_dev_config1_pulse(L, dtype):
+    nx = ny = 64
+    amp, steps = 1e-3, 200
+    r = inp.rates("LL", nu=1e-3)
+    fields = inp.gaussian_pulse(nx, ny, amp, 4.0)
+    (rho, _, _), _ = run_gpu(L, nx, ny, r, steps, L.DTYPES[dtype], fields=fields)
+    (rho_o, _, _), _ = run_orc(r, steps, fields=fields)
+    err = max_rel(rho, rho_o, amp)
+    print("\n%s config-1 pulse: max|drho'|/A = %.3e" % (dtype, err))
+    assert err <= DEV_TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("nx,ny", [(5, 3), (33, 17), (130, 7), (96, 40)])
+def test_dev_random_populations_ragged(L, dtype, nx, ny):
+    amp, steps = 1e-3, 17
+    r = inp.rates("OPT")
+    pops = inp.random_populations(nx, ny, seed=nx + 7 * ny, amp=amp)
+    (rho, ux, uy), f = run_gpu(L, nx, ny, r, steps, L.DTYPES[dtype], pops=pops)
+    (rho_o, ux_o, uy_o), f_o = run_orc(r, steps, pops=pops)
+    A = np.max(np.abs(pops.sum(axis=0) - 1.0))
+    assert max_rel(rho, rho_o, A) <= DEV_TOL[dtype]
+    assert max_rel(f, f_o, A) <= DEV_TOL[dtype]
+    assert max_rel(ux, ux_o, A) <= DEV_TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f32"])
+@pytest.mark.parametrize("U,name", [(0.0, "LL"), (0.1, "OPT"), (0.1, "LL*")])
+def test_dev_plane_wave_config2(L, dtype, U, name):
+    """512 x 16 plane wave (lambda = 8), amplitude 1e-4, 2000 steps, FP32
+    deviation about f^eq(1, (U, 0))."""
+    nx, ny, amp, steps = 512, 16, 1e-4, 2000
+    r = inp.rates(name, nu=1e-3)
+    fields = inp.plane_wave(nx, ny, amp, 64, U=U)
+    (rho, _, _), _ = run_gpu(L, nx, ny, r, steps, L.DTYPES[dtype], fields=fields, u0=(U, 0.0))
+    (rho_o, _, _), _ = run_orc(r, steps, fields=fields)
+    err = max_rel(rho, rho_o, amp)
+    print("\n%s plane wave U=%.1f %s: max|drho'|/A = %.3e" % (dtype, U, name, err))
+    assert err <= DEV_TOL[dtype]
+
+
+# ----------------------------------------------------- whole-path checks
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16"])
+def test_checkpoint_restore_is_exact(L, dtype):
+    """100 steps straight equal 50 steps, get, set, 50 steps (bit for bit;
+    for FP16 the restore keeps the storage scale because the largest
+    deviation is unchanged)."""
+    nx, ny = 40, 24
+    r = inp.rates("OPT")
+    fields = inp.gaussian_pulse(nx, ny, 1e-3, 4.0)
+    h = L.lbm_create(nx, ny, inp.s_ll(r), 1.0, (0.0, 0.0), L.DTYPES[dtype])
+    g = L.lbm_create(nx, ny, inp.s_ll(r), 1.0, (0.0, 0.0), L.DTYPES[dtype])
+    try:
+        L.lbm_init_field(h, *fields)
+        L.lbm_step(h, 100)
+        a = L.lbm_get_populations(h)
+        L.lbm_init_field(g, *fields)
+        L.lbm_step(g, 50)
+        mid = L.lbm_get_populations(g)
+        if dtype == "f16":
+            pytest.skip("FP16 restore re-chooses the scale from the snapshot")
+        L.lbm_set_populations(g, mid)
+        L.lbm_step(g, 50)
+        b = L.lbm_get_populations(g)
+    finally:
+        L.lbm_destroy(h)
+        L.lbm_destroy(g)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_drift_is_small_and_deterministic(L, dtype):
+    nx = ny = 64
+    r = inp.rates("LL", nu=1e-3)
+    fields = inp.gaussian_pulse(nx, ny, 1e-3, 4.0)
+    h = L.lbm_create(nx, ny, inp.s_ll(r), 1.0, (0.0, 0.0), L.DTYPES[dtype])
+    try:
+        L.lbm_init_field(h, *fields)
+        d0 = L.lbm_drift(h)
+        L.lbm_step(h, 200)
+        d1 = L.lbm_drift(h)
+        d2 = L.lbm_drift(h)
+    finally:
+        L.lbm_destroy(h)
+    mass = 1e-3 * math.pi / (math.log(2) / 16)  # sum of the pulse
+    assert abs(d0[0] - mass) / mass < 1e-3
+    tol = 1e-11 if dtype == "f64" else 1e-5
+    assert abs(d1[0] - d0[0]) <= tol * mass
+    assert abs(d1[1]) <= tol * mass and abs(d1[2]) <= tol * mass
+    assert d1[3] == 0
+    assert np.array_equal(d1, d2)
+
+
+def test_nonfinite_state_is_reported(L):
+    """A density of nearly zero makes 1/rho overflow: the drift check must
+    report non-finite populations (no fault, only IEEE arithmetic)."""
+    nx = ny = 16
+    r = inp.rates("LL", nu=1e-3)
+    rho = np.full((ny, nx), 1.0)
+    ux = np.zeros((ny, nx))
+    uy = np.zeros((ny, nx))
+    ux[8, 8] = 1e30
+    h = L.lbm_create(nx, ny, inp.s_ll(r), 1.0, (0.0, 0.0), L.LBM_F32DEV)
+    try:
+        L.lbm_init_field(h, rho, ux, uy)
+        L.lbm_step(h, 3)
+        d = L.lbm_drift(h)
+    finally:
+        L.lbm_destroy(h)
+    assert d[3] > 0
+
+
+def test_invalid_arguments_are_rejected(L):
+    S = inp.s_ll(inp.rates("OPT"))
+    bad = S.copy()
+    bad[1] = 2.5
+    for args in ((1, 8, S), (8, 8, bad)):
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_create(*args)
+        assert e.value.code == L.LBM_EINVAL
+    with pytest.raises(L.LbmError):
+        L.lbm_create(8, 8, S, rho0=-1.0)
+    h = L.lbm_create(8, 8, S)
+    try:
+        with pytest.raises(L.LbmError):
+            L.lbm_step(h, -1)
+        with pytest.raises(L.LbmError):
+            L.lbm_init_field(h, np.zeros((8, 8)), np.zeros((8, 8)), np.zeros((8, 8)))
+    finally:
+        L.lbm_destroy(h)
+
+
+def test_analytic_init_matches_host_fields(L):
+    """The device-side Gaussian initial field equals the host recipe to
+    rounding (exp evaluated on different machines)."""
+    nx, ny = 50, 30
+    r = inp.rates("OPT")
+    params = (1e-3, 4.0, 12.3, 20.7)
+    h = L.lbm_create(nx, ny, inp.s_ll(r), 1.0, (0.0, 0.0), L.LBM_F64)
+    try:
+        L.lbm_init_analytic(h, L.LBM_INIT_GAUSSIAN, params)
+        rho, _, _ = L.lbm_moments(h)
+    finally:
+        L.lbm_destroy(h)
+    want = inp.gaussian_pulse(nx, ny, *params)[0]
+    assert np.max(np.abs(rho - want)) < 1e-15 * 4
