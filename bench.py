@@ -1,0 +1,488 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the D2Q9 MRT lattice Boltzmann library on GB300.
+
+Default workload (one JSON line): 512 independent periodic lattices, areas
+log-uniform in [32^2, 1024^2] (7.7e7 nodes), per-lattice relaxation rates,
+Gaussian pulses, FP32 deviation storage.  One benchmark step = the whole
+batch advanced 500 time steps (500 batched fused step launches replayed from
+CUDA graphs) followed by the FP64 drift check of every lattice.
+
+  value      MLUPS with the populations resident in HBM
+  e2e        MLUPS through the C ABI with host buffers: every step uploads
+             the initial fields (rho, ux, uy) from pinned host memory,
+             steps, and downloads rho, ux, uy
+  roofline   the batched step kernel: algorithmic 72 B per lattice update
+             over its average launch time against the measured HBM copy
+             bandwidth
+  fp64_plain the plain FP64 path on one 8192^2 lattice, for comparison
+  cpu_baseline  the FP64 CPU oracle on a bounded sample of the workload
+
+Other workloads: --workload large (one 8192^2 lattice, per storage type)
+and --workload serving (Poisson request stream through lbm_submit/poll).
+--impl reference times the CPU oracle on the same metric.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lbm_inputs as inp  # noqa: E402
+
+BYTES_PER_LU = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}
+KERNEL_SOURCES = ["csrc/step.cu", "csrc/d2q9_pull.cuh", "csrc/collide.cuh", "csrc/step_f64.cu"]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="batched", choices=["batched", "large", "serving"])
+    p.add_argument("--lattices", type=int, default=512)
+    p.add_argument("--lbm-steps", type=int, default=500)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--requests", type=int, default=10000)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------ environment
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def traffic_record(kernel):
+    """DRAM bytes per lattice update from the committed ncu summary, or None
+    when the kernel sources changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_sha") != sources_sha():
+        return None
+    return rec
+
+
+def sources_sha():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1107_4543_gb300", rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# -------------------------------------------------------------- CPU oracle
+def cpu_oracle_mlups(specs, target_s=12.0, threads=None):
+    """The FP64 oracle (as it stands) on a bounded sample of the workload:
+    the first lattices of the list, stepped until about target_s seconds of
+    CPU work.  Returns (MLUPS, cores, sample description)."""
+    import oracle as orc
+
+    threads = threads or os.cpu_count() or 1
+    orc.set_threads(threads)
+    nodes = steps_done = 0
+    t_total = 0.0
+    used = []
+    for spec in specs:
+        rho, ux, uy = inp.batch_fields(spec) if "b" in spec else spec["fields"]
+        f = orc.init_eq(rho, ux, uy)
+        s = inp.s_paper(spec["rates"])
+        t0 = time.perf_counter()
+        f = orc.run(f, s, 2)
+        dt = time.perf_counter() - t0
+        n = spec["nx"] * spec["ny"]
+        steps = max(2, int(min(50, (target_s / 4) / max(dt / 2, 1e-9))))
+        t0 = time.perf_counter()
+        orc.run(f, s, steps)
+        dt = time.perf_counter() - t0
+        nodes += n * steps
+        t_total += dt
+        steps_done += steps
+        used.append("%dx%d x%d" % (spec["nx"], spec["ny"], steps))
+        if t_total >= target_s or len(used) >= 6:
+            break
+    return nodes / t_total / 1e6, threads, "; ".join(used)
+
+
+# ------------------------------------------------------------- GPU workloads
+def setup_batch(L, torch, specs, dtype, stream):
+    hs = []
+    fields = []
+    for spec in specs:
+        h = L.lbm_create(spec["nx"], spec["ny"], inp.s_ll(spec["rates"]), 1.0, (0.0, 0.0),
+                         L.DTYPES[dtype])
+        L.lbm_set_stream(h, stream)
+        rho, ux, uy = inp.batch_fields(spec)
+        pinned = []
+        for a in (rho, ux, uy):
+            t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+            t.numpy()[...] = a
+            pinned.append(t.numpy())
+        L.lbm_init_field(h, *pinned)
+        hs.append(h)
+        fields.append(pinned)
+    return hs, fields
+
+
+def fp64_plain(L, torch, stream, n=8192, steps=20):
+    """Plain FP64 path on one n x n lattice (pulse + vortices), MLUPS."""
+    r = inp.rates("OPT")
+    h = L.lbm_create(n, n, inp.s_ll(r), 1.0, (0.0, 0.0), L.LBM_F64)
+    try:
+        L.lbm_set_stream(h, stream)
+        L.lbm_init_analytic(h, L.LBM_INIT_GAUSSIAN, (1e-3, 20.0, n / 2, n / 2))
+        L.lbm_step(h, 4)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        L.lbm_step(h, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    finally:
+        L.lbm_destroy(h)
+    return n * n * steps / (ms * 1e-3) / 1e6, ms / steps
+
+
+def bench_batched(args, L, torch, rank, ws):
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    specs = inp.batch_specs(args.lattices, seed=1107 + 4 + 1000 * rank, steps=args.lbm_steps)
+    hs, fields = setup_batch(L, torch, specs, "f32", stream)
+    nodes = sum(s["nx"] * s["ny"] for s in specs)
+    b = L.lbm_batch_create(hs)
+    lbm_steps = args.lbm_steps
+
+    def one_step():
+        L.lbm_batch_step(b, lbm_steps)
+        for h in hs:
+            L.lbm_drift(h)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(dev)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 2)]
+    ev[0].record()
+    for k in range(args.steps):
+        ev[2 * k + 1].record()
+        L.lbm_batch_step(b, lbm_steps)
+        ev[2 * k + 2].record()
+        for h in hs:
+            L.lbm_drift(h)
+    ev[-1].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = ev[0].elapsed_time(ev[-1])
+    step_ms = [ev[2 * k + 1].elapsed_time(ev[2 * k + 2]) for k in range(args.steps)]
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    lu_per_step = nodes * lbm_steps
+    value = ws * lu_per_step * args.steps / (total_ms * 1e-3) / 1e6
+    launch_ms = float(np.mean(step_ms)) / lbm_steps  # one batched kernel per time step
+    launches = args.steps * (lbm_steps + 2 * len(hs))
+
+    # e2e: host fields in, moments out, through the public API
+    outs = []
+    for spec in specs:
+        o = []
+        for _ in range(3):
+            t = torch.empty((spec["ny"], spec["nx"]), dtype=torch.float64, pin_memory=True)
+            o.append(t.numpy())
+        outs.append(o)
+    L.lbm_batch_destroy(b)
+
+    def e2e_step():
+        for h, f in zip(hs, fields):
+            L.lbm_init_field(h, *f)
+        bb = L.lbm_batch_create(hs)
+        L.lbm_batch_step(bb, lbm_steps)
+        for h in hs:
+            L.lbm_drift(h)
+        L.lbm_batch_destroy(bb)
+        for h, o in zip(hs, outs):
+            L.lbm_moments(h, out=o)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = ws * lu_per_step * args.steps / e2e_s / 1e6
+    h2d = 3 * 8 * nodes
+    d2h = 3 * 8 * nodes
+
+    fp64 = None
+    if not args.no_fp64:
+        mlups64, ms64 = fp64_plain(L, torch, stream)
+        fp64 = {"workload": "single 8192x8192 lattice, plain FP64 full populations",
+                "mlups": round(mlups64, 1), "ms_per_lbm_step": round(ms64, 3)}
+    for h in hs:
+        L.lbm_destroy(h)
+
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_LU["f32"] * nodes / (launch_ms * 1e-3) / 1e9
+    tr = traffic_record("k_step_batch<float>")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": (round(tr["dram_bytes_per_lu"] * nodes) if tr else None),
+                "kernel": "k_step_batch<float>", "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": BYTES_PER_LU["f32"] * nodes,
+                "avg_launch_ms": round(launch_ms, 4)}
+    line = {
+        "metric": "MLUPS (lattice updates/s, millions), batched FP32-deviation D2Q9 MRT",
+        "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Gaussian pulses, per-lattice relaxation rates)",
+        "config": {"workload": "batched-512-lattices-fp32dev-500-steps",
+                   "lattices_per_gpu": len(specs), "nodes_per_gpu": nodes,
+                   "lbm_steps_per_step": lbm_steps, "storage": "fp32 deviation",
+                   "l2": "working set %.1f GB per time step > L2 (129 MB)" % (
+                       2 * 72 / 2 * nodes / 1e9),
+                   "parallelism": "independent lattices per GPU (weak scaling)"},
+        "e2e": {"value": round(e2e_value, 1), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "roofline": roofline,
+        "fp64_plain": fp64,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    return line, specs
+
+
+def bench_large(args, L, torch, rank, ws):
+    """One 8192^2 lattice per storage type; prints one line per type."""
+    stream = torch.cuda.current_stream()
+    n = 8192
+    r = inp.rates("OPT")
+    lines = []
+    peak, peak_kind = peaks()
+    for dtype in ("f32", "f16", "bf16", "f64"):
+        h = L.lbm_create(n, n, inp.s_ll(r), 1.0, (0.0, 0.0), L.DTYPES[dtype])
+        L.lbm_set_stream(h, stream)
+        L.lbm_init_analytic(h, L.LBM_INIT_GAUSSIAN, (1e-3, 20.0, n / 2, n / 2))
+        lbm_steps = 50 if dtype != "f64" else 10
+        for _ in range(args.warmup):
+            L.lbm_step(h, lbm_steps)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            L.lbm_step(h, lbm_steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        L.lbm_destroy(h)
+        lu = n * n * lbm_steps * args.steps
+        launch_ms = ms / (lbm_steps * args.steps)
+        achieved = BYTES_PER_LU[dtype] * n * n / (launch_ms * 1e-3) / 1e9
+        lines.append({"metric": "MLUPS, single 8192x8192 lattice", "value": round(lu / ms / 1e3, 1),
+                      "unit": "MLUPS", "dtype": dtype, "n_gpus": ws, "steps": args.steps,
+                      "warmup": args.warmup, "higher_is_better": True,
+                      "config": {"workload": "single-8192x8192-%s" % dtype},
+                      "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                                   "unit": "GB/s", "frac": round(achieved / peak, 4),
+                                   "peak_source": peak_kind}})
+    return lines
+
+
+def bench_serving(args, L, torch):
+    """Poisson request stream through lbm_submit / lbm_poll."""
+    reqs = inp.request_stream(args.requests, seed=1107 + 5)
+    srv = L.lbm_server_create(150 * 10**9, 100)
+    ids = {}
+    t0 = time.perf_counter()
+    k = 0
+    pending = {}
+    lat = []
+    while k < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while k < len(reqs) and reqs[k]["arrival"] <= now:
+            q = reqs[k]
+            init = q["init"]
+            if init["kind"] == "gaussian":
+                kind, params = L.LBM_INIT_GAUSSIAN, (init["amp"], init["b"], init["xc"], init["yc"])
+            else:
+                kind, params = L.LBM_INIT_PLANE, (init["amp"], init["m"])
+            req, _ = L.make_request(q["nx"], q["ny"], inp.s_ll(q["rates"]), q["steps"],
+                                    dtype=q["dtype"], init_kind=kind, init_params=params)
+            pending[L.lbm_submit(srv, req)] = q
+            k += 1
+        done = []
+        for rid, q in pending.items():
+            rc, _, _, _, latency = L.lbm_poll(srv, rid, q["nx"], q["ny"])
+            if rc == L.LBM_OK:
+                lat.append(latency)
+                done.append(rid)
+        for rid in done:
+            del pending[rid]
+        time.sleep(0.002)
+    wall = time.perf_counter() - t0
+    st = L.lbm_server_stats(srv)
+    L.lbm_server_destroy(srv)
+    lu = sum(q["nx"] * q["ny"] * q["steps"] for q in reqs)
+    return {"metric": "served MLUPS and solve latency", "value": round(lu / wall / 1e6, 1),
+            "unit": "MLUPS", "higher_is_better": True,
+            "config": {"workload": "serving-poisson-%d-requests" % len(reqs)},
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "server": st}
+
+
+def reference_arm(args):
+    """The CPU oracle timed as the reference implementation."""
+    specs = inp.batch_specs(args.lattices, seed=1107 + 4, steps=args.lbm_steps)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        mlups, cores, sample = cpu_oracle_mlups(specs[:3], target_s=8.0)
+        if k >= args.warmup:
+            vals.append(mlups)
+    v = float(np.mean(vals))
+    return {"impl": "reference", "metric": "MLUPS (lattice updates/s, millions), batched "
+            "FP32-deviation D2Q9 MRT", "value": round(v, 2), "unit": "MLUPS",
+            "higher_is_better": True, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched-512-lattices-fp32dev-500-steps"},
+            "cpu_baseline": {"value": round(v, 2), "unit": "MLUPS", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 2), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(reference_arm(args)))
+        return
+    import torch
+
+    from paper_1107_4543_gb300 import build, lbm as L
+
+    if rank == 0 or not os.path.exists(L.LIB_PATH):
+        build.build()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+        torch.distributed.barrier()
+    else:
+        torch.cuda.set_device(0)
+    L.load()
+    if args.workload == "large":
+        if rank == 0:
+            for line in bench_large(args, L, torch, rank, ws):
+                print(json.dumps(line))
+        return
+    if args.workload == "serving":
+        if rank == 0:
+            print(json.dumps(bench_serving(args, L, torch)))
+        return
+    line, specs = bench_batched(args, L, torch, rank, ws)
+    if rank == 0:
+        if not args.no_cpu_baseline and ws == 1:
+            mlups, cores, sample = cpu_oracle_mlups(specs[:3])
+            line["cpu_baseline"] = {"value": round(mlups, 2), "unit": "MLUPS", "cores": cores,
+                                    "kind": "oracle", "sample": sample}
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -150,17 +150,18 @@ def vortical(nx, ny, seed, nmodes=32, kmax=64, std=1e-4, period=None):
     Ly = ny if period is None else period[1]
     x = np.arange(nx, dtype=np.float64)
     y = np.arange(ny, dtype=np.float64)
-    ux = np.zeros((ny, nx))
-    uy = np.zeros((ny, nx))
-    for n in range(nmodes):
-        kx = 2 * math.pi * px[n] / Lx
-        ky = 2 * math.pi * qy[n] / Ly
-        ax = kx * x[None, :] + phi[n]
-        by = ky * y[:, None]
-        # sin(kx x + ky y + phi) by the angle-sum rule, separably
-        s = np.sin(ax) * np.cos(by) + np.cos(ax) * np.sin(by)
-        ux += -a[n] * ky * s
-        uy += a[n] * kx * s
+    kx = 2 * math.pi * px / Lx
+    ky = 2 * math.pi * qy / Ly
+    ax = kx[:, None] * x[None, :] + phi[:, None]  # (nmodes, nx)
+    by = ky[:, None] * y[None, :]                 # (nmodes, ny)
+    # sin(kx x + ky y + phi) = sin(ax) cos(by) + cos(ax) sin(by): every
+    # component is a sum of separable products, i.e. one matrix product
+    Y = np.concatenate([np.cos(by), np.sin(by)]).T          # (ny, 2 nmodes)
+    Sx = np.concatenate([np.sin(ax), np.cos(ax)])            # (2 nmodes, nx)
+    wx = np.concatenate([-a * ky, -a * ky])[:, None]
+    wy = np.concatenate([a * kx, a * kx])[:, None]
+    ux = Y @ (wx * Sx)
+    uy = Y @ (wy * Sx)
     # the rms of each mode is known in closed form: scale without a pass
     var = 0.5 * np.sum(a * a * ((2 * math.pi * qy / Ly) ** 2 + (2 * math.pi * px / Lx) ** 2))
     scale = std / math.sqrt(var / 2.0)

@@ -27,9 +27,8 @@ __host__ __device__ constexpr double dnorm(int k) {
   return k == 0 ? 9.0 : (k <= 2 ? 6.0 : (k <= 4 ? 36.0 : (k <= 6 ? 12.0 : 4.0)));
 }
 
-// f^eq(rho, u) = M^-1 m^eq(rho, rho u), m^eq of section 2.3
-__host__ __device__ inline void feq_canonical(double rho, double ux, double uy, double f[9]) {
-  const double jx = rho * ux, jy = rho * uy;
+// f^eq = M^-1 m^eq(rho, j), m^eq of section 2.3
+__host__ __device__ inline void feq_of_j(double rho, double jx, double jy, double f[9]) {
   const double jsq = jx * jx + jy * jy;
   const double m[9] = {rho, jx, jy, -2.0 * rho + 3.0 * jsq / rho, rho - 3.0 * jsq / rho,
                        -jx, -jy, (jx * jx - jy * jy) / rho, jx * jy / rho};
@@ -43,8 +42,13 @@ __host__ __device__ inline void feq_canonical(double rho, double ux, double uy, 
   }
 }
 
-void host_feq(double rho, double ux, double uy, double out[9]) {
-  feq_canonical(rho, ux, uy, out);
+// f^eq(rho, u) with j = rho u formed first, as a plain implementation does
+__host__ __device__ inline void feq_canonical(double rho, double ux, double uy, double f[9]) {
+  feq_of_j(rho, rho * ux, rho * uy, f);
+}
+
+void host_feq_j(double rho, double jx, double jy, double out[9]) {
+  feq_of_j(rho, jx, jy, out);
 }
 
 __device__ __forceinline__ int wrapi(int a, int n) {

@@ -107,8 +107,8 @@ struct lbm_ctx {
   Lattice L;
   int device = 0;
   double S_paper[9];
-  double rho0 = 1.0, u0[2] = {0, 0};
-  double f0[9];
+  double rho0 = 1.0, j0[2] = {0, 0};  // reference state (FP32-exact for *DEV)
+  double f0[9];                       // base populations f^eq(rho0, j0)
   double qscale = 1.0;
   cudaStream_t own_stream = nullptr, stream = nullptr;
   long t = 0;
@@ -147,8 +147,8 @@ static AuxView aux_view(const lbm_ctx *h) {
   a.dtype = h->L.dtype;
   a.buf = h->L.buf[h->L.cur];
   a.rho0 = h->rho0;
-  a.jx0 = h->rho0 * h->u0[0];
-  a.jy0 = h->rho0 * h->u0[1];
+  a.jx0 = h->j0[0];
+  a.jy0 = h->j0[1];
   for (int i = 0; i < 9; ++i) a.f0[i] = h->f0[i];
   a.scale = h->qscale;
   return a;
@@ -317,14 +317,23 @@ int lbm_create(int nx, int ny, const double S[9], double rho0, const double u0[2
   // order (rho, jx, jy, e, eps, qx, qy, pxx, pxy)
   const int ll_of_paper[9] = {0, 3, 5, 1, 2, 4, 6, 7, 8};
   for (int k = 0; k < 9; ++k) h->S_paper[k] = S[ll_of_paper[k]];
-  h->rho0 = rho0;
-  h->u0[0] = u0[0];
-  h->u0[1] = u0[1];
-  host_feq(rho0, u0[0], u0[1], h->f0);
+  // The FP32 collision of the deviation types knows the reference state
+  // only as FP32 numbers, so the base f^eq(rho0, j0) is built from exactly
+  // those values: any mismatch would act as a spurious mean-flow error.
   DevParams &dp = h->L.dp;
   dp.rho0 = (float)rho0;
   dp.jx0 = (float)(rho0 * u0[0]);
   dp.jy0 = (float)(rho0 * u0[1]);
+  if (storage_dtype == LBM_F64) {
+    h->rho0 = rho0;
+    h->j0[0] = rho0 * u0[0];
+    h->j0[1] = rho0 * u0[1];
+  } else {
+    h->rho0 = dp.rho0;
+    h->j0[0] = dp.jx0;
+    h->j0[1] = dp.jy0;
+  }
+  host_feq_j(h->rho0, h->j0[0], h->j0[1], h->f0);
   dp.k3 = (float)(h->S_paper[3] / 36.0);
   dp.k4 = (float)(h->S_paper[4] / 36.0);
   dp.k5 = (float)(h->S_paper[5] / 12.0);

@@ -46,7 +46,7 @@ struct AuxView {
   int dtype;
   void *buf;          // current buffer
   double rho0, jx0, jy0;
-  double f0[9];       // base populations f^eq(rho0, u0) (deviation types)
+  double f0[9];       // base populations f^eq(rho0, j0) (deviation types)
   double scale;       // stored = f' * scale (FP16), 1 otherwise
 };
 cudaError_t launch_init_eq(const AuxView &a, const double *rho, const double *ux,
@@ -65,8 +65,8 @@ int drift_blocks();
 cudaError_t launch_drift(const AuxView &a, double *partials, double *out,
                          cudaStream_t st);
 
-// base populations f^eq(rho0, u0) on the host, in the canonical FP64 order
-void host_feq(double rho, double ux, double uy, double out[9]);
+// base populations f^eq(rho0, j0) on the host, in the canonical FP64 order
+void host_feq_j(double rho, double jx, double jy, double out[9]);
 
 // device memory through the configurable allocator
 void *dev_alloc(size_t bytes);

@@ -1,0 +1,226 @@
+"""GPU checks of the batched step and of the continuous-batching server.
+
+A lattice advanced inside a batch, or served among other requests, must
+give exactly the result it gives alone (same kernel body, same per-lattice
+parameters), and that result must match the FP64 oracle within its storage
+type's tolerance.
+"""
+import os
+import time
+
+import numpy as np
+import pytest
+
+import lbm_inputs as inp
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+TOL = {"f32": 1e-6, "f16": 2e-3, "bf16": 2e-3}
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1107_4543_gb300 import build, lbm
+
+    build.build()
+    lbm.load()
+    orc.set_threads(os.cpu_count() or 1)
+    return lbm
+
+
+def alone(L, spec, dtype, steps):
+    h = L.lbm_create(spec["nx"], spec["ny"], inp.s_ll(spec["rates"]), 1.0, (0.0, 0.0),
+                     L.DTYPES[dtype])
+    try:
+        L.lbm_init_field(h, *inp.batch_fields(spec))
+        L.lbm_step(h, steps)
+        return L.lbm_get_populations(h), L.lbm_moments(h)
+    finally:
+        L.lbm_destroy(h)
+
+
+def small_specs(n, seed):
+    return inp.batch_specs(n, seed=seed, amin=6 * 6, amax=96 * 96)
+
+
+@pytest.mark.parametrize("steps", [1, 7, 64, 131])
+def test_batch_member_equals_alone(L, steps):
+    specs = small_specs(12, seed=11)
+    dtypes = ["f32", "f16", "bf16"] * 4
+    hs = []
+    try:
+        for spec, dt in zip(specs, dtypes):
+            h = L.lbm_create(spec["nx"], spec["ny"], inp.s_ll(spec["rates"]), 1.0, (0.0, 0.0),
+                             L.DTYPES[dt])
+            L.lbm_init_field(h, *inp.batch_fields(spec))
+            hs.append(h)
+        # one member starts on its other buffer
+        L.lbm_step(hs[0], 1)
+        b = L.lbm_batch_create(hs)
+        L.lbm_batch_step(b, steps)
+        L.lbm_batch_step(b, 3)
+        got = [L.lbm_get_populations(h) for h in hs]
+        L.lbm_batch_destroy(b)
+    finally:
+        for h in hs:
+            L.lbm_destroy(h)
+    for k, (spec, dt) in enumerate(zip(specs, dtypes)):
+        want, _ = alone(L, spec, dt, steps + 3 + (1 if k == 0 else 0))
+        assert np.array_equal(got[k], want), (k, dt, spec["nx"], spec["ny"])
+
+
+def test_batch_results_match_oracle(L):
+    specs = small_specs(6, seed=12)
+    hs = []
+    steps = 60
+    try:
+        for spec in specs:
+            h = L.lbm_create(spec["nx"], spec["ny"], inp.s_ll(spec["rates"]), 1.0, (0.0, 0.0),
+                             L.LBM_F32DEV)
+            L.lbm_init_field(h, *inp.batch_fields(spec))
+            hs.append(h)
+        b = L.lbm_batch_create(hs)
+        L.lbm_batch_step(b, steps)
+        L.lbm_batch_destroy(b)
+        got = [L.lbm_moments(h)[0] for h in hs]
+    finally:
+        for h in hs:
+            L.lbm_destroy(h)
+    for spec, rho in zip(specs, got):
+        f = orc.run(orc.init_eq(*inp.batch_fields(spec)), inp.s_paper(spec["rates"]), steps)
+        rho_o = orc.moments(f)[0]
+        assert np.max(np.abs(rho - rho_o)) / spec["amp"] <= TOL["f32"]
+
+
+def test_batch_rejects_bad_members(L):
+    S = inp.s_ll(inp.rates("OPT"))
+    h64 = L.lbm_create(8, 8, S, dtype=L.LBM_F64)
+    h = L.lbm_create(8, 8, S, dtype=L.LBM_F32DEV)
+    try:
+        with pytest.raises(L.LbmError):
+            L.lbm_batch_create([h64])
+        with pytest.raises(L.LbmError):
+            L.lbm_batch_create([h, h])
+        b = L.lbm_batch_create([h])
+        with pytest.raises(L.LbmError):
+            L.lbm_step(h, 1)  # members step through the batch only
+        with pytest.raises(L.LbmError):
+            L.lbm_batch_create([h])  # already in a batch
+        L.lbm_batch_destroy(b)
+        L.lbm_step(h, 1)  # released
+    finally:
+        L.lbm_destroy(h)
+        L.lbm_destroy(h64)
+
+
+def served_requests(n, seed):
+    reqs = inp.request_stream(n, rate=1e9, seed=seed, side=(8, 80), steps=(1, 300))
+    return reqs
+
+
+def submit(L, srv, q, fields=False):
+    init = q["init"]
+    if fields:
+        kind, params, fl = L.LBM_INIT_FIELDS, (), inp.request_fields(q)
+    elif init["kind"] == "gaussian":
+        kind, params, fl = L.LBM_INIT_GAUSSIAN, (init["amp"], init["b"], init["xc"], init["yc"]), None
+    else:
+        kind, params, fl = L.LBM_INIT_PLANE, (init["amp"], init["m"]), None
+    req, keep = L.make_request(q["nx"], q["ny"], inp.s_ll(q["rates"]), q["steps"],
+                               dtype=q["dtype"], init_kind=kind, init_params=params, fields=fl)
+    return L.lbm_submit(srv, req), kind, params
+
+
+def alone_request(L, q, kind, params):
+    h = L.lbm_create(q["nx"], q["ny"], inp.s_ll(q["rates"]), 1.0, (0.0, 0.0),
+                     L.DTYPES[q["dtype"]])
+    try:
+        if kind == L.LBM_INIT_FIELDS:
+            L.lbm_init_field(h, *inp.request_fields(q))
+        else:
+            L.lbm_init_analytic(h, kind, params)
+        L.lbm_step(h, q["steps"])
+        return L.lbm_moments(h)
+    finally:
+        L.lbm_destroy(h)
+
+
+def wait_all(L, srv, ids, reqs, timeout=120.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(ids):
+        assert time.time() - t0 < timeout, "server did not finish in time"
+        for rid, q in zip(ids, reqs):
+            if rid in out:
+                continue
+            rc, rho, ux, uy, lat = L.lbm_poll(srv, rid, q["nx"], q["ny"])
+            if rc == L.LBM_OK:
+                out[rid] = (rho, ux, uy, lat)
+        time.sleep(0.001)
+    return out
+
+
+@pytest.mark.parametrize("budget_mb", [1000, 2])
+def test_served_result_equals_alone(L, budget_mb):
+    """Each served result equals the same solve run alone, with a budget
+    that admits everything at once and with one so tight that requests
+    queue and join generations as others retire."""
+    reqs = served_requests(16, seed=21)
+    srv = L.lbm_server_create(budget_mb * 2**20, 37)
+    try:
+        ids, kinds = [], []
+        for k, q in enumerate(reqs):
+            rid, kind, params = submit(L, srv, q, fields=(k % 4 == 0))
+            ids.append(rid)
+            kinds.append((kind, params))
+        out = wait_all(L, srv, ids, reqs)
+        st = L.lbm_server_stats(srv)
+    finally:
+        L.lbm_server_destroy(srv)
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    if budget_mb == 2:
+        assert st["peak_bytes"] <= 2 * 2**20
+        assert st["generations"] > 3
+    else:
+        assert st["peak_resident"] > 1
+    for rid, q, (kind, params) in zip(ids, reqs, kinds):
+        want = alone_request(L, q, kind, params)
+        for a, b in zip(out[rid][:3], want):
+            assert np.array_equal(a, b), (q["nx"], q["steps"], q["dtype"])
+
+
+def test_served_results_match_oracle(L):
+    reqs = served_requests(6, seed=22)
+    srv = L.lbm_server_create(2**30, 50)
+    try:
+        ids = [submit(L, srv, q, fields=True)[0] for q in reqs]
+        out = wait_all(L, srv, ids, reqs)
+    finally:
+        L.lbm_server_destroy(srv)
+    for rid, q in zip(ids, reqs):
+        f = orc.run(orc.init_eq(*inp.request_fields(q)), inp.s_paper(q["rates"]), q["steps"])
+        rho_o = orc.moments(f)[0]
+        err = np.max(np.abs(out[rid][0] - rho_o)) / q["init"]["amp"]
+        assert err <= TOL[q["dtype"]], (q["dtype"], err)
+        assert out[rid][3] > 0
+
+
+def test_server_rejects_and_reports(L):
+    srv = L.lbm_server_create(2**20, 10)
+    try:
+        big, _ = L.make_request(2048, 2048, inp.s_ll(inp.rates("OPT")), 10)
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_submit(srv, big)
+        assert e.value.code == L.LBM_ENOMEM
+        bad, _ = L.make_request(1, 8, inp.s_ll(inp.rates("OPT")), 10)
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_submit(srv, bad)
+        assert e.value.code == L.LBM_EINVAL
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_poll(srv, 12345, 8, 8)
+        assert e.value.code == L.LBM_ENOTFOUND
+    finally:
+        L.lbm_server_destroy(srv)

@@ -1,0 +1,153 @@
+"""GPU runs against the von Neumann analysis of section 4.1.
+
+(i) An acoustic eigenvector of the amplification matrix G(k), placed on the
+    512 x 16 lattice at small amplitude, must turn and decay by exactly its
+    eigenvalue per step.
+(ii) The plane-wave workload (rho' = A cos kx, u = U + c_s rho'/rho0): the
+    damping rate and phase speed fitted from the GPU run over t in
+    [200, 2000] must match the acoustic eigenvalue of G(k).
+G(k) is built in oracle.vn from the printed Psi of section 2.3.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import lbm_inputs as inp
+import oracle as orc
+from oracle import vn
+
+pytestmark = pytest.mark.gpu
+NX, NY = 512, 16
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1107_4543_gb300 import build, lbm
+
+    build.build()
+    lbm.load()
+    orc.set_threads(os.cpu_count() or 1)
+    return lbm
+
+
+def forward_mode(k, U, s):
+    G = vn.amplification(k, 0.0, U, 0.0, s)
+    lam, V = np.linalg.eig(G)
+    _, c = vn.mode_rates(lam, k)
+    j = int(np.argmin(np.abs(c - (U + vn.CS)) + 10 * (np.abs(lam) < 0.5)))
+    return lam[j], V[:, j]
+
+
+def mode_coeff(f, base, k, v):
+    fp = f[:, 0, :] - base[:, 0, :]
+    x = np.arange(NX)
+    fh = (fp * np.exp(-1j * k * x)[None, :]).sum(axis=1) / NX
+    return np.vdot(v, fh) / np.vdot(v, v)
+
+
+@pytest.mark.parametrize("dtype,amp,tol", [("f64", 1e-6, 1e-9), ("f32", 1e-4, 1e-7)])
+@pytest.mark.parametrize("U,name,lam_len", [(0.0, "LL", 8), (0.1, "OPT", 16), (0.1, "LL*", 6),
+                                            (0.0, "OPT-Z", 12), (0.0, "OPT", 32)])
+def test_eigenmode_evolves_by_its_eigenvalue(L, dtype, amp, tol, U, name, lam_len):
+    r = inp.rates(name, nu=1e-3)
+    s = inp.s_paper(r)
+    m = int(round(NX / lam_len))
+    k = 2 * math.pi * m / NX
+    lam, v = forward_mode(k, U, s)
+    base = orc.init_eq(np.ones((NY, NX)), np.full((NY, NX), U), np.zeros((NY, NX)))
+    x = np.arange(NX)
+    f0 = base + amp * np.real(v[:, None, None] * np.exp(1j * k * x)[None, None, :]
+                              * np.ones((1, NY, 1)))
+    h = L.lbm_create(NX, NY, inp.s_ll(r), 1.0, (U, 0.0), L.DTYPES[dtype])
+    try:
+        L.lbm_set_populations(h, f0)
+        L.lbm_step(h, 50)
+        c1 = mode_coeff(L.lbm_get_populations(h), base, k, v)
+        L.lbm_step(h, 200)
+        c2 = mode_coeff(L.lbm_get_populations(h), base, k, v)
+    finally:
+        L.lbm_destroy(h)
+    lam_meas = (c2 / c1) ** (1.0 / 200)
+    # the principal 200th root may sit on another branch: compare lambda^200
+    err = abs(c2 / c1 / lam ** 200 - 1.0) / 200
+    print("\n%s %s U=%.1f lambda=%d: |lam|=%.10f meas=%.10f rel.err/step=%.2e"
+          % (dtype, name, U, lam_len, abs(lam), abs(lam_meas), err))
+    assert err <= tol
+
+
+def fit_rates(series, t, k, lam):
+    """Damping per step and phase speed from the complex Fourier amplitude.
+    The series is first divided by lam^t (lam the VN eigenvalue) so that the
+    remaining phase turns slowly and unwraps unambiguously between samples;
+    the fitted residual slopes correct the VN rates."""
+    res = series / lam ** t
+    dd = -np.polyfit(t, np.log(np.abs(res)), 1)[0]
+    dphi = np.polyfit(t, np.unwrap(np.angle(res)), 1)[0]
+    d_vn, c_vn = vn.mode_rates(lam, k)
+    return d_vn + dd, c_vn - dphi / k
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_plane_wave_damping_and_speed(L, dtype):
+    """Config 2: lambda in {4, 6, 8, 12, 16, 32, 64}, U in {0, 0.1}, Lallemand-
+    Luo, LL* and optimized rates; 2000 steps; moments sampled every 100
+    steps from t = 200.  Reports the table; gates the match with VN."""
+    cases = []
+    for U in (0.0, 0.1):
+        for name in ("LL", "LL*", "OPT") + (("OPT-Z",) if U == 0.0 else ()):
+            for lam_len in (4, 6, 8, 12, 16, 32, 64):
+                cases.append((U, name, lam_len))
+    amp = 1e-4
+    hs = []
+    for U, name, lam_len in cases:
+        r = inp.rates(name, nu=1e-3)
+        m = int(round(NX / lam_len))
+        h = L.lbm_create(NX, NY, inp.s_ll(r), 1.0, (U, 0.0), L.DTYPES[dtype])
+        L.lbm_init_field(h, *inp.plane_wave(NX, NY, amp, m, U=U))
+        hs.append(h)
+    ts = np.arange(200, 2001, 100)
+    series = np.zeros((len(cases), len(ts)), dtype=complex)
+    x = np.arange(NX)
+    try:
+        b = L.lbm_batch_create(hs) if dtype != "f64" else None
+        t = 0
+        for j, tt in enumerate(ts):
+            if b is not None:
+                L.lbm_batch_step(b, tt - t)
+            else:
+                for h in hs:
+                    L.lbm_step(h, tt - t)
+            t = tt
+            for i, (U, name, lam_len) in enumerate(cases):
+                k = 2 * math.pi * round(NX / lam_len) / NX
+                rho = L.lbm_moments(hs[i])[0]
+                series[i, j] = ((rho[0] - 1.0) * np.exp(-1j * k * x)).sum() / NX
+        if b is not None:
+            L.lbm_batch_destroy(b)
+    finally:
+        for h in hs:
+            L.lbm_destroy(h)
+    rows = []
+    worst_c = worst_d = 0.0
+    for i, (U, name, lam_len) in enumerate(cases):
+        r = inp.rates(name, nu=1e-3)
+        m = int(round(NX / lam_len))
+        k = 2 * math.pi * m / NX
+        lam, _ = forward_mode(k, U, inp.s_paper(r))
+        d_vn, c_vn = vn.mode_rates(lam, k)
+        d, c = fit_rates(series[i], ts, k, lam)
+        rows.append((U, name, lam_len, d, d_vn, c, c_vn))
+        if lam_len >= 8:
+            worst_c = max(worst_c, abs(c - c_vn) / abs(c_vn))
+            # relative, with an absolute floor for the nearly undamped sets
+            worst_d = max(worst_d, abs(d - d_vn) / (abs(d_vn) + 4e-6))
+    print("\n%s plane waves: U  set  lambda  damping(GPU)  damping(VN)  c(GPU)  c(VN)" % dtype)
+    for row in rows:
+        print("  %.1f %-5s %3d  %.4e  %.4e  %.6f  %.6f" % row)
+    assert worst_c < 1e-4
+    assert worst_d < 0.05
