@@ -463,6 +463,10 @@ def main():
         torch.distributed.barrier()
     else:
         torch.cuda.set_device(0)
+    # all work on one non-default stream: the library launches on it (the
+    # handle of the legacy default stream is 0, which lbm_set_stream reads as
+    # "the handle's own stream"), and the CUDA events record on it
+    torch.cuda.set_stream(torch.cuda.Stream())
     L.load()
     if args.workload == "large":
         if rank == 0:

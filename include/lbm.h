@@ -135,7 +135,9 @@ int lbm_get_populations(lbm_handle h, double *f);
 int lbm_set_populations(lbm_handle h, const double *f);
 
 /* Use `stream` (a cudaStream_t, e.g. torch.cuda.current_stream()) for all
- * further work of the handle; NULL restores the handle's own stream. */
+ * further work of the handle; NULL restores the handle's own stream (so the
+ * legacy default stream cannot be selected: pass a created stream).
+ * Synchronizes the previous stream first. */
 int lbm_set_stream(lbm_handle h, void *stream);
 
 /* Wait for the handle's stream. */

@@ -131,17 +131,23 @@ def window_run(rho, ux, uy, s, nsteps, x, y):
 
     A node after T steps depends only on the initial field within distance
     T (one node per step), so the plain periodic oracle is run on the
-    (2T+3)^2 window around (x, y) cut out of the initial macroscopic fields;
-    wrong data entering from the window's own wrap cannot reach the centre.
-    Returns the 9 populations of the centre node.
+    (2T+3)-wide window around (x, y) cut out of the initial macroscopic
+    fields; wrong data entering from the window's own wrap cannot reach the
+    centre.  Along a dimension no longer than the window the whole periodic
+    extent is kept (its wrap is then the true one).  Returns the 9
+    populations of the node.
     """
     ny, nx = rho.shape
     h = int(nsteps) + 1
-    n = 2 * h + 1
-    if n >= nx or n >= ny:
-        raise ValueError("window larger than the lattice; run the full oracle")
-    ys = (np.arange(y - h, y + h + 1) % ny)[:, None]
-    xs = (np.arange(x - h, x + h + 1) % nx)[None, :]
-    f = init_eq(rho[ys, xs], ux[ys, xs], uy[ys, xs])
+    if 2 * h + 1 < ny:
+        ys, cy = np.arange(y - h, y + h + 1) % ny, h
+    else:
+        ys, cy = np.arange(ny), y
+    if 2 * h + 1 < nx:
+        xs, cx = np.arange(x - h, x + h + 1) % nx, h
+    else:
+        xs, cx = np.arange(nx), x
+    sel = (ys[:, None], xs[None, :])
+    f = init_eq(rho[sel], ux[sel], uy[sel])
     f = run(f, s, nsteps)
-    return f[:, h, h].copy()
+    return f[:, cy, cx].copy()

@@ -222,6 +222,12 @@ static int ensure_stage(lbm_ctx *h) {
   return LBM_OK;
 }
 
+// v = hi + lo with hi = fl32(v), lo = fl32(v - hi)
+static void split_rate(double v, float &hi, float &lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
 static int check_rates(const double S[9]) {
   static const int conserved[3] = {0, 3, 5};  // rho, jx, jy in LL order
   for (int k = 0; k < 9; ++k) {
@@ -334,12 +340,19 @@ int lbm_create(int nx, int ny, const double S[9], double rho0, const double u0[2
     h->j0[1] = dp.jy0;
   }
   host_feq_j(h->rho0, h->j0[0], h->j0[1], h->f0);
-  dp.k3 = (float)(h->S_paper[3] / 36.0);
-  dp.k4 = (float)(h->S_paper[4] / 36.0);
-  dp.k5 = (float)(h->S_paper[5] / 12.0);
-  dp.k6 = (float)(h->S_paper[6] / 12.0);
-  dp.k7 = (float)(h->S_paper[7] / 4.0);
-  dp.k8 = (float)(h->S_paper[8] / 4.0);
+  split_rate(h->S_paper[3] / 36.0, dp.k3, dp.l3);
+  split_rate(h->S_paper[4] / 36.0, dp.k4, dp.l4);
+  split_rate(h->S_paper[5] / 12.0, dp.k5, dp.l5);
+  split_rate(h->S_paper[6] / 12.0, dp.k6, dp.l6);
+  split_rate(h->S_paper[7] / 4.0, dp.k7, dp.l7);
+  split_rate(h->S_paper[8] / 4.0, dp.k8, dp.l8);
+  {
+    const double jx = dp.jx0, jy = dp.jy0, r = dp.rho0;
+    split_rate(jx * jx + jy * jy, dp.q0h, dp.q0l);
+    split_rate(jx * jx - jy * jy, dp.d0h, dp.d0l);
+    split_rate(jx * jy, dp.x0h, dp.x0l);
+    split_rate(1.0 / (r * r), dp.i2h, dp.i2l);
+  }
   dp.scale = 1.0f;
   dp.inv_scale = 1.0f;
   F64Params &fp = h->L.fp;

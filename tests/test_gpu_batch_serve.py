@@ -69,7 +69,9 @@ def test_batch_member_equals_alone(L, steps):
             L.lbm_destroy(h)
     for k, (spec, dt) in enumerate(zip(specs, dtypes)):
         want, _ = alone(L, spec, dt, steps + 3 + (1 if k == 0 else 0))
-        assert np.array_equal(got[k], want), (k, dt, spec["nx"], spec["ny"])
+        # some sweep members are linearly unstable (Lallemand-Luo free rates
+        # at small bulk viscosity, section 4.2) and overflow: NaN == NaN here
+        assert np.array_equal(got[k], want, equal_nan=True), (k, dt, spec["nx"], spec["ny"])
 
 
 def test_batch_results_match_oracle(L):
