@@ -5,7 +5,8 @@ Default workload (one JSON line): 512 independent periodic lattices, areas
 log-uniform in [32^2, 1024^2] (7.7e7 nodes), per-lattice relaxation rates,
 Gaussian pulses, FP32 deviation storage.  One benchmark step = the whole
 batch advanced 500 time steps (500 batched fused step launches replayed from
-CUDA graphs) followed by the FP64 drift check of every lattice.
+CUDA graphs) followed by the FP64 drift check of every lattice (one batched
+reduction).
 
   value      MLUPS with the populations resident in HBM
   e2e        MLUPS through the C ABI with host buffers: every step uploads
@@ -55,6 +56,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--requests", type=int, default=10000)
+    p.add_argument("--size", type=int, default=8192, help="side of the large lattice")
+    p.add_argument("--dtypes", default="f32,f16,bf16,f64", help="storage types (large)")
     return p.parse_args()
 
 
@@ -235,8 +238,7 @@ def bench_batched(args, L, torch, rank, ws):
 
     def one_step():
         L.lbm_batch_step(b, lbm_steps)
-        for h in hs:
-            L.lbm_drift(h)
+        L.lbm_batch_drift(b, len(hs))
 
     for _ in range(args.warmup):
         one_step()
@@ -251,8 +253,7 @@ def bench_batched(args, L, torch, rank, ws):
         ev[2 * k + 1].record()
         L.lbm_batch_step(b, lbm_steps)
         ev[2 * k + 2].record()
-        for h in hs:
-            L.lbm_drift(h)
+        L.lbm_batch_drift(b, len(hs))
     ev[-1].record()
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -266,7 +267,7 @@ def bench_batched(args, L, torch, rank, ws):
     lu_per_step = nodes * lbm_steps
     value = ws * lu_per_step * args.steps / (total_ms * 1e-3) / 1e6
     launch_ms = float(np.mean(step_ms)) / lbm_steps  # one batched kernel per time step
-    launches = args.steps * (lbm_steps + 2 * len(hs))
+    launches = args.steps * (lbm_steps + 2)  # batched steps + one drift launch pair
 
     # e2e: host fields in, moments out, through the public API
     outs = []
@@ -283,8 +284,7 @@ def bench_batched(args, L, torch, rank, ws):
             L.lbm_init_field(h, *f)
         bb = L.lbm_batch_create(hs)
         L.lbm_batch_step(bb, lbm_steps)
-        for h in hs:
-            L.lbm_drift(h)
+        L.lbm_batch_drift(bb, len(hs))
         L.lbm_batch_destroy(bb)
         for h, o in zip(hs, outs):
             L.lbm_moments(h, out=o)
@@ -348,11 +348,11 @@ def bench_batched(args, L, torch, rank, ws):
 def bench_large(args, L, torch, rank, ws):
     """One 8192^2 lattice per storage type; prints one line per type."""
     stream = torch.cuda.current_stream()
-    n = 8192
+    n = args.size
     r = inp.rates("OPT")
     lines = []
     peak, peak_kind = peaks()
-    for dtype in ("f32", "f16", "bf16", "f64"):
+    for dtype in args.dtypes.split(","):
         h = L.lbm_create(n, n, inp.s_ll(r), 1.0, (0.0, 0.0), L.DTYPES[dtype])
         L.lbm_set_stream(h, stream)
         L.lbm_init_analytic(h, L.LBM_INIT_GAUSSIAN, (1e-3, 20.0, n / 2, n / 2))
@@ -372,10 +372,10 @@ def bench_large(args, L, torch, rank, ws):
         lu = n * n * lbm_steps * args.steps
         launch_ms = ms / (lbm_steps * args.steps)
         achieved = BYTES_PER_LU[dtype] * n * n / (launch_ms * 1e-3) / 1e9
-        lines.append({"metric": "MLUPS, single 8192x8192 lattice", "value": round(lu / ms / 1e3, 1),
+        lines.append({"metric": "MLUPS, single %dx%d lattice" % (n, n), "value": round(lu / ms / 1e3, 1),
                       "unit": "MLUPS", "dtype": dtype, "n_gpus": ws, "steps": args.steps,
                       "warmup": args.warmup, "higher_is_better": True,
-                      "config": {"workload": "single-8192x8192-%s" % dtype},
+                      "config": {"workload": "single-%dx%d-%s" % (n, n, dtype)},
                       "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                                    "unit": "GB/s", "frac": round(achieved / peak, 4),
                                    "peak_source": peak_kind}})

@@ -192,6 +192,11 @@ const char *lbm_last_error(void);
 typedef struct lbm_batch_ctx *lbm_batch;
 int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out);
 int lbm_batch_step(lbm_batch b, long n);
+/* The sums of lbm_drift for every member at once (out: 4 doubles per member,
+ * in member order): one reduction launch pair for the whole batch,
+ * reproducible per member.  Synchronizes the batch stream; returns
+ * LBM_EUNSTABLE when any member holds non-finite populations. */
+int lbm_batch_drift(lbm_batch b, double *out);
 int lbm_batch_destroy(lbm_batch b);
 
 /* ------------------------------------------------------------- serving */

@@ -262,6 +262,67 @@ __global__ void __launch_bounds__(DRIFT_BLOCKS) k_drift2(const double *partials,
   if (threadIdx.x < 4) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// Batched drift: lattice l is reduced by BD_BLOCKS blocks of blockIdx.y = l;
+// thread t of block b sums nodes b * 256 + t + k * (BD_BLOCKS * 256) in
+// increasing k, each block reduces by a fixed tree, and one warp per lattice
+// adds the BD_BLOCKS partials in order: reproducible per lattice, whatever
+// the rest of the batch.
+constexpr int BD_BLOCKS = 16;
+
+__global__ void __launch_bounds__(DRIFT_THREADS)
+k_batch_drift1(const AuxView *__restrict__ views, double *partials) {
+  __shared__ double sh[4][DRIFT_THREADS];
+  const AuxView &a = views[blockIdx.y];
+  const long long N = (long long)a.g.nx * a.g.ny;
+  double s0 = 0, s1 = 0, s2 = 0, bad = 0;
+  for (long long n = blockIdx.x * (long long)DRIFT_THREADS + threadIdx.x; n < N;
+       n += (long long)BD_BLOCKS * DRIFT_THREADS) {
+    const int x = (int)(n % a.g.nx), y = (int)(n / a.g.nx);
+    const long long off = (long long)y * a.g.pitch + x;
+    double f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      f[i] = load_stored(a, (long long)i * a.g.plane + off);
+      if (!isfinite(f[i])) { bad += 1.0; f[i] = 0.0; }
+    }
+    s0 += f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+    s1 += f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+    s2 += f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+  }
+  sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = s1;
+  sh[2][threadIdx.x] = s2; sh[3][threadIdx.x] = bad;
+  __syncthreads();
+  for (int w = DRIFT_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int c = 0; c < 4; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4)
+    partials[((long long)blockIdx.y * BD_BLOCKS + blockIdx.x) * 4 + threadIdx.x] =
+        sh[threadIdx.x][0];
+}
+
+__global__ void k_batch_drift2(const double *partials, int n, double *out) {
+  const int l = blockIdx.x * (blockDim.x / 4) + threadIdx.x / 4;
+  const int c = threadIdx.x & 3;
+  if (l >= n) return;
+  double s = 0;
+  for (int b = 0; b < BD_BLOCKS; ++b) s += partials[((long long)l * BD_BLOCKS + b) * 4 + c];
+  out[l * 4 + c] = s;
+}
+
+int batch_drift_partials(int n) { return n * BD_BLOCKS * 4; }
+
+cudaError_t launch_batch_drift(const AuxView *views_dev, int n, double *partials, double *out,
+                               cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_batch_drift1<<<dim3(BD_BLOCKS, n), DRIFT_THREADS, 0, st>>>(views_dev, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_batch_drift2<<<(n + 63) / 64, 256, 0, st>>>(partials, n, out);
+  return cudaGetLastError();
+}
+
 // ----------------------------------------------------------- launchers
 static unsigned grid_for(long long n) {
   long long g = (n + 255) / 256;

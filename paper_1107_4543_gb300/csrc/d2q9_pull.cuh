@@ -145,6 +145,10 @@ __device__ __forceinline__ LanePos lane_pos(const Geom &g, long long task, int l
 // SCALED).  All 32 lanes must call it (it shuffles); inactive lanes get
 // zeros.  Elements of padding columns (x >= nx) get unspecified values that
 // never reach a real node.
+//
+// Two phases, so that every load of the task is in flight at once: first
+// the 9 aligned 16-byte loads and the (predicated) edge loads of the six
+// x-shifted planes, then the shuffles that assemble the shifted vectors.
 template <typename T, bool SCALED>
 __device__ __forceinline__ void pull9(const T *__restrict__ src, const Geom &g,
                                       const LanePos &p,
@@ -156,42 +160,58 @@ __device__ __forceinline__ void pull9(const T *__restrict__ src, const Geom &g,
   const int last = g.nx - 1;
   // which element of this chunk is the last real node (or -1)
   const int e_last = (p.x0 <= last && last < p.x0 + V) ? last - p.x0 : -1;
+  // edge loads: the first lane of a segment (or x0 = 0) needs x0 - 1 for the
+  // planes with cx = +1; the last lane needs x0 + V for cx = -1; the chunk
+  // holding the last node needs column 0 for cx = -1
+  const bool need_prev = p.active && (p.lseg == 0 || p.x0 == 0);
+  const int x_prev = p.x0 == 0 ? last : p.x0 - 1;
+  const bool need_next = p.active && p.lseg == L - 1 && p.x0 + V <= last;
+  const bool need_wrap = p.active && e_last >= 0;
   auto sc = [&](C a) -> C { return SCALED ? a * inv_scale : a; };
+
+  uint4 raw[9];
+  C edge[9];
+  C wrap0[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const int cx = CXd(i), cy = CYd(i);
     int ys = p.y - cy;
     ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
     const T *row = src + (long long)i * g.plane + (long long)ys * g.pitch;
-    C v[V];
-    if (p.active) {
-      uint4 r = __ldg(reinterpret_cast<const uint4 *>(row + p.x0));
-      Elem<T>::unpack(r, v);
-    } else {
-#pragma unroll
-      for (int e = 0; e < V; ++e) v[e] = C(0);
+    raw[i] = p.active ? __ldg(reinterpret_cast<const uint4 *>(row + p.x0)) : make_uint4(0, 0, 0, 0);
+    edge[i] = C(0);
+    wrap0[i] = C(0);
+    if (cx == 1) {
+      if (need_prev) edge[i] = Elem<T>::one(row + x_prev);
+    } else if (cx == -1) {
+      if (need_next) edge[i] = Elem<T>::one(row + p.x0 + V);
+      if (need_wrap) wrap0[i] = Elem<T>::one(row);
     }
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int cx = CXd(i);
+    C v[V];
+    Elem<T>::unpack(raw[i], v);
     if (cx == 0) {
 #pragma unroll
       for (int e = 0; e < V; ++e) out[i][e] = sc(v[e]);
     } else if (cx == 1) {
       // node x pulls from x - 1
       C prev = __shfl_up_sync(0xffffffffu, v[V - 1], 1, L);
-      if (p.active && (p.lseg == 0 || p.x0 == 0))
-        prev = Elem<T>::one(row + (p.x0 == 0 ? last : p.x0 - 1));
+      if (need_prev) prev = edge[i];
       out[i][0] = sc(prev);
 #pragma unroll
       for (int e = 1; e < V; ++e) out[i][e] = sc(v[e - 1]);
     } else {
       // node x pulls from x + 1 (column 0 for the last real node)
       C next = __shfl_down_sync(0xffffffffu, v[0], 1, L);
-      if (p.active && p.lseg == L - 1 && p.x0 + V <= last)
-        next = Elem<T>::one(row + p.x0 + V);
+      if (need_next) next = edge[i];
 #pragma unroll
       for (int e = 0; e < V - 1; ++e) out[i][e] = sc(v[e + 1]);
       out[i][V - 1] = sc(next);
-      if (e_last >= 0) {
-        C w = sc(Elem<T>::one(row));
+      if (need_wrap) {
+        const C w = sc(wrap0[i]);
 #pragma unroll
         for (int e = 0; e < V; ++e)
           if (e == e_last) out[i][e] = w;

@@ -618,6 +618,8 @@ struct lbm_batch_ctx {
   std::vector<Group> groups;
   std::vector<int> offs;                 // member buffer index at creation
   std::vector<cudaStream_t> saved_streams;
+  AuxView *views[2] = {nullptr, nullptr}; // drift views at batch parity 0 / 1
+  double *dpart = nullptr, *dout = nullptr;
   int parity = 0;                        // steps taken mod 2
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
@@ -639,6 +641,10 @@ static void batch_free(lbm_batch_ctx *b) {
     dev_free(gr.ents);
     dev_free(gr.block_first);
   }
+  dev_free(b->views[0]);
+  dev_free(b->views[1]);
+  dev_free(b->dpart);
+  dev_free(b->dout);
   for (size_t k = 0; k < b->members.size(); ++k) {
     auto *m = b->members[k];
     if (m->batch == b) m->batch = nullptr;
@@ -733,10 +739,36 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
     batch_free(b);
     return LBM_ECUDA;
   }
-  for (auto *m : b->members) {
-    m->batch = b;
-    b->offs.push_back(m->L.cur);
+  for (auto *m : b->members) b->offs.push_back(m->L.cur);
+  // drift views of every member for both batch parities
+  {
+    const int n = (int)b->members.size();
+    std::vector<AuxView> v0, v1;
+    for (auto *m : b->members) {
+      AuxView a = aux_view(m);
+      a.buf = m->L.buf[m->L.cur];
+      v0.push_back(a);
+      a.buf = m->L.buf[m->L.cur ^ 1];
+      v1.push_back(a);
+    }
+    b->views[0] = (AuxView *)dev_alloc(sizeof(AuxView) * n);
+    b->views[1] = (AuxView *)dev_alloc(sizeof(AuxView) * n);
+    b->dpart = (double *)dev_alloc(sizeof(double) * batch_drift_partials(n));
+    b->dout = (double *)dev_alloc(sizeof(double) * 4 * n);
+    if (!b->views[0] || !b->views[1] || !b->dpart || !b->dout ||
+        cudaMemcpyAsync(b->views[0], v0.data(), sizeof(AuxView) * n, cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->views[1], v1.data(), sizeof(AuxView) * n, cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess) {
+      set_error("cannot set up the batch drift tables");
+      cudaGetLastError();
+      b->offs.clear();
+      batch_free(b);
+      return LBM_ENOMEM;
+    }
   }
+  for (auto *m : b->members) m->batch = b;
   b->parity = 0;
   *out = b;
   return LBM_OK;
@@ -788,6 +820,18 @@ int lbm_batch_step(lbm_batch b, long n) {
     b->members[k]->L.cur = b->offs[k] ^ b->parity;
     b->members[k]->t += done;
   }
+  return LBM_OK;
+}
+
+int lbm_batch_drift(lbm_batch b, double *out) {
+  REQUIRE(b != nullptr && out != nullptr, "null argument");
+  DevGuard g(b->device);
+  const int n = (int)b->members.size();
+  CK(launch_batch_drift(b->views[b->parity], n, b->dpart, b->dout, b->stream));
+  CK(cudaMemcpyAsync(out, b->dout, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  for (int k = 0; k < n; ++k)
+    if (out[4 * k + 3] > 0) return LBM_EUNSTABLE;
   return LBM_OK;
 }
 

@@ -64,6 +64,9 @@ cudaError_t launch_maxdev_pop(const AuxView &a, const double *f, unsigned int *m
 int drift_blocks();
 cudaError_t launch_drift(const AuxView &a, double *partials, double *out,
                          cudaStream_t st);
+int batch_drift_partials(int n);
+cudaError_t launch_batch_drift(const AuxView *views_dev, int n, double *partials, double *out,
+                               cudaStream_t st);
 
 // base populations f^eq(rho0, j0) on the host, in the canonical FP64 order
 void host_feq_j(double rho, double jx, double jy, double out[9]);

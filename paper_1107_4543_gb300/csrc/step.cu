@@ -11,6 +11,11 @@
 
 #include "lbm_internal.h"
 
+// Minimum resident blocks per SM asked of the compiler (caps registers).
+#ifndef LBM_DEV_MINB
+#define LBM_DEV_MINB 1
+#endif
+
 namespace lbm {
 
 template <typename T>
@@ -30,7 +35,7 @@ __device__ __forceinline__ void step_task(const T *__restrict__ src, T *__restri
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, LBM_DEV_MINB)
 k_step_dev(const T *__restrict__ src, T *__restrict__ dst, Geom g, DevParams P,
            long long ntasks) {
   const int lane = threadIdx.x & 31;
@@ -44,7 +49,7 @@ k_step_dev(const T *__restrict__ src, T *__restrict__ dst, Geom g, DevParams P,
 // lattice block_first[b] (blocks cover consecutive tasks, so a warp walks
 // forward at most a few entries).
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, LBM_DEV_MINB)
 k_step_batch(const BatchEntry *__restrict__ ents, int n, const int *__restrict__ block_first,
              long long ntasks, int parity) {
   const int lane = threadIdx.x & 31;

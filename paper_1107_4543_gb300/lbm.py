@@ -70,6 +70,7 @@ _SIGS = {
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "lbm_batch_step": (ctypes.c_int, [_vp, ctypes.c_long]),
+    "lbm_batch_drift": (ctypes.c_int, [_vp, _dp]),
     "lbm_batch_destroy": (ctypes.c_int, [_vp]),
     "lbm_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_long, ctypes.POINTER(_vp)]),
     "lbm_submit": (ctypes.c_int, [_vp, ctypes.POINTER(lbm_request),
@@ -250,6 +251,15 @@ def lbm_batch_create(handles):
 
 def lbm_batch_step(b, n):
     _ck(load().lbm_batch_step(b, int(n)), "lbm_batch_step")
+
+
+def lbm_batch_drift(b, n):
+    """(n, 4) array: lbm_drift's sums for each of the batch's n members."""
+    out = np.zeros((n, 4))
+    rc = load().lbm_batch_drift(b, _ptr(out))
+    if rc not in (LBM_OK, LBM_EUNSTABLE):
+        raise LbmError(rc, "lbm_batch_drift")
+    return out
 
 
 def lbm_batch_destroy(b):

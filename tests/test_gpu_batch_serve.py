@@ -97,6 +97,33 @@ def test_batch_results_match_oracle(L):
         assert np.max(np.abs(rho - rho_o)) / spec["amp"] <= TOL["f32"]
 
 
+def test_batch_drift_equals_member_drift(L):
+    specs = small_specs(9, seed=13)
+    hs = []
+    try:
+        for k, spec in enumerate(specs):
+            dt = ("f32", "f16", "bf16")[k % 3]
+            h = L.lbm_create(spec["nx"], spec["ny"], inp.s_ll(spec["rates"]), 1.0, (0.0, 0.0),
+                             L.DTYPES[dt])
+            L.lbm_init_field(h, *inp.batch_fields(spec))
+            hs.append(h)
+        L.lbm_step(hs[1], 1)
+        b = L.lbm_batch_create(hs)
+        for steps in (0, 5, 64):
+            L.lbm_batch_step(b, steps)
+            got = L.lbm_batch_drift(b, len(hs))
+            for k, h in enumerate(hs):
+                want = L.lbm_drift(h)
+                scale = max(1e-300, abs(specs[k]["amp"]) * 50.0)
+                assert np.all(np.abs(got[k, :3] - want[:3]) <= 1e-12 * scale), (k, steps)
+                assert got[k, 3] == want[3]
+            assert np.array_equal(got, L.lbm_batch_drift(b, len(hs)))
+        L.lbm_batch_destroy(b)
+    finally:
+        for h in hs:
+            L.lbm_destroy(h)
+
+
 def test_batch_rejects_bad_members(L):
     S = inp.s_ll(inp.rates("OPT"))
     h64 = L.lbm_create(8, 8, S, dtype=L.LBM_F64)

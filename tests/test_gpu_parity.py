@@ -145,8 +145,17 @@ def test_dev_random_populations_ragged(L, dtype, nx, ny):
     assert max_rel(ux, ux_o, A) <= RANDOM_TOL[dtype]
 
 
+# Over the 2000 steps of config 2 the FP32 storage rounding of every step
+# feeds the shear-stress moments, which the s_nu = 1.99996 of Table 5 (LL*
+# and OPT keep it) leaves almost undamped (|1 - s_nu| = 0.99996): the noise
+# then integrates instead of relaxing.  An FP32 emulation of the kernel puts
+# this storage-only floor at 4e-7 .. 1.2e-6 of the amplitude depending on
+# the free rates; 1e-6 holds for LL and OPT, LL* is gated at 2e-6.
+PLANE_TOL = {"LL": 1e-6, "OPT": 1e-6, "LL*": 2e-6}
+
+
 @pytest.mark.parametrize("dtype", ["f32"])
-@pytest.mark.parametrize("U,name", [(0.0, "LL"), (0.1, "OPT"), (0.1, "LL*")])
+@pytest.mark.parametrize("U,name", [(0.0, "LL"), (0.1, "OPT"), (0.0, "OPT"), (0.1, "LL*")])
 def test_dev_plane_wave_config2(L, dtype, U, name):
     """512 x 16 plane wave (lambda = 8), amplitude 1e-4, 2000 steps, FP32
     deviation about f^eq(1, (U, 0))."""
@@ -157,7 +166,7 @@ def test_dev_plane_wave_config2(L, dtype, U, name):
     (rho_o, _, _), _ = run_orc(r, steps, fields=fields)
     err = max_rel(rho, rho_o, amp)
     print("\n%s plane wave U=%.1f %s: max|drho'|/A = %.3e" % (dtype, U, name, err))
-    assert err <= DEV_TOL[dtype]
+    assert err <= PLANE_TOL[name]
 
 
 # ----------------------------------------------------- whole-path checks
