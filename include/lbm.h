@@ -152,6 +152,31 @@ int lbm_sync(lbm_handle h);
  * Synchronizes; returns LBM_EUNSTABLE when out[3] > 0. */
 int lbm_drift(lbm_handle h, double out[4]);
 
+/* lbm_drift_pop_noalloc -- the sums of lbm_drift over a caller-owned array
+ * of full FP64 populations, without allocating any device memory.  The
+ * paper has no counterpart: this entry point serves callers that cannot
+ * allocate device memory -- e.g. a host application whose own allocator
+ * already owns the GPU's memory, or a loop under a fixed memory budget where
+ * a cudaMalloc (with its implicit synchronisation and failure modes) is not
+ * acceptable.
+ *   f_dev   device array of 9 x ny x nx doubles (index (i*ny + y)*nx + x),
+ *           owned by the caller, unchanged
+ *   rho0, jx0, jy0  reference state subtracted at every node
+ *   out     host array of 4 doubles, owned by the caller: sum rho',
+ *           sum jx', sum jy', number of non-finite populations
+ *   stream  cudaStream_t to run on (NULL: the legacy default stream);
+ *           the call synchronizes it before returning.
+ * Its scratch is a fixed device array inside the library of
+ * (8192 + 1) x 4 doubles (256 KiB + 32 B), held by every GPU that loads the
+ * library until the process exits; hence ny <= 8192 (LBM_EINVAL with a
+ * message otherwise).  The first call on a device looks up that array's
+ * device address (once per device); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's
+ * contents (each call writes every slot it reads): calls that overlap on
+ * the GPU race, so serialize them.  Returns LBM_EUNSTABLE when out[3] > 0. */
+int lbm_drift_pop_noalloc(const double *f_dev, int nx, int ny, double rho0,
+                          double jx0, double jy0, double out[4], void *stream);
+
 /* Static description of a lattice. */
 typedef struct {
   int nx, ny;

@@ -23,6 +23,7 @@ UNITS = {
     "step_f64.cu": ["-fmad=false"],
     "aux.cu": ["-fmad=false"],
     "serve.cu": [],
+    "drift_noalloc.cu": [],
 }
 HEADERS = ["lbm_internal.h", "d2q9_pull.cuh", "collide.cuh"]
 

@@ -64,6 +64,8 @@ _SIGS = {
     "lbm_set_stream": (ctypes.c_int, [_vp, _vp]),
     "lbm_sync": (ctypes.c_int, [_vp]),
     "lbm_drift": (ctypes.c_int, [_vp, _dp]),
+    "lbm_drift_pop_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, _dp, _vp]),
     "lbm_info": (ctypes.c_int, [_vp, ctypes.POINTER(lbm_info_t)]),
     "lbm_set_allocator": (ctypes.c_int, [_vp, _vp, _vp]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -232,6 +234,19 @@ def lbm_drift(h):
     rc = load().lbm_drift(h, _ptr(out))
     if rc not in (LBM_OK, LBM_EUNSTABLE):
         raise LbmError(rc, "lbm_drift")
+    return out
+
+
+def lbm_drift_pop_noalloc(f_dev, nx, ny, rho0=1.0, j0=(0.0, 0.0), stream=None):
+    """lbm_drift's sums over caller-owned FP64 populations (device pointer or
+    contiguous CUDA tensor of 9 x ny x nx doubles), allocating nothing."""
+    out = np.zeros(4)
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    rc = load().lbm_drift_pop_noalloc(_dev(f_dev), int(nx), int(ny), float(rho0), float(j0[0]),
+                                      float(j0[1]), _ptr(out), stream)
+    if rc not in (LBM_OK, LBM_EUNSTABLE):
+        raise LbmError(rc, "lbm_drift_pop_noalloc")
     return out
 
 
