@@ -114,6 +114,18 @@ int lbm_init_analytic(lbm_handle h, int kind, const double params[8]);
  * LBM_ECUDA (launch failure). */
 int lbm_step(lbm_handle h, long n);
 
+/* lbm_tune -- time the launch variants of the step kernel on this lattice
+ * (LBM_TUNE_VARIANTS register caps of the deviation-storage kernel) and keep
+ * the fastest for later steps.  Trial launches read the current state and
+ * write only the idle buffer, so the lattice's state does not change.
+ * times_ms (may be NULL) receives each variant's average launch time,
+ * chosen (may be NULL) the variant kept.  lbm_step tunes lattices of at
+ * least 2^20 nodes on their first step unless the environment sets
+ * LBM_AUTOTUNE=0; choices are shared by lattices of the same type and size
+ * within the process.  LBM_F64 has one variant (times -1).  Synchronizes. */
+#define LBM_TUNE_VARIANTS 3
+int lbm_tune(lbm_handle h, double *times_ms, int *chosen);
+
 /* lbm_moments -- rho, ux, uy (host, ny x nx) at the current time: the
  * moments of the pre-collision populations, u = j / rho.  Synchronizes. */
 int lbm_moments(lbm_handle h, double *rho, double *ux, double *uy);
@@ -217,6 +229,10 @@ const char *lbm_last_error(void);
 typedef struct lbm_batch_ctx *lbm_batch;
 int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out);
 int lbm_batch_step(lbm_batch b, long n);
+/* As lbm_tune for the batch's launches (one variant for all its storage
+ * types; the first lbm_batch_step of a batch of >= 2^20 nodes tunes unless
+ * LBM_AUTOTUNE=0).  Members' states do not change. */
+int lbm_batch_tune(lbm_batch b, double *times_ms, int *chosen);
 /* The sums of lbm_drift for every member at once (out: 4 doubles per member,
  * in member order): one reduction launch pair for the whole batch,
  * reproducible per member.  Synchronizes the batch stream; returns

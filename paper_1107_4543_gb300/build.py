@@ -19,13 +19,15 @@ COMMON = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                  "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr"]
 UNITS = {
     "lbm_api.cu": [],
-    "step.cu": [],
+    "step_f32.cu": [],
+    "step_f16.cu": [],
+    "step_bf16.cu": [],
     "step_f64.cu": ["-fmad=false"],
     "aux.cu": ["-fmad=false"],
     "serve.cu": [],
     "drift_noalloc.cu": [],
 }
-HEADERS = ["lbm_internal.h", "d2q9_pull.cuh", "collide.cuh"]
+HEADERS = ["lbm_internal.h", "d2q9_pull.cuh", "collide.cuh", "step_impl.cuh"]
 
 
 def _newest_input():

@@ -8,8 +8,9 @@
 // pull.
 //
 // Work unit ("task"): one warp covers R = 32 / L rows; in each row L lanes
-// cover L consecutive chunks of V nodes (V * sizeof(T) = 16 bytes).  Every
-// plane is read with aligned 16-byte loads; the +-1 x-shifts are formed from
+// cover L consecutive chunks of V nodes (V * sizeof(T) = 16 bytes, or 8 for
+// the 16-bit types built with LBM_V16=4).  Every plane is read with aligned
+// vector loads; the +-1 x-shifts are formed from
 // the neighbouring lane's chunk by a warp shuffle (width L), and only the two
 // chunks at a segment's ends make one extra scalar load (a cache hit: the
 // neighbouring warp loads the same line).  Periodic wrap is folded into the
@@ -30,11 +31,40 @@ __host__ __device__ constexpr int CYd(int i) {
 }
 
 // ---------------------------------------------------------- element I/O
+// Nodes per vector for the 16-bit storage types: 8 (16-byte vectors) or 4
+// (8-byte vectors, half the registers).
+#ifndef LBM_V16
+#define LBM_V16 8
+#endif
+
+template <int BYTES> struct RawOf;
+template <> struct RawOf<16> {
+  using type = uint4;
+  static __device__ __forceinline__ void words(const uint4 &r, uint32_t *w) {
+    w[0] = r.x; w[1] = r.y; w[2] = r.z; w[3] = r.w;
+  }
+  static __device__ __forceinline__ uint4 make(const uint32_t *w) {
+    return make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  static __device__ __forceinline__ uint4 zero() { return make_uint4(0, 0, 0, 0); }
+};
+template <> struct RawOf<8> {
+  using type = uint2;
+  static __device__ __forceinline__ void words(const uint2 &r, uint32_t *w) {
+    w[0] = r.x; w[1] = r.y;
+  }
+  static __device__ __forceinline__ uint2 make(const uint32_t *w) {
+    return make_uint2(w[0], w[1]);
+  }
+  static __device__ __forceinline__ uint2 zero() { return make_uint2(0, 0); }
+};
+
 template <typename T> struct Elem;
 
 template <> struct Elem<float> {
   static constexpr int V = 4;
   using C = float;  // compute type
+  using R = RawOf<16>;
   static __device__ __forceinline__ void unpack(const uint4 &r, float *o) {
     o[0] = __uint_as_float(r.x); o[1] = __uint_as_float(r.y);
     o[2] = __uint_as_float(r.z); o[3] = __uint_as_float(r.w);
@@ -47,25 +77,27 @@ template <> struct Elem<float> {
 };
 
 template <> struct Elem<__half> {
-  static constexpr int V = 8;
+  static constexpr int V = LBM_V16;
   using C = float;
-  static __device__ __forceinline__ void unpack(const uint4 &r, float *o) {
-    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+  using R = RawOf<2 * V>;
+  static __device__ __forceinline__ void unpack(const typename R::type &r, float *o) {
+    uint32_t w[V / 2];
+    R::words(r, w);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < V / 2; ++k) {
       __half2 h = *reinterpret_cast<const __half2 *>(&w[k]);
       float2 f = __half22float2(h);
       o[2 * k] = f.x; o[2 * k + 1] = f.y;
     }
   }
-  static __device__ __forceinline__ uint4 pack(const float *v) {
-    uint32_t w[4];
+  static __device__ __forceinline__ typename R::type pack(const float *v) {
+    uint32_t w[V / 2];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < V / 2; ++k) {
       __half2 h = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
       w[k] = *reinterpret_cast<uint32_t *>(&h);
     }
-    return make_uint4(w[0], w[1], w[2], w[3]);
+    return R::make(w);
   }
   static __device__ __forceinline__ float one(const __half *p) {
     return __half2float(__ldg(p));
@@ -73,25 +105,27 @@ template <> struct Elem<__half> {
 };
 
 template <> struct Elem<__nv_bfloat16> {
-  static constexpr int V = 8;
+  static constexpr int V = LBM_V16;
   using C = float;
-  static __device__ __forceinline__ void unpack(const uint4 &r, float *o) {
-    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+  using R = RawOf<2 * V>;
+  static __device__ __forceinline__ void unpack(const typename R::type &r, float *o) {
+    uint32_t w[V / 2];
+    R::words(r, w);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      // bf16 -> f32 is exact: the bf16 bits are the high half of the f32
-      o[2 * k] = __uint_as_float(w[k] << 16);
-      o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    for (int k = 0; k < V / 2; ++k) {
+      __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[k]);
+      float2 f = __bfloat1622float2(h);
+      o[2 * k] = f.x; o[2 * k + 1] = f.y;
     }
   }
-  static __device__ __forceinline__ uint4 pack(const float *v) {
-    uint32_t w[4];
+  static __device__ __forceinline__ typename R::type pack(const float *v) {
+    uint32_t w[V / 2];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < V / 2; ++k) {
       __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
       w[k] = *reinterpret_cast<uint32_t *>(&h);
     }
-    return make_uint4(w[0], w[1], w[2], w[3]);
+    return R::make(w);
   }
   static __device__ __forceinline__ float one(const __nv_bfloat16 *p) {
     return __bfloat162float(__ldg(p));
@@ -101,6 +135,7 @@ template <> struct Elem<__nv_bfloat16> {
 template <> struct Elem<double> {
   static constexpr int V = 2;
   using C = double;
+  using R = RawOf<16>;
   static __device__ __forceinline__ void unpack(const uint4 &r, double *o) {
     o[0] = __hiloint2double((int)r.y, (int)r.x);
     o[1] = __hiloint2double((int)r.w, (int)r.z);
@@ -169,7 +204,8 @@ __device__ __forceinline__ void pull9(const T *__restrict__ src, const Geom &g,
   const bool need_wrap = p.active && e_last >= 0;
   auto sc = [&](C a) -> C { return SCALED ? a * inv_scale : a; };
 
-  uint4 raw[9];
+  using RawT = typename Elem<T>::R::type;
+  RawT raw[9];
   C edge[9];
   C wrap0[9];
 #pragma unroll
@@ -178,7 +214,7 @@ __device__ __forceinline__ void pull9(const T *__restrict__ src, const Geom &g,
     int ys = p.y - cy;
     ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
     const T *row = src + (long long)i * g.plane + (long long)ys * g.pitch;
-    raw[i] = p.active ? __ldg(reinterpret_cast<const uint4 *>(row + p.x0)) : make_uint4(0, 0, 0, 0);
+    raw[i] = p.active ? __ldg(reinterpret_cast<const RawT *>(row + p.x0)) : Elem<T>::R::zero();
     edge[i] = C(0);
     wrap0[i] = C(0);
     if (cx == 1) {
@@ -235,7 +271,7 @@ __device__ __forceinline__ void store9(T *__restrict__ dst, const Geom &g, const
 #pragma unroll
     for (int e = 0; e < V; ++e) v[e] = SCALED ? in[i][e] * scale : in[i][e];
     T *row = dst + (long long)i * g.plane + (long long)p.y * g.pitch;
-    *reinterpret_cast<uint4 *>(row + p.x0) = Elem<T>::pack(v);
+    *reinterpret_cast<typename Elem<T>::R::type *>(row + p.x0) = Elem<T>::pack(v);
   }
 }
 

@@ -5,8 +5,12 @@
 #include <math.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -120,6 +124,7 @@ struct lbm_ctx {
   int graph_steps = 0;
   int block = 256;
   int grid_cap = 0;
+  bool tuned = false;
   lbm_batch_ctx *batch = nullptr;
 };
 
@@ -178,11 +183,57 @@ static int free_graph(lbm_ctx *h) {
   return LBM_OK;
 }
 
+// Launch variant used before (or without) tuning, from GB300 measurements:
+// the 80-register cap (3 blocks per SM) is fastest for FP32 and FP16,
+// 128 registers for BF16.
+static int default_variant(int dtype) {
+  return dtype == LBM_BF16DEV ? 1 : 2;
+}
+
+static bool autotune_enabled() {
+  const char *e = getenv("LBM_AUTOTUNE");
+  return !(e && e[0] == '0');
+}
+
+// Tuner results per (dtype, nx, ny), shared by the handles of a process.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, int> g_tune_cache;
+
+// Average duration of `reps` launches produced by `launch(k)` on stream st.
+template <typename F>
+static int time_launches(cudaStream_t st, int reps, F launch, double *ms) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaError_t e = launch(0);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  for (int k = 0; k < reps && e == cudaSuccess; ++k) e = launch(k);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    set_error(std::string("tuning: ") + cudaGetErrorString(e));
+    cudaGetLastError();
+    return LBM_ECUDA;
+  }
+  *ms = t / reps;
+  return LBM_OK;
+}
+
+// repetitions for ~2 ms of traffic per variant at ~6 TB/s
+static int tune_reps(double bytes) {
+  const int r = (int)(2e-3 * 6e12 / std::max(bytes, 1.0));
+  return std::max(2, std::min(200, r));
+}
+
 static cudaError_t launch_one(lbm_ctx *h, int from, cudaStream_t st) {
   const void *src = h->L.buf[from];
   void *dst = h->L.buf[from ^ 1];
   if (h->L.dtype == LBM_F64) return launch_step_f64(h->L, src, dst, st, h->block, h->grid_cap);
-  return launch_step_dev(h->L, src, dst, st, h->block, h->grid_cap);
+  return launch_step_dev(h->L, src, dst, st, h->block, h->L.variant);
 }
 
 // capture `steps` (even) launches starting from buffer 0 into a graph
@@ -226,6 +277,65 @@ static int ensure_stage(lbm_ctx *h) {
 static void split_rate(double v, float &hi, float &lo) {
   hi = (float)v;
   lo = (float)(v - (double)hi);
+}
+
+// Time every launch variant of the step kernel on this lattice and keep the
+// fastest.  Each trial launch reads the current buffer and writes the idle
+// one, so the lattice's state is unchanged.
+static int tune_handle(lbm_ctx *h, double *times) {
+  if (h->L.dtype == LBM_F64) {
+    if (times)
+      for (int v = 0; v < kStepVariants; ++v) times[v] = -1.0;
+    h->tuned = true;
+    return LBM_OK;
+  }
+  const double bytes = (double)h->L.g.nx * h->L.g.ny * 18.0 * h->L.esize;
+  const int reps = tune_reps(bytes);
+  const int from = h->L.cur;
+  double best = 1e300;
+  int bv = h->L.variant;
+  for (int v = 0; v < kStepVariants; ++v) {
+    double ms = 0;
+    int rc = time_launches(h->stream, reps, [&](int) {
+      return launch_step_dev(h->L, h->L.buf[from], h->L.buf[from ^ 1], h->stream, h->block, v);
+    }, &ms);
+    if (rc != LBM_OK) return rc;
+    if (times) times[v] = ms;
+    if (ms < best) {
+      best = ms;
+      bv = v;
+    }
+  }
+  if (bv != h->L.variant) {
+    h->L.variant = bv;
+    free_graph(h);
+  }
+  h->tuned = true;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[std::make_tuple(h->L.dtype, h->L.g.nx, h->L.g.ny)] = bv;
+  return LBM_OK;
+}
+
+// First step of a large lattice: reuse a cached choice or tune now.
+static int maybe_autotune(lbm_ctx *h) {
+  if (h->tuned || h->L.dtype == LBM_F64) return LBM_OK;
+  if ((long long)h->L.g.nx * h->L.g.ny < (1LL << 20) || !autotune_enabled()) {
+    h->tuned = true;
+    return LBM_OK;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(std::make_tuple(h->L.dtype, h->L.g.nx, h->L.g.ny));
+    if (it != g_tune_cache.end()) {
+      if (it->second != h->L.variant) {
+        h->L.variant = it->second;
+        free_graph(h);
+      }
+      h->tuned = true;
+      return LBM_OK;
+    }
+  }
+  return tune_handle(h, nullptr);
 }
 
 static int check_rates(const double S[9]) {
@@ -303,12 +413,13 @@ int lbm_create(int nx, int ny, const double S[9], double rho0, const double u0[2
   REQUIRE(check_rates(S), "rates: non-conserved entries must lie in (0, 2], all finite");
   int esize, V;
   switch (storage_dtype) {
-    case LBM_F64: esize = 8; V = 2; break;
-    case LBM_F32DEV: esize = 4; V = 4; break;
+    case LBM_F64: esize = 8; break;
+    case LBM_F32DEV: esize = 4; break;
     case LBM_F16DEV:
-    case LBM_BF16DEV: esize = 2; V = 8; break;
+    case LBM_BF16DEV: esize = 2; break;
     default: REQUIRE(false, "unknown storage dtype");
   }
+  V = vec_nodes(storage_dtype);
   int dev = 0;
   CK(cudaGetDevice(&dev));
   lbm_ctx *h = new (std::nothrow) lbm_ctx();
@@ -317,6 +428,7 @@ int lbm_create(int nx, int ny, const double S[9], double rho0, const double u0[2
   h->L.g = make_geom(nx, ny, V, esize);
   h->L.dtype = storage_dtype;
   h->L.V = V;
+  h->L.variant = default_variant(storage_dtype);
   h->L.esize = esize;
   h->L.cur = 0;
   // Lallemand-Luo order (rho, e, eps, jx, qx, jy, qy, pxx, pxy) -> paper
@@ -478,6 +590,10 @@ int lbm_step(lbm_handle h, long n) {
   REQUIRE(n >= 0, "negative step count");
   REQUIRE(h->batch == nullptr, "lattice is a batch member; step the batch");
   DevGuard g(h->device);
+  if (n > 0) {
+    int rc = maybe_autotune(h);
+    if (rc != LBM_OK) return rc;
+  }
   const int G = 64;  // steps per captured graph (even)
   while (n > 0) {
     if (h->L.cur == 0 && n >= G) {
@@ -496,6 +612,15 @@ int lbm_step(lbm_handle h, long n) {
     }
   }
   return LBM_OK;
+}
+
+int lbm_tune(lbm_handle h, double *times_ms, int *chosen) {
+  REQUIRE(h != nullptr, "null handle");
+  REQUIRE(h->batch == nullptr, "lattice is a batch member; tune the batch");
+  DevGuard g(h->device);
+  int rc = tune_handle(h, times_ms);
+  if (rc == LBM_OK && chosen) *chosen = h->L.variant;
+  return rc;
 }
 
 int lbm_moments_dev(lbm_handle h, double *rho, double *ux, double *uy) {
@@ -624,15 +749,49 @@ struct lbm_batch_ctx {
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
   int block = 256;
+  int variant = 2;                       // launch variant (tuner)
+  bool tuned = false;
+  long long nodes = 0;
 };
 
-static cudaError_t batch_launch_all(lbm_batch_ctx *b, int parity, cudaStream_t st) {
+static cudaError_t batch_launch_all(lbm_batch_ctx *b, int parity, cudaStream_t st,
+                                    int variant) {
   for (auto &gr : b->groups) {
     cudaError_t e = launch_step_batch(gr.dtype, gr.ents, gr.n, gr.block_first, gr.ntasks, parity,
-                                      st, b->block);
+                                      st, b->block, variant);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// As tune_handle, for the whole batch: trial launches at the current parity
+// write only the idle buffers.
+static int tune_batch(lbm_batch_ctx *b, double *times) {
+  double bytes = 0;
+  for (auto *m : b->members) bytes += (double)m->L.g.nx * m->L.g.ny * 18.0 * m->L.esize;
+  const int reps = tune_reps(bytes);
+  double best = 1e300;
+  int bv = b->variant;
+  for (int v = 0; v < kStepVariants; ++v) {
+    double ms = 0;
+    int rc = time_launches(b->stream, reps,
+                           [&](int) { return batch_launch_all(b, b->parity, b->stream, v); }, &ms);
+    if (rc != LBM_OK) return rc;
+    if (times) times[v] = ms;
+    if (ms < best) {
+      best = ms;
+      bv = v;
+    }
+  }
+  if (bv != b->variant) {
+    b->variant = bv;
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+  }
+  b->tuned = true;
+  return LBM_OK;
 }
 
 static void batch_free(lbm_batch_ctx *b) {
@@ -739,7 +898,11 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
     batch_free(b);
     return LBM_ECUDA;
   }
-  for (auto *m : b->members) b->offs.push_back(m->L.cur);
+  for (auto *m : b->members) {
+    b->offs.push_back(m->L.cur);
+    b->nodes += (long long)m->L.g.nx * m->L.g.ny;
+  }
+  b->variant = default_variant(b->members[0]->L.dtype);
   // drift views of every member for both batch parities
   {
     const int n = (int)b->members.size();
@@ -781,6 +944,13 @@ int lbm_batch_step(lbm_batch b, long n) {
   for (size_t k = 0; k < b->members.size(); ++k)
     REQUIRE(b->members[k]->L.cur == (b->offs[k] ^ b->parity),
             "a member was modified outside the batch");
+  if (n > 0 && !b->tuned) {
+    if (b->nodes >= (1LL << 20) && autotune_enabled()) {
+      int rc = tune_batch(b, nullptr);
+      if (rc != LBM_OK) return rc;
+    }
+    b->tuned = true;
+  }
   const int G = 64;
   long done = 0;
   while (n > 0) {
@@ -791,7 +961,8 @@ int lbm_batch_step(lbm_batch b, long n) {
         cudaGraph_t gr = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-          for (int k = 0; k < G && e == cudaSuccess; ++k) e = batch_launch_all(b, k & 1, cs);
+          for (int k = 0; k < G && e == cudaSuccess; ++k)
+            e = batch_launch_all(b, k & 1, cs, b->variant);
           cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
           if (e == cudaSuccess) e = e2;
         }
@@ -810,7 +981,7 @@ int lbm_batch_step(lbm_batch b, long n) {
       n -= G;
       done += G;
     } else {
-      CK(batch_launch_all(b, b->parity, b->stream));
+      CK(batch_launch_all(b, b->parity, b->stream, b->variant));
       b->parity ^= 1;
       n -= 1;
       done += 1;
@@ -821,6 +992,14 @@ int lbm_batch_step(lbm_batch b, long n) {
     b->members[k]->t += done;
   }
   return LBM_OK;
+}
+
+int lbm_batch_tune(lbm_batch b, double *times_ms, int *chosen) {
+  REQUIRE(b != nullptr, "null batch");
+  DevGuard g(b->device);
+  int rc = tune_batch(b, times_ms);
+  if (rc == LBM_OK && chosen) *chosen = b->variant;
+  return rc;
 }
 
 int lbm_batch_drift(lbm_batch b, double *out) {

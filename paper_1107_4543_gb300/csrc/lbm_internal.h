@@ -14,7 +14,8 @@ namespace lbm {
 struct Lattice {
   Geom g;
   int dtype;
-  int V;             // nodes per 16-byte vector
+  int V;             // nodes per vector (vec_nodes)
+  int variant;       // launch variant of the step kernel (tuner)
   int esize;         // bytes per stored population
   void *buf[2];      // double buffer (each 9 planes)
   int cur;           // buffer holding the current state
@@ -31,14 +32,56 @@ struct BatchEntry {
   long long task0;   // first task of this lattice in the flattened list
 };
 
-// launch helpers (step.cu / step_f64.cu)
-cudaError_t launch_step_dev(const Lattice &L, const void *src, void *dst,
-                            cudaStream_t st, int block, int grid_cap);
+// launch helpers (step_f32.cu, step_f16.cu, step_bf16.cu, step_f64.cu).
+// `variant` selects the register cap of the deviation step kernels
+// (0, 1, 2: at least 1, 2, 3 resident 256-thread blocks per SM).
+constexpr int kStepVariants = 3;
+cudaError_t launch_step_dev_f32(const Lattice &L, const void *src, void *dst, cudaStream_t st,
+                                int block, int variant);
+cudaError_t launch_step_dev_f16(const Lattice &L, const void *src, void *dst, cudaStream_t st,
+                                int block, int variant);
+cudaError_t launch_step_dev_bf16(const Lattice &L, const void *src, void *dst, cudaStream_t st,
+                                 int block, int variant);
+cudaError_t launch_step_batch_f32(const BatchEntry *ents, int n, const int *block_first,
+                                  long long ntasks, int parity, cudaStream_t st, int block,
+                                  int variant);
+cudaError_t launch_step_batch_f16(const BatchEntry *ents, int n, const int *block_first,
+                                  long long ntasks, int parity, cudaStream_t st, int block,
+                                  int variant);
+cudaError_t launch_step_batch_bf16(const BatchEntry *ents, int n, const int *block_first,
+                                   long long ntasks, int parity, cudaStream_t st, int block,
+                                   int variant);
 cudaError_t launch_step_f64(const Lattice &L, const void *src, void *dst,
                             cudaStream_t st, int block, int grid_cap);
-cudaError_t launch_step_batch(int dtype, const BatchEntry *entries_dev, int n,
-                              const int *block_first_dev, long long ntasks,
-                              int parity, cudaStream_t st, int block);
+
+inline cudaError_t launch_step_dev(const Lattice &L, const void *src, void *dst,
+                                   cudaStream_t st, int block, int variant) {
+  switch (L.dtype) {
+    case LBM_F32DEV: return launch_step_dev_f32(L, src, dst, st, block, variant);
+    case LBM_F16DEV: return launch_step_dev_f16(L, src, dst, st, block, variant);
+    case LBM_BF16DEV: return launch_step_dev_bf16(L, src, dst, st, block, variant);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+inline cudaError_t launch_step_batch(int dtype, const BatchEntry *ents, int n,
+                                     const int *block_first, long long ntasks, int parity,
+                                     cudaStream_t st, int block, int variant) {
+  switch (dtype) {
+    case LBM_F32DEV:
+      return launch_step_batch_f32(ents, n, block_first, ntasks, parity, st, block, variant);
+    case LBM_F16DEV:
+      return launch_step_batch_f16(ents, n, block_first, ntasks, parity, st, block, variant);
+    case LBM_BF16DEV:
+      return launch_step_batch_bf16(ents, n, block_first, ntasks, parity, st, block, variant);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Nodes per vector of a storage type (host side of d2q9_pull.cuh's Elem).
+inline int vec_nodes(int dtype) {
+  return dtype == LBM_F64 ? 2 : (dtype == LBM_F32DEV ? 4 : LBM_V16);
+}
 
 // aux kernels (aux.cu)
 struct AuxView {

@@ -57,7 +57,7 @@ struct Req {
 
 size_t estimate_bytes(const lbm_request &r) {
   int esize = r.dtype == LBM_F32DEV ? 4 : 2;
-  int V = r.dtype == LBM_F32DEV ? 4 : 8;
+  int V = vec_nodes(r.dtype);
   int align = std::max(V, 128 / esize);
   size_t pitch = (size_t)((r.nx + align - 1) / align * align);
   return 2 * pitch * (size_t)r.ny * 9 * esize + 64 * 1024;

@@ -1,0 +1,17 @@
+// Step kernels for one storage type (__half); see step_impl.cuh.
+#include "step_impl.cuh"
+
+namespace lbm {
+
+cudaError_t launch_step_dev_f16(const Lattice &L, const void *src, void *dst, cudaStream_t st,
+                              int block, int variant) {
+  return launch_step_dev_t<__half>(L, src, dst, st, block, variant);
+}
+
+cudaError_t launch_step_batch_f16(const BatchEntry *ents, int n, const int *block_first,
+                                long long ntasks, int parity, cudaStream_t st, int block,
+                                int variant) {
+  return launch_step_batch_t<__half>(ents, n, block_first, ntasks, parity, st, block, variant);
+}
+
+}  // namespace lbm

@@ -1,5 +1,7 @@
 // Fused pull-stream + MRT collide step for the deviation storage types
 // (FP32, FP16 scaled, BF16; FP32 collision), single lattice and batched.
+// Template implementation; step_f32.cu, step_f16.cu and step_bf16.cu each
+// instantiate one storage type (parallel compilation).
 //
 // One time step of section 2.1 (Eq. blbs) per launch: each warp task pulls
 // the 9 populations of 32 x V nodes with 16-byte loads, collides them in
@@ -7,14 +9,10 @@
 // the kernel moves 9 reads + 9 writes of one stored population (72 B in
 // FP32, 36 B in FP16/BF16): an HBM-bound stream with ~110 FP32 operations
 // per node.
+#pragma once
 #include <type_traits>
 
 #include "lbm_internal.h"
-
-// Minimum resident blocks per SM asked of the compiler (caps registers).
-#ifndef LBM_DEV_MINB
-#define LBM_DEV_MINB 1
-#endif
 
 namespace lbm {
 
@@ -34,8 +32,11 @@ __device__ __forceinline__ void step_task(const T *__restrict__ src, T *__restri
   store9<T, SCALED>(dst, g, p, P.scale, f);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256, LBM_DEV_MINB)
+// MINB: minimum resident 256-thread blocks per SM asked of the compiler,
+// i.e. a register cap (1: none, 2: 128, 3: 80 registers).  The launch
+// variants of the tuner are MINB = 1, 2, 3.
+template <typename T, int MINB>
+__global__ void __launch_bounds__(256, MINB)
 k_step_dev(const T *__restrict__ src, T *__restrict__ dst, Geom g, DevParams P,
            long long ntasks) {
   const int lane = threadIdx.x & 31;
@@ -48,8 +49,8 @@ k_step_dev(const T *__restrict__ src, T *__restrict__ dst, Geom g, DevParams P,
 // Batched: tasks of all lattices flattened; block b starts its lookup at
 // lattice block_first[b] (blocks cover consecutive tasks, so a warp walks
 // forward at most a few entries).
-template <typename T>
-__global__ void __launch_bounds__(256, LBM_DEV_MINB)
+template <typename T, int MINB>
+__global__ void __launch_bounds__(256, MINB)
 k_step_batch(const BatchEntry *__restrict__ ents, int n, const int *__restrict__ block_first,
              long long ntasks, int parity) {
   const int lane = threadIdx.x & 31;
@@ -64,52 +65,42 @@ k_step_batch(const BatchEntry *__restrict__ ents, int n, const int *__restrict__
   step_task<T>(src, dst, E.g, E.dp, task - E.task0, lane);
 }
 
-static long long n_tasks(const Geom &g) { return (long long)g.rgroups * g.nseg; }
+static inline long long n_tasks(const Geom &g) { return (long long)g.rgroups * g.nseg; }
 
-cudaError_t launch_step_dev(const Lattice &L, const void *src, void *dst, cudaStream_t st,
-                            int block, int grid_cap) {
+template <typename T>
+cudaError_t launch_step_dev_t(const Lattice &L, const void *src, void *dst, cudaStream_t st,
+                              int block, int variant) {
   const long long nt = n_tasks(L.g);
   const int wpb = block / 32;
   long long grid = (nt + wpb - 1) / wpb;
-  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
   if (grid < 1) grid = 1;
-  switch (L.dtype) {
-    case LBM_F32DEV:
-      k_step_dev<float><<<(unsigned)grid, block, 0, st>>>(
-          (const float *)src, (float *)dst, L.g, L.dp, nt);
-      break;
-    case LBM_F16DEV:
-      k_step_dev<__half><<<(unsigned)grid, block, 0, st>>>(
-          (const __half *)src, (__half *)dst, L.g, L.dp, nt);
-      break;
-    case LBM_BF16DEV:
-      k_step_dev<__nv_bfloat16><<<(unsigned)grid, block, 0, st>>>(
-          (const __nv_bfloat16 *)src, (__nv_bfloat16 *)dst, L.g, L.dp, nt);
-      break;
-    default:
-      return cudaErrorInvalidValue;
+  const T *s = static_cast<const T *>(src);
+  T *d = static_cast<T *>(dst);
+  switch (variant) {
+    case 0: k_step_dev<T, 1><<<(unsigned)grid, block, 0, st>>>(s, d, L.g, L.dp, nt); break;
+    case 1: k_step_dev<T, 2><<<(unsigned)grid, block, 0, st>>>(s, d, L.g, L.dp, nt); break;
+    default: k_step_dev<T, 3><<<(unsigned)grid, block, 0, st>>>(s, d, L.g, L.dp, nt); break;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_step_batch(int dtype, const BatchEntry *ents, int n, const int *block_first,
-                              long long ntasks, int parity, cudaStream_t st, int block) {
+template <typename T>
+cudaError_t launch_step_batch_t(const BatchEntry *ents, int n, const int *block_first,
+                                long long ntasks, int parity, cudaStream_t st, int block,
+                                int variant) {
   const int wpb = block / 32;
   const long long grid = (ntasks + wpb - 1) / wpb;
   if (grid < 1) return cudaSuccess;
-  switch (dtype) {
-    case LBM_F32DEV:
-      k_step_batch<float><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity);
+  switch (variant) {
+    case 0:
+      k_step_batch<T, 1><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity);
       break;
-    case LBM_F16DEV:
-      k_step_batch<__half><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity);
-      break;
-    case LBM_BF16DEV:
-      k_step_batch<__nv_bfloat16><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks,
-                                                                      parity);
+    case 1:
+      k_step_batch<T, 2><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity);
       break;
     default:
-      return cudaErrorInvalidValue;
+      k_step_batch<T, 3><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity);
+      break;
   }
   return cudaGetLastError();
 }

@@ -56,6 +56,8 @@ _SIGS = {
     "lbm_init_field_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lbm_init_analytic": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
     "lbm_step": (ctypes.c_int, [_vp, ctypes.c_long]),
+    "lbm_tune": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_tune": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_int)]),
     "lbm_moments": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
     "lbm_moments_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lbm_destroy": (ctypes.c_int, [_vp]),
@@ -185,6 +187,24 @@ def lbm_init_analytic(h, kind, params):
 
 def lbm_step(h, n):
     _ck(load().lbm_step(h, int(n)), "lbm_step")
+
+
+LBM_TUNE_VARIANTS = 3
+
+
+def lbm_tune(h):
+    """(times_ms per launch variant, chosen variant)."""
+    t = np.zeros(LBM_TUNE_VARIANTS)
+    c = ctypes.c_int()
+    _ck(load().lbm_tune(h, _ptr(t), ctypes.byref(c)), "lbm_tune")
+    return t, c.value
+
+
+def lbm_batch_tune(b):
+    t = np.zeros(LBM_TUNE_VARIANTS)
+    c = ctypes.c_int()
+    _ck(load().lbm_batch_tune(b, _ptr(t), ctypes.byref(c)), "lbm_batch_tune")
+    return t, c.value
 
 
 def lbm_moments(h, out=None):

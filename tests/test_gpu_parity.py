@@ -260,6 +260,32 @@ def test_invalid_arguments_are_rejected(L):
         L.lbm_destroy(h)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_tuning_leaves_state_unchanged(L, dtype):
+    """Trial launches of the tuner write only the idle buffer; every launch
+    variant then gives the same populations."""
+    nx, ny = 300, 70
+    r = inp.rates("OPT")
+    h = L.lbm_create(nx, ny, inp.s_ll(r), 1.0, (0.0, 0.0), L.DTYPES[dtype])
+    g = L.lbm_create(nx, ny, inp.s_ll(r), 1.0, (0.0, 0.0), L.DTYPES[dtype])
+    try:
+        fields = inp.gaussian_pulse(nx, ny, 1e-3, 6.0)
+        L.lbm_init_field(h, *fields)
+        L.lbm_init_field(g, *fields)
+        L.lbm_step(h, 5)
+        L.lbm_step(g, 5)
+        before = L.lbm_get_populations(h)
+        times, chosen = L.lbm_tune(h)
+        assert np.all(times > 0) and 0 <= chosen < L.LBM_TUNE_VARIANTS
+        assert np.array_equal(before, L.lbm_get_populations(h))
+        L.lbm_step(h, 9)
+        L.lbm_step(g, 9)
+        assert np.array_equal(L.lbm_get_populations(h), L.lbm_get_populations(g))
+    finally:
+        L.lbm_destroy(h)
+        L.lbm_destroy(g)
+
+
 def test_analytic_init_matches_host_fields(L):
     """The device-side Gaussian initial field equals the host recipe to
     rounding (exp evaluated on different machines)."""
