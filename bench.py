@@ -69,6 +69,40 @@ def dist():
     return ws, rank, local
 
 
+def rank_specs(args, rank):
+    """The lattices of one rank: the whole 512-lattice workload, seeded per
+    rank (weak scaling: each GPU steps its own independent batch, and no
+    data crosses ranks)."""
+    return inp.batch_specs(args.lattices, seed=1107 + 4 + 1000 * rank, steps=args.lbm_steps)
+
+
+def reduce_max(x, device="cuda"):
+    """Max of a float over the ranks (the timing rule: the slowest rank)."""
+    import torch
+
+    if not torch.distributed.is_initialized() or torch.distributed.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, device="cuda"):
+    """Sum of a float over the ranks."""
+    import torch
+
+    if not torch.distributed.is_initialized() or torch.distributed.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_mlups(units_all_ranks, seconds):
+    """Whole-job throughput: the units all ranks processed over the max time."""
+    return units_all_ranks / seconds / 1e6
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -230,7 +264,7 @@ def fp64_plain(L, torch, stream, n=8192, steps=20):
 def bench_batched(args, L, torch, rank, ws):
     dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream()
-    specs = inp.batch_specs(args.lattices, seed=1107 + 4 + 1000 * rank, steps=args.lbm_steps)
+    specs = rank_specs(args, rank)
     hs, fields = setup_batch(L, torch, specs, "f32", stream)
     nodes = sum(s["nx"] * s["ny"] for s in specs)
     b = L.lbm_batch_create(hs)
@@ -259,13 +293,12 @@ def bench_batched(args, L, torch, rank, ws):
     clk = clocks.stop()
     total_ms = ev[0].elapsed_time(ev[-1])
     step_ms = [ev[2 * k + 1].elapsed_time(ev[2 * k + 2]) for k in range(args.steps)]
+    total_ms = reduce_max(total_ms)
     if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
     lu_per_step = nodes * lbm_steps
-    value = ws * lu_per_step * args.steps / (total_ms * 1e-3) / 1e6
+    lu_job = reduce_sum(lu_per_step * args.steps)  # every rank's lattice updates
+    value = job_mlups(lu_job, total_ms * 1e-3)
     launch_ms = float(np.mean(step_ms)) / lbm_steps  # one batched kernel per time step
     launches = args.steps * (lbm_steps + 2)  # batched steps + one drift launch pair
 
@@ -297,12 +330,8 @@ def bench_batched(args, L, torch, rank, ws):
     for _ in range(args.steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = ws * lu_per_step * args.steps / e2e_s / 1e6
+    e2e_s = reduce_max(time.perf_counter() - t0)
+    e2e_value = job_mlups(lu_job, e2e_s)
     h2d = 3 * 8 * nodes
     d2h = 3 * 8 * nodes
 
@@ -406,7 +435,7 @@ def bench_serving(args, L, torch):
             k += 1
         done = []
         for rid, q in pending.items():
-            rc, _, _, _, latency = L.lbm_poll(srv, rid, q["nx"], q["ny"])
+            rc, _, _, _, latency = L.lbm_poll(srv, rid)
             if rc == L.LBM_OK:
                 lat.append(latency)
                 done.append(rid)

@@ -7,14 +7,13 @@
 // y - cy_i): the collide-then-stream of section 2.1 (Eq. blbs) written as a
 // pull.
 //
-// Work unit ("task"): one warp covers R = 32 / L rows; in each row L lanes
-// cover L consecutive chunks of V nodes (V * sizeof(T) = 16 bytes, or 8 for
-// the 16-bit types built with LBM_V16=4).  Every plane is read with aligned
-// vector loads; the +-1 x-shifts are formed from
-// the neighbouring lane's chunk by a warp shuffle (width L), and only the two
-// chunks at a segment's ends make one extra scalar load (a cache hit: the
-// neighbouring warp loads the same line).  Periodic wrap is folded into the
-// row index (y) and into those edge loads (x).
+// Work unit ("task"): one warp takes 32 consecutive chunks of V nodes
+// (V * sizeof(T) = 16 bytes, or 8 bytes for BF16); see lane_pos.  Every plane is read with aligned vector loads;
+// the +-1 x-shifts are formed from the neighbouring lane's chunk by a warp
+// shuffle, and only lanes whose neighbouring chunk is elsewhere make one
+// extra scalar load (a cache hit: the neighbouring warp or row loads the
+// same line).  Periodic wrap is folded into the row index (y) and into
+// those edge loads (x).
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -32,9 +31,13 @@ __host__ __device__ constexpr int CYd(int i) {
 
 // ---------------------------------------------------------- element I/O
 // Nodes per vector for the 16-bit storage types: 8 (16-byte vectors) or 4
-// (8-byte vectors, half the registers).
-#ifndef LBM_V16
-#define LBM_V16 8
+// (8-byte vectors, half the registers).  Measured on GB300: FP16 streams
+// fastest with 8, BF16 (whose 8-wide kernel needs ~180 registers) with 4.
+#ifndef LBM_VF16
+#define LBM_VF16 8
+#endif
+#ifndef LBM_VBF16
+#define LBM_VBF16 4
 #endif
 
 template <int BYTES> struct RawOf;
@@ -77,7 +80,7 @@ template <> struct Elem<float> {
 };
 
 template <> struct Elem<__half> {
-  static constexpr int V = LBM_V16;
+  static constexpr int V = LBM_VF16;
   using C = float;
   using R = RawOf<2 * V>;
   static __device__ __forceinline__ void unpack(const typename R::type &r, float *o) {
@@ -105,7 +108,7 @@ template <> struct Elem<__half> {
 };
 
 template <> struct Elem<__nv_bfloat16> {
-  static constexpr int V = LBM_V16;
+  static constexpr int V = LBM_VBF16;
   using C = float;
   using R = RawOf<2 * V>;
   static __device__ __forceinline__ void unpack(const typename R::type &r, float *o) {
@@ -147,31 +150,37 @@ template <> struct Elem<double> {
   static __device__ __forceinline__ double one(const double *p) { return __ldg(p); }
 };
 
+// Work mapping: the lattice's rows of ceil(nx / V) chunks form one row-major
+// sequence of chunks and warp task k takes chunks 32k .. 32k+31, so every
+// lane has work whatever nx is (a warp may span rows); a lane whose
+// neighbouring chunk lies in another row loads the edge element itself.
+
 // geometry of one lattice as the step kernels see it
 struct Geom {
   int nx, ny, pitch;
-  int L;       // lanes per row segment (4, 8, 16 or 32)
-  int nseg;    // segments per row: ceil(ceil(nx / V) / L)
-  int rgroups; // row groups: ceil(ny / (32 / L))
+  int nchunks;      // vectors per row: ceil(nx / V)
   long long plane;  // pitch * ny
+  long long tasks;  // warp tasks per step: ceil(nchunks * ny / 32)
 };
 
 // Position of this lane for task `task` of a lattice.
 struct LanePos {
-  int y, x0, lseg;  // row, first node of the chunk, lane index in segment
-  bool active;      // chunk holds at least one real node of a real row
+  int y, x0;         // row, first node of the chunk
+  bool first, last;  // the row's previous / next chunk is not in the previous / next lane
+  bool active;       // the chunk exists (task * 32 + lane < nchunks * ny)
 };
 
 template <int V>
 __device__ __forceinline__ LanePos lane_pos(const Geom &g, long long task, int lane) {
   LanePos p;
-  int rows_per_warp = 32 / g.L;
-  int seg = (int)(task % g.nseg);
-  int rg = (int)(task / g.nseg);
-  p.lseg = lane & (g.L - 1);
-  p.y = rg * rows_per_warp + lane / g.L;
-  p.x0 = (seg * g.L + p.lseg) * V;
-  p.active = (p.y < g.ny) && (p.x0 < g.nx);
+  const long long c = task * 32 + lane;
+  p.active = c < (long long)g.nchunks * g.ny;
+  const int y = p.active ? (int)(c / g.nchunks) : 0;
+  const int xc = p.active ? (int)(c - (long long)y * g.nchunks) : 0;
+  p.y = y;
+  p.x0 = xc * V;
+  p.first = lane == 0 || xc == 0;
+  p.last = lane == 31 || xc + 1 == g.nchunks;
   return p;
 }
 
@@ -191,16 +200,16 @@ __device__ __forceinline__ void pull9(const T *__restrict__ src, const Geom &g,
                                       typename Elem<T>::C (&out)[9][Elem<T>::V]) {
   using C = typename Elem<T>::C;
   constexpr int V = Elem<T>::V;
-  const int L = g.L;
   const int last = g.nx - 1;
   // which element of this chunk is the last real node (or -1)
   const int e_last = (p.x0 <= last && last < p.x0 + V) ? last - p.x0 : -1;
-  // edge loads: the first lane of a segment (or x0 = 0) needs x0 - 1 for the
-  // planes with cx = +1; the last lane needs x0 + V for cx = -1; the chunk
+  // edge loads: a lane whose previous chunk is not in the previous lane (or
+  // x0 = 0, the wrap) needs x0 - 1 for the planes with cx = +1; one whose
+  // next chunk is not in the next lane needs x0 + V for cx = -1; the chunk
   // holding the last node needs column 0 for cx = -1
-  const bool need_prev = p.active && (p.lseg == 0 || p.x0 == 0);
+  const bool need_prev = p.active && p.first;
   const int x_prev = p.x0 == 0 ? last : p.x0 - 1;
-  const bool need_next = p.active && p.lseg == L - 1 && p.x0 + V <= last;
+  const bool need_next = p.active && p.last && p.x0 + V <= last;
   const bool need_wrap = p.active && e_last >= 0;
   auto sc = [&](C a) -> C { return SCALED ? a * inv_scale : a; };
 
@@ -234,14 +243,14 @@ __device__ __forceinline__ void pull9(const T *__restrict__ src, const Geom &g,
       for (int e = 0; e < V; ++e) out[i][e] = sc(v[e]);
     } else if (cx == 1) {
       // node x pulls from x - 1
-      C prev = __shfl_up_sync(0xffffffffu, v[V - 1], 1, L);
+      C prev = __shfl_up_sync(0xffffffffu, v[V - 1], 1);
       if (need_prev) prev = edge[i];
       out[i][0] = sc(prev);
 #pragma unroll
       for (int e = 1; e < V; ++e) out[i][e] = sc(v[e - 1]);
     } else {
       // node x pulls from x + 1 (column 0 for the last real node)
-      C next = __shfl_down_sync(0xffffffffu, v[0], 1, L);
+      C next = __shfl_down_sync(0xffffffffu, v[0], 1);
       if (need_next) next = edge[i];
 #pragma unroll
       for (int e = 0; e < V - 1; ++e) out[i][e] = sc(v[e + 1]);

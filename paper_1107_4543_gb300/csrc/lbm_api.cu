@@ -70,26 +70,15 @@ int sm_count() {
   return n;
 }
 
-// Lanes per row segment: the smallest power of two covering the row's
-// 16-byte chunks, at most a warp.
-static int lanes_for(int nchunks) {
-  int L = 1;
-  while (L < nchunks && L < 32) L <<= 1;
-  return L;
-}
-
 static Geom make_geom(int nx, int ny, int V, int esize) {
   Geom g;
   g.nx = nx;
   g.ny = ny;
   const int align = std::max(V, 128 / esize);  // rows start on 128-byte lines
   g.pitch = (nx + align - 1) / align * align;
-  const int nchunks = (nx + V - 1) / V;
-  g.L = lanes_for(nchunks);
-  g.nseg = (nchunks + g.L - 1) / g.L;
-  const int rows_per_warp = 32 / g.L;
-  g.rgroups = (ny + rows_per_warp - 1) / rows_per_warp;
+  g.nchunks = (nx + V - 1) / V;
   g.plane = (long long)g.pitch * ny;
+  g.tasks = ((long long)g.nchunks * ny + 31) / 32;
   return g;
 }
 
@@ -794,6 +783,22 @@ static int tune_batch(lbm_batch_ctx *b, double *times) {
   return LBM_OK;
 }
 
+namespace lbm {
+// Pin a batch's launch variant (no automatic tuning); -1 leaves it to the
+// tuner.  Used by the server, which tunes once and reuses the choice.
+void batch_pin_variant(lbm_batch_ctx *b, int variant) {
+  if (variant < 0 || variant >= kStepVariants) return;
+  if (b->variant != variant && b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->variant = variant;
+  b->tuned = true;
+}
+int batch_variant(const lbm_batch_ctx *b) { return b->tuned ? b->variant : -1; }
+long long batch_nodes(const lbm_batch_ctx *b) { return b->nodes; }
+}  // namespace lbm
+
 static void batch_free(lbm_batch_ctx *b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (auto &gr : b->groups) {
@@ -858,7 +863,7 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
       e.buf[1] = m->L.buf[1];
       e.off = m->L.cur;
       e.task0 = t0;
-      t0 += (long long)m->L.g.rgroups * m->L.g.nseg;
+      t0 += m->L.g.tasks;
       ents.push_back(e);
     }
     if (ents.empty()) continue;
@@ -993,6 +998,7 @@ int lbm_batch_step(lbm_batch b, long n) {
   }
   return LBM_OK;
 }
+
 
 int lbm_batch_tune(lbm_batch b, double *times_ms, int *chosen) {
   REQUIRE(b != nullptr, "null batch");

@@ -80,7 +80,9 @@ inline cudaError_t launch_step_batch(int dtype, const BatchEntry *ents, int n,
 
 // Nodes per vector of a storage type (host side of d2q9_pull.cuh's Elem).
 inline int vec_nodes(int dtype) {
-  return dtype == LBM_F64 ? 2 : (dtype == LBM_F32DEV ? 4 : LBM_V16);
+  return dtype == LBM_F64 ? 2
+         : dtype == LBM_F32DEV ? 4
+         : dtype == LBM_F16DEV ? LBM_VF16 : LBM_VBF16;
 }
 
 // aux kernels (aux.cu)
@@ -113,6 +115,11 @@ cudaError_t launch_batch_drift(const AuxView *views_dev, int n, double *partials
 
 // base populations f^eq(rho0, j0) on the host, in the canonical FP64 order
 void host_feq_j(double rho, double jx, double jy, double out[9]);
+
+// batch launch-variant control (lbm_api.cu), for the server
+void batch_pin_variant(lbm_batch_ctx *b, int variant);
+int batch_variant(const lbm_batch_ctx *b);
+long long batch_nodes(const lbm_batch_ctx *b);
 
 // device memory through the configurable allocator
 void *dev_alloc(size_t bytes);

@@ -81,6 +81,7 @@ struct lbm_server_ctx {
   double *stage = nullptr;  // 3 * max nodes doubles, for fields in and moments out
   size_t stage_nodes = 0;
   lbm_server_stats_t st{};
+  int variant = -1;  // step launch variant, tuned on the first large generation
 };
 
 static int ensure_server_stage(lbm_server_ctx *s, size_t nodes) {
@@ -210,7 +211,11 @@ static void worker_loop(lbm_server_ctx *s) {
       lbm_batch b = nullptr;
       rc = lbm_batch_create((int)hs.size(), hs.data(), &b);
       if (rc == LBM_OK) {
+        // tune once, on the first generation large enough to be tuned, and
+        // keep that choice for every later generation
+        if (s->variant >= 0) batch_pin_variant(b, s->variant);
         rc = lbm_batch_step(b, n);
+        if (s->variant < 0 && batch_nodes(b) >= (1LL << 20)) s->variant = batch_variant(b);
         lbm_batch_destroy(b);
       }
     }

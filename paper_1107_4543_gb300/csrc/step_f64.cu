@@ -36,7 +36,7 @@ k_step_f64(const double *__restrict__ src, double *__restrict__ dst, Geom g, F64
 
 cudaError_t launch_step_f64(const Lattice &L, const void *src, void *dst, cudaStream_t st,
                             int block, int grid_cap) {
-  const long long nt = (long long)L.g.rgroups * L.g.nseg;
+  const long long nt = L.g.tasks;
   const int wpb = block / 32;
   long long grid = (nt + wpb - 1) / wpb;
   if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;

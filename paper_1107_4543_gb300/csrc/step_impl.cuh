@@ -65,7 +65,7 @@ k_step_batch(const BatchEntry *__restrict__ ents, int n, const int *__restrict__
   step_task<T>(src, dst, E.g, E.dp, task - E.task0, lane);
 }
 
-static inline long long n_tasks(const Geom &g) { return (long long)g.rgroups * g.nseg; }
+static inline long long n_tasks(const Geom &g) { return g.tasks; }
 
 template <typename T>
 cudaError_t launch_step_dev_t(const Lattice &L, const void *src, void *dst, cudaStream_t st,

@@ -334,15 +334,22 @@ def lbm_submit(s, req):
     return rid.value
 
 
-def lbm_poll(s, rid, nx, ny):
-    """(code, rho, ux, uy, latency_s); arrays are None unless code == LBM_OK."""
-    rho, ux, uy = (np.empty((ny, nx)) for _ in range(3))
+def lbm_poll(s, rid, nx=None, ny=None):
+    """(code, rho, ux, uy, latency_s).  With nx, ny the finished fields are
+    returned as (ny, nx) arrays; without them they are discarded.  Arrays are
+    None unless code == LBM_OK."""
     lat = ctypes.c_double()
-    rc = load().lbm_poll(s, ctypes.c_longlong(rid), _ptr(rho), _ptr(ux), _ptr(uy),
-                         ctypes.byref(lat))
-    if rc == LBM_OK:
-        return rc, rho, ux, uy, lat.value
-    if rc in (LBM_PENDING,):
+    if nx is None:
+        rc = load().lbm_poll(s, ctypes.c_longlong(rid), None, None, None, ctypes.byref(lat))
+        if rc == LBM_OK:
+            return rc, None, None, None, lat.value
+    else:
+        rho, ux, uy = (np.empty((ny, nx)) for _ in range(3))
+        rc = load().lbm_poll(s, ctypes.c_longlong(rid), _ptr(rho), _ptr(ux), _ptr(uy),
+                             ctypes.byref(lat))
+        if rc == LBM_OK:
+            return rc, rho, ux, uy, lat.value
+    if rc == LBM_PENDING:
         return rc, None, None, None, None
     raise LbmError(rc, "lbm_poll")
 
