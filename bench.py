@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--requests", type=int, default=10000)
+    p.add_argument("--policy", default="fifo", choices=["fifo", "shortest"])
+    p.add_argument("--max-nodes", type=int, default=0, help="server resident-node cap")
     p.add_argument("--size", type=int, default=8192, help="side of the large lattice")
     p.add_argument("--dtypes", default="f32,f16,bf16,f64", help="storage types (large)")
     return p.parse_args()
@@ -415,6 +417,8 @@ def bench_serving(args, L, torch):
     """Poisson request stream through lbm_submit / lbm_poll."""
     reqs = inp.request_stream(args.requests, seed=1107 + 5)
     srv = L.lbm_server_create(150 * 10**9, 100)
+    L.lbm_server_set_policy(srv, L.LBM_SERVE_SHORTEST if args.policy == "shortest"
+                            else L.LBM_SERVE_FIFO, args.max_nodes)
     ids = {}
     t0 = time.perf_counter()
     k = 0
@@ -448,7 +452,9 @@ def bench_serving(args, L, torch):
     lu = sum(q["nx"] * q["ny"] * q["steps"] for q in reqs)
     return {"metric": "served MLUPS and solve latency", "value": round(lu / wall / 1e6, 1),
             "unit": "MLUPS", "higher_is_better": True,
-            "config": {"workload": "serving-poisson-%d-requests" % len(reqs)},
+            "config": {"workload": "serving-poisson-%d-requests" % len(reqs),
+                       "policy": args.policy, "max_resident_nodes": args.max_nodes,
+                       "hbm_budget_gb": 150, "chunk_steps": 100},
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "server": st}
 

@@ -260,12 +260,28 @@ typedef struct lbm_server_ctx *lbm_server;
 
 /* A continuous-batching server on the current device: a host scheduler
  * thread admits queued requests while their device bytes fit in
- * hbm_budget_bytes, steps all admitted lattices together in generations of
- * at most chunk_steps steps (one batched launch per step), retires finished
- * lattices (moments copied to host, memory freed) and admits newcomers
- * between generations.  Thread-safe. */
+ * hbm_budget_bytes (see lbm_server_set_policy for order and caps), steps
+ * all admitted lattices together in generations of at most chunk_steps
+ * steps (one batched launch per step and storage type; each lattice stops
+ * at its own step count), retires finished lattices (moments copied to
+ * host, memory freed) and admits newcomers between generations.  Every
+ * result equals the same solve run alone.  Thread-safe. */
 int lbm_server_create(size_t hbm_budget_bytes, long chunk_steps,
                       lbm_server *out);
+
+/* Admission order and resident-work cap of a server:
+ *   LBM_SERVE_FIFO      requests are admitted in arrival order (default);
+ *   LBM_SERVE_SHORTEST  the queued request with the least work
+ *                       (nx * ny * steps) is admitted first;
+ *   max_resident_nodes  > 0: admit only while the resident lattices hold at
+ *                       most this many nodes (one request is always
+ *                       admitted when the device is empty); 0: the byte
+ *                       budget alone limits admission.
+ * A cap keeps generations short -- every resident lattice advances in each
+ * generation -- while enough work stays resident to saturate the GPU. */
+#define LBM_SERVE_FIFO 0
+#define LBM_SERVE_SHORTEST 1
+int lbm_server_set_policy(lbm_server s, int policy, long long max_resident_nodes);
 
 /* Queue a request; never waits for the GPU.  *id identifies it.
  * Errors: LBM_EINVAL (bad request), LBM_ENOMEM (the request alone exceeds

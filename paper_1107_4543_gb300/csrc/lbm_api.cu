@@ -728,7 +728,10 @@ struct lbm_batch_ctx {
     long long ntasks;
     BatchEntry *ents = nullptr;
     int *block_first = nullptr;
+    int *limits = nullptr;  // per-entry step limits of a ragged generation
   };
+  std::vector<int> member_group, member_local;  // member -> (group, entry)
+  bool spent = false;  // a ragged generation ran: members' parities differ
   std::vector<Group> groups;
   std::vector<int> offs;                 // member buffer index at creation
   std::vector<cudaStream_t> saved_streams;
@@ -796,6 +799,43 @@ void batch_pin_variant(lbm_batch_ctx *b, int variant) {
   b->tuned = true;
 }
 int batch_variant(const lbm_batch_ctx *b) { return b->tuned ? b->variant : -1; }
+
+int batch_step_ragged(lbm_batch_ctx *b, const long *steps, long n) {
+  REQUIRE(b != nullptr && steps != nullptr && n >= 0, "bad ragged step arguments");
+  REQUIRE(!b->spent && b->parity == 0, "ragged steps need a fresh batch");
+  REQUIRE(n <= 0x3fffffffL, "too many steps for one generation");
+  DevGuard g(b->device);
+  if (n > 0 && !b->tuned) {
+    if (b->nodes >= (1LL << 20) && autotune_enabled()) {
+      int rc = tune_batch(b, nullptr);
+      if (rc != LBM_OK) return rc;
+    }
+    b->tuned = true;
+  }
+  const size_t nm = b->members.size();
+  std::vector<std::vector<int>> lim(b->groups.size());
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) lim[gi].assign(b->groups[gi].n, 0);
+  std::vector<long> take(nm);
+  for (size_t mi = 0; mi < nm; ++mi) {
+    take[mi] = std::max(0L, std::min(steps[mi], n));
+    lim[b->member_group[mi]][b->member_local[mi]] = (int)take[mi];
+  }
+  for (size_t gi = 0; gi < b->groups.size(); ++gi)
+    CK(cudaMemcpyAsync(b->groups[gi].limits, lim[gi].data(), sizeof(int) * lim[gi].size(),
+                       cudaMemcpyHostToDevice, b->stream));
+  for (long k = 0; k < n; ++k)
+    for (auto &gr : b->groups)
+      CK(launch_step_batch(gr.dtype, gr.ents, gr.n, gr.block_first, gr.ntasks, (int)(k & 1),
+                           b->stream, b->block, b->variant, gr.limits, (int)k));
+  for (size_t mi = 0; mi < nm; ++mi) {
+    b->members[mi]->L.cur = b->offs[mi] ^ (int)(take[mi] & 1);
+    b->members[mi]->t += take[mi];
+  }
+  b->spent = true;
+  // the host arrays above must outlive the copies
+  CK(cudaStreamSynchronize(b->stream));
+  return LBM_OK;
+}
 long long batch_nodes(const lbm_batch_ctx *b) { return b->nodes; }
 }  // namespace lbm
 
@@ -804,6 +844,7 @@ static void batch_free(lbm_batch_ctx *b) {
   for (auto &gr : b->groups) {
     dev_free(gr.ents);
     dev_free(gr.block_first);
+    dev_free(gr.limits);
   }
   dev_free(b->views[0]);
   dev_free(b->views[1]);
@@ -851,11 +892,16 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
     m->stream = b->stream;
   }
   const int wpb = b->block / 32;
+  b->member_group.assign(b->members.size(), -1);
+  b->member_local.assign(b->members.size(), -1);
   for (int dt : {LBM_F32DEV, LBM_F16DEV, LBM_BF16DEV}) {
     std::vector<BatchEntry> ents;
     long long t0 = 0;
-    for (auto *m : b->members) {
+    for (size_t mi = 0; mi < b->members.size(); ++mi) {
+      auto *m = b->members[mi];
       if (m->L.dtype != dt) continue;
+      b->member_group[mi] = (int)b->groups.size();
+      b->member_local[mi] = (int)ents.size();
       BatchEntry e;
       e.g = m->L.g;
       e.dp = m->L.dp;
@@ -881,8 +927,9 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
     }
     gr.ents = (BatchEntry *)dev_alloc(sizeof(BatchEntry) * ents.size());
     gr.block_first = (int *)dev_alloc(sizeof(int) * bf.size());
+    gr.limits = (int *)dev_alloc(sizeof(int) * ents.size());
     b->groups.push_back(gr);
-    if (!gr.ents || !gr.block_first) {
+    if (!gr.ents || !gr.block_first || !gr.limits) {
       set_error("cannot allocate batch tables");
       batch_free(b);
       return LBM_ENOMEM;
@@ -946,6 +993,7 @@ int lbm_batch_step(lbm_batch b, long n) {
   REQUIRE(b != nullptr, "null batch");
   REQUIRE(n >= 0, "negative step count");
   DevGuard g(b->device);
+  REQUIRE(!b->spent, "batch ran a ragged generation; create a new batch");
   for (size_t k = 0; k < b->members.size(); ++k)
     REQUIRE(b->members[k]->L.cur == (b->offs[k] ^ b->parity),
             "a member was modified outside the batch");
@@ -1010,6 +1058,7 @@ int lbm_batch_tune(lbm_batch b, double *times_ms, int *chosen) {
 
 int lbm_batch_drift(lbm_batch b, double *out) {
   REQUIRE(b != nullptr && out != nullptr, "null argument");
+  REQUIRE(!b->spent, "batch ran a ragged generation; use lbm_drift per member");
   DevGuard g(b->device);
   const int n = (int)b->members.size();
   CK(launch_batch_drift(b->views[b->parity], n, b->dpart, b->dout, b->stream));

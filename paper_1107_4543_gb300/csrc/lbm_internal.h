@@ -44,13 +44,13 @@ cudaError_t launch_step_dev_bf16(const Lattice &L, const void *src, void *dst, c
                                  int block, int variant);
 cudaError_t launch_step_batch_f32(const BatchEntry *ents, int n, const int *block_first,
                                   long long ntasks, int parity, cudaStream_t st, int block,
-                                  int variant);
+                                  int variant, const int *limits, int k);
 cudaError_t launch_step_batch_f16(const BatchEntry *ents, int n, const int *block_first,
                                   long long ntasks, int parity, cudaStream_t st, int block,
-                                  int variant);
+                                  int variant, const int *limits, int k);
 cudaError_t launch_step_batch_bf16(const BatchEntry *ents, int n, const int *block_first,
                                    long long ntasks, int parity, cudaStream_t st, int block,
-                                   int variant);
+                                   int variant, const int *limits, int k);
 cudaError_t launch_step_f64(const Lattice &L, const void *src, void *dst,
                             cudaStream_t st, int block, int grid_cap);
 
@@ -66,14 +66,18 @@ inline cudaError_t launch_step_dev(const Lattice &L, const void *src, void *dst,
 
 inline cudaError_t launch_step_batch(int dtype, const BatchEntry *ents, int n,
                                      const int *block_first, long long ntasks, int parity,
-                                     cudaStream_t st, int block, int variant) {
+                                     cudaStream_t st, int block, int variant,
+                                     const int *limits = nullptr, int k = 0) {
   switch (dtype) {
     case LBM_F32DEV:
-      return launch_step_batch_f32(ents, n, block_first, ntasks, parity, st, block, variant);
+      return launch_step_batch_f32(ents, n, block_first, ntasks, parity, st, block, variant,
+                                   limits, k);
     case LBM_F16DEV:
-      return launch_step_batch_f16(ents, n, block_first, ntasks, parity, st, block, variant);
+      return launch_step_batch_f16(ents, n, block_first, ntasks, parity, st, block, variant,
+                                   limits, k);
     case LBM_BF16DEV:
-      return launch_step_batch_bf16(ents, n, block_first, ntasks, parity, st, block, variant);
+      return launch_step_batch_bf16(ents, n, block_first, ntasks, parity, st, block, variant,
+                                    limits, k);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -118,6 +122,10 @@ void host_feq_j(double rho, double jx, double jy, double out[9]);
 
 // batch launch-variant control (lbm_api.cu), for the server
 void batch_pin_variant(lbm_batch_ctx *b, int variant);
+// One generation of a server batch: member k advances min(steps[k], n)
+// steps (n launches; a member's warps return once it is done).  The batch
+// can only be destroyed afterwards.
+int batch_step_ragged(lbm_batch_ctx *b, const long *steps, long n);
 int batch_variant(const lbm_batch_ctx *b);
 long long batch_nodes(const lbm_batch_ctx *b);
 

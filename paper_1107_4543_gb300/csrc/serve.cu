@@ -2,12 +2,14 @@
 // lbm_poll in include/lbm.h).
 //
 // One scheduler thread per server owns the device work.  Each loop it
-//   1. admits queued requests in arrival order while the device bytes of
-//      the resident lattices plus the next request fit in the budget
+//   1. admits queued requests -- in arrival order (LBM_SERVE_FIFO) or
+//      smallest remaining work first (LBM_SERVE_SHORTEST) -- while the
+//      device bytes of the resident lattices plus the request fit in the
+//      budget and, if a cap is set, their nodes fit in the resident-node cap
 //      (create + initialise on the device);
-//   2. steps every resident lattice together for one "generation" of
-//      min(chunk_steps, smallest remaining step count) steps: one batched
-//      launch per step and storage type, replayed from a captured graph;
+//   2. steps every resident lattice together for one "generation" of up to
+//      chunk_steps steps: one batched launch per step and storage type, in
+//      which each lattice takes part until its own step count is reached;
 //   3. retires the lattices that are done: moments to host, memory freed,
 //      latency stamped.
 // Requests that arrive while a generation runs join at the next one, so
@@ -82,6 +84,9 @@ struct lbm_server_ctx {
   size_t stage_nodes = 0;
   lbm_server_stats_t st{};
   int variant = -1;  // step launch variant, tuned on the first large generation
+  int policy = LBM_SERVE_FIFO;
+  long long max_nodes = 0;  // resident-node cap (0: bytes only)
+  long long resident_nodes = 0;
 };
 
 static int ensure_server_stage(lbm_server_ctx *s, size_t nodes) {
@@ -148,7 +153,10 @@ static void finish(lbm_server_ctx *s, Req *q, int err) {
     lbm_destroy(q->h);
     q->h = nullptr;
   }
-  if (q->state == RUNNING) s->resident_bytes -= q->bytes;
+  if (q->state == RUNNING) {
+    s->resident_bytes -= q->bytes;
+    s->resident_nodes -= (long long)q->r.nx * q->r.ny;
+  }
   q->state = err == LBM_OK ? DONE : FAILED;
   q->err = err;
   q->latency = now_s() - q->t_submit;
@@ -167,13 +175,22 @@ static void worker_loop(lbm_server_ctx *s) {
       s->cv.wait(lk, [&] { return s->stop || !s->queue.empty() || !s->running.empty(); });
       if (s->stop && s->queue.empty() && s->running.empty()) return;
       while (!s->queue.empty()) {
-        Req *q = s->queue.front();
+        auto pick = s->queue.begin();
+        if (s->policy == LBM_SERVE_SHORTEST)
+          pick = std::min_element(s->queue.begin(), s->queue.end(), [](Req *a, Req *b) {
+            return (double)a->r.nx * a->r.ny * a->r.steps < (double)b->r.nx * b->r.ny * b->r.steps;
+          });
+        Req *q = *pick;
         const size_t need = estimate_bytes(q->r);
+        const long long nodes = (long long)q->r.nx * q->r.ny;
         if (s->resident_bytes + need > s->budget) break;
-        s->queue.pop_front();
+        if (s->max_nodes > 0 && s->resident_nodes > 0 && s->resident_nodes + nodes > s->max_nodes)
+          break;
+        s->queue.erase(pick);
         q->state = RUNNING;
         q->bytes = need;
         s->resident_bytes += need;
+        s->resident_nodes += nodes;
         fresh.push_back(q);
       }
     }
@@ -201,8 +218,12 @@ static void worker_loop(lbm_server_ctx *s) {
       s->st.resident_bytes = s->resident_bytes;
     }
     if (run.empty()) continue;
-    long n = s->chunk;
-    for (Req *q : run) n = std::min(n, q->remaining);
+    // a generation lasts up to chunk steps; each lattice stops at its own count
+    long n = 0;
+    for (Req *q : run) n = std::max(n, q->remaining);
+    n = std::min(n, s->chunk);
+    std::vector<long> take(run.size());
+    for (size_t k = 0; k < run.size(); ++k) take[k] = std::min(run[k]->remaining, n);
     const double t0 = now_s();
     int rc = LBM_OK;
     if (n > 0) {
@@ -214,21 +235,22 @@ static void worker_loop(lbm_server_ctx *s) {
         // tune once, on the first generation large enough to be tuned, and
         // keep that choice for every later generation
         if (s->variant >= 0) batch_pin_variant(b, s->variant);
-        rc = lbm_batch_step(b, n);
+        rc = batch_step_ragged(b, take.data(), n);
         if (s->variant < 0 && batch_nodes(b) >= (1LL << 20)) s->variant = batch_variant(b);
         lbm_batch_destroy(b);
       }
     }
     double lu = 0;
-    for (Req *q : run) lu += (double)q->r.nx * q->r.ny * n;
+    for (size_t k = 0; k < run.size(); ++k) lu += (double)run[k]->r.nx * run[k]->r.ny * take[k];
     // retire finished lattices (moments to host)
     std::vector<std::pair<Req *, int>> done;
-    for (Req *q : run) {
+    for (size_t k = 0; k < run.size(); ++k) {
+      Req *q = run[k];
       if (rc != LBM_OK) {
         done.push_back({q, rc});
         continue;
       }
-      q->remaining -= n;
+      q->remaining -= take[k];
       if (q->remaining <= 0) done.push_back({q, retire_one(s, q)});
     }
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) cudaGetLastError();
@@ -266,6 +288,18 @@ int lbm_server_create(size_t hbm_budget_bytes, long chunk_steps, lbm_server *out
   }
   s->worker = std::thread(worker_loop, s);
   *out = s;
+  return LBM_OK;
+}
+
+int lbm_server_set_policy(lbm_server s, int policy, long long max_resident_nodes) {
+  if (!s || (policy != LBM_SERVE_FIFO && policy != LBM_SERVE_SHORTEST) ||
+      max_resident_nodes < 0) {
+    set_error("bad server policy");
+    return LBM_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->policy = policy;
+  s->max_nodes = max_resident_nodes;
   return LBM_OK;
 }
 

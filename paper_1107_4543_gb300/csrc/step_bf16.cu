@@ -10,8 +10,9 @@ cudaError_t launch_step_dev_bf16(const Lattice &L, const void *src, void *dst, c
 
 cudaError_t launch_step_batch_bf16(const BatchEntry *ents, int n, const int *block_first,
                                 long long ntasks, int parity, cudaStream_t st, int block,
-                                int variant) {
-  return launch_step_batch_t<__nv_bfloat16>(ents, n, block_first, ntasks, parity, st, block, variant);
+                                int variant, const int *limits, int k) {
+  return launch_step_batch_t<__nv_bfloat16>(ents, n, block_first, ntasks, parity, st, block, variant,
+                                 limits, k);
 }
 
 }  // namespace lbm

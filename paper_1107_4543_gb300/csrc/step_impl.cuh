@@ -49,15 +49,18 @@ k_step_dev(const T *__restrict__ src, T *__restrict__ dst, Geom g, DevParams P,
 // Batched: tasks of all lattices flattened; block b starts its lookup at
 // lattice block_first[b] (blocks cover consecutive tasks, so a warp walks
 // forward at most a few entries).
+// limits (may be null): lattice l takes part only while k < limits[l], so
+// members of one launch sequence can stop after different step counts.
 template <typename T, int MINB>
 __global__ void __launch_bounds__(256, MINB)
 k_step_batch(const BatchEntry *__restrict__ ents, int n, const int *__restrict__ block_first,
-             long long ntasks, int parity) {
+             long long ntasks, int parity, const int *__restrict__ limits, int k) {
   const int lane = threadIdx.x & 31;
   const long long task = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (task >= ntasks) return;  // warp-uniform
   int l = block_first[blockIdx.x];
   while (l + 1 < n && ents[l + 1].task0 <= task) ++l;
+  if (limits != nullptr && k >= limits[l]) return;  // warp-uniform
   const BatchEntry &E = ents[l];
   const int from = parity ^ E.off;
   const T *src = static_cast<const T *>(E.buf[from]);
@@ -87,19 +90,22 @@ cudaError_t launch_step_dev_t(const Lattice &L, const void *src, void *dst, cuda
 template <typename T>
 cudaError_t launch_step_batch_t(const BatchEntry *ents, int n, const int *block_first,
                                 long long ntasks, int parity, cudaStream_t st, int block,
-                                int variant) {
+                                int variant, const int *limits, int k) {
   const int wpb = block / 32;
   const long long grid = (ntasks + wpb - 1) / wpb;
   if (grid < 1) return cudaSuccess;
   switch (variant) {
     case 0:
-      k_step_batch<T, 1><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity);
+      k_step_batch<T, 1><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity,
+                                                          limits, k);
       break;
     case 1:
-      k_step_batch<T, 2><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity);
+      k_step_batch<T, 2><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity,
+                                                          limits, k);
       break;
     default:
-      k_step_batch<T, 3><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity);
+      k_step_batch<T, 3><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity,
+                                                          limits, k);
       break;
   }
   return cudaGetLastError();

@@ -81,6 +81,7 @@ _SIGS = {
                                   ctypes.POINTER(ctypes.c_longlong)]),
     "lbm_poll": (ctypes.c_int, [_vp, ctypes.c_longlong, _dp, _dp, _dp, _dp]),
     "lbm_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(lbm_server_stats_t)]),
+    "lbm_server_set_policy": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_longlong]),
     "lbm_server_destroy": (ctypes.c_int, [_vp]),
 }
 
@@ -306,6 +307,14 @@ def lbm_server_create(hbm_budget_bytes, chunk_steps=100):
     _ck(load().lbm_server_create(int(hbm_budget_bytes), int(chunk_steps), ctypes.byref(s)),
         "lbm_server_create")
     return s
+
+
+LBM_SERVE_FIFO, LBM_SERVE_SHORTEST = 0, 1
+
+
+def lbm_server_set_policy(s, policy=LBM_SERVE_FIFO, max_resident_nodes=0):
+    _ck(load().lbm_server_set_policy(s, int(policy), int(max_resident_nodes)),
+        "lbm_server_set_policy")
 
 
 def make_request(nx, ny, S, steps, dtype=LBM_F32DEV, rho0=1.0, u0=(0.0, 0.0),

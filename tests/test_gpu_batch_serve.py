@@ -192,13 +192,16 @@ def wait_all(L, srv, ids, reqs, timeout=120.0):
     return out
 
 
-@pytest.mark.parametrize("budget_mb", [1000, 2])
-def test_served_result_equals_alone(L, budget_mb):
-    """Each served result equals the same solve run alone, with a budget
-    that admits everything at once and with one so tight that requests
-    queue and join generations as others retire."""
+@pytest.mark.parametrize("budget_mb,policy,cap", [(1000, 0, 0), (2, 0, 0), (1000, 1, 20000)])
+def test_served_result_equals_alone(L, budget_mb, policy, cap):
+    """Each served result equals the same solve run alone: with a budget
+    that admits everything at once, with one so tight that requests queue
+    and join generations as others retire, and shortest-work-first with a
+    resident-node cap.  Lattices of one generation stop at different step
+    counts."""
     reqs = served_requests(16, seed=21)
     srv = L.lbm_server_create(budget_mb * 2**20, 37)
+    L.lbm_server_set_policy(srv, policy, cap)
     try:
         ids, kinds = [], []
         for k, q in enumerate(reqs):
