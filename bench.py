@@ -41,7 +41,8 @@ sys.path.insert(0, ROOT)
 import lbm_inputs as inp  # noqa: E402
 
 BYTES_PER_LU = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}
-KERNEL_SOURCES = ["csrc/step.cu", "csrc/d2q9_pull.cuh", "csrc/collide.cuh", "csrc/step_f64.cu"]
+KERNEL_SOURCES = ["csrc/step_impl.cuh", "csrc/d2q9_pull.cuh", "csrc/collide.cuh",
+                  "csrc/step_f32.cu", "csrc/step_f16.cu", "csrc/step_bf16.cu", "csrc/step_f64.cu"]
 
 
 def parse():
@@ -190,35 +191,33 @@ def sources_sha():
 
 
 # -------------------------------------------------------------- CPU oracle
-def cpu_oracle_mlups(specs, target_s=12.0, threads=None):
+def cpu_oracle_mlups(specs, target_s=20.0, threads=None, lattices=4):
     """The FP64 oracle (as it stands) on a bounded sample of the workload:
-    the first lattices of the list, stepped until about target_s seconds of
-    CPU work.  Returns (MLUPS, cores, sample description)."""
+    the first `lattices` lattices of the list, each stepped for about
+    target_s / lattices seconds (at most the workload's step count).
+    Returns (MLUPS, cores, sample description)."""
     import oracle as orc
 
     threads = threads or os.cpu_count() or 1
     orc.set_threads(threads)
-    nodes = steps_done = 0
+    nodes = 0
     t_total = 0.0
     used = []
-    for spec in specs:
-        rho, ux, uy = inp.batch_fields(spec) if "b" in spec else spec["fields"]
+    for spec in specs[:lattices]:
+        rho, ux, uy = inp.batch_fields(spec)
         f = orc.init_eq(rho, ux, uy)
         s = inp.s_paper(spec["rates"])
+        f = orc.run(f, s, 1)  # thread start-up outside the estimate
         t0 = time.perf_counter()
-        f = orc.run(f, s, 2)
-        dt = time.perf_counter() - t0
+        f = orc.run(f, s, 4)
+        per_step = (time.perf_counter() - t0) / 4
         n = spec["nx"] * spec["ny"]
-        steps = max(2, int(min(50, (target_s / 4) / max(dt / 2, 1e-9))))
+        steps = int(max(2, min(spec.get("steps", 500), (target_s / lattices) / max(per_step, 1e-9))))
         t0 = time.perf_counter()
         orc.run(f, s, steps)
-        dt = time.perf_counter() - t0
+        t_total += time.perf_counter() - t0
         nodes += n * steps
-        t_total += dt
-        steps_done += steps
-        used.append("%dx%d x%d" % (spec["nx"], spec["ny"], steps))
-        if t_total >= target_s or len(used) >= 6:
-            break
+        used.append("%dx%d x %d steps" % (spec["nx"], spec["ny"], steps))
     return nodes / t_total / 1e6, threads, "; ".join(used)
 
 
@@ -350,6 +349,8 @@ def bench_batched(args, L, torch, rank, ws):
     tr = traffic_record("k_step_batch<float>")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
+                # ncu DRAM bytes per lattice update of a smaller capture of the
+                # same kernel, scaled to this launch's lattice updates
                 "traffic": (round(tr["dram_bytes_per_lu"] * nodes) if tr else None),
                 "kernel": "k_step_batch<float>", "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": BYTES_PER_LU["f32"] * nodes,
@@ -464,7 +465,7 @@ def reference_arm(args):
     specs = inp.batch_specs(args.lattices, seed=1107 + 4, steps=args.lbm_steps)
     vals = []
     for k in range(args.warmup + args.steps):
-        mlups, cores, sample = cpu_oracle_mlups(specs[:3], target_s=8.0)
+        mlups, cores, sample = cpu_oracle_mlups(specs, target_s=12.0)
         if k >= args.warmup:
             vals.append(mlups)
     v = float(np.mean(vals))
@@ -515,7 +516,7 @@ def main():
     line, specs = bench_batched(args, L, torch, rank, ws)
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
-            mlups, cores, sample = cpu_oracle_mlups(specs[:3])
+            mlups, cores, sample = cpu_oracle_mlups(specs)
             line["cpu_baseline"] = {"value": round(mlups, 2), "unit": "MLUPS", "cores": cores,
                                     "kind": "oracle", "sample": sample}
         print(json.dumps(line))

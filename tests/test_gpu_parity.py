@@ -260,6 +260,52 @@ def test_invalid_arguments_are_rejected(L):
         L.lbm_destroy(h)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16", "bf16"])
+def test_translation_shifts_the_result(L, dtype):
+    """Every node runs the same arithmetic: stepping a shifted initial field
+    gives the shifted result bit for bit (no oracle needed)."""
+    nx, ny, steps = 45, 26, 37
+    r = inp.rates("OPT")
+    fields = inp.gaussian_pulse(nx, ny, 1e-3, 3.0, 14.3, 9.6)
+    shifted = tuple(np.roll(a, (5, 11), axis=(0, 1)) for a in fields)
+    (rho_a, _, _), _ = run_gpu(L, nx, ny, r, steps, L.DTYPES[dtype], fields=fields)
+    (rho_b, _, _), _ = run_gpu(L, nx, ny, r, steps, L.DTYPES[dtype], fields=shifted)
+    assert np.array_equal(np.roll(rho_a, (5, 11), axis=(0, 1)), rho_b)
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-6)])
+def test_centred_pulse_keeps_d4_symmetry(L, dtype, tol):
+    """A pulse centred on a node of a square lattice at rest stays symmetric
+    under the 8 symmetries of the square (up to rounding)."""
+    n, steps, amp = 48, 120, 1e-3
+    r = inp.rates("LL", nu=1e-3)
+    fields = inp.gaussian_pulse(n, n, amp, 4.0, 24.0, 24.0)
+    (rho, _, _), _ = run_gpu(L, n, n, r, steps, L.DTYPES[dtype], fields=fields)
+    d = rho - 1.0
+    c = np.roll(d, (-24, -24), axis=(0, 1))  # centre at index 0
+    # reflections i -> -i (mod n) about the centre, and the diagonal
+    images = (np.roll(c[::-1, :], 1, axis=0), np.roll(c[:, ::-1], 1, axis=1), c.T,
+              np.roll(c[::-1, ::-1], (1, 1), axis=(0, 1)))
+    assert np.max(np.abs(d)) > 1e-2 * amp
+    for img in images:
+        assert np.max(np.abs(img - c)) <= tol * amp
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 0.0), ("f32", 1e-6)])
+def test_bgk_rates_match_oracle(L, dtype, tol):
+    """All non-conserved rates equal: the single-relaxation-time scheme of
+    section 2.1 (Lambda = s I) as a special case of the MRT path."""
+    nx, ny, steps, amp = 40, 36, 150, 1e-3
+    sv = 1.0 / (0.5 + 3e-3)
+    r = dict(s_e=sv, s_eps=sv, s_q=sv, s_nu=sv)
+    fields = inp.gaussian_pulse(nx, ny, amp, 4.0)
+    (rho, _, _), f = run_gpu(L, nx, ny, r, steps, L.DTYPES[dtype], fields=fields)
+    (rho_o, _, _), f_o = run_orc(r, steps, fields=fields)
+    assert np.max(np.abs(rho - rho_o)) <= tol * amp
+    if dtype == "f64":
+        assert np.array_equal(f, f_o)
+
+
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
 def test_tuning_leaves_state_unchanged(L, dtype):
     """Trial launches of the tuner write only the idle buffer; every launch
