@@ -114,6 +114,15 @@ int lbm_init_analytic(lbm_handle h, int kind, const double params[8]);
  * LBM_ECUDA (launch failure). */
 int lbm_step(lbm_handle h, long n);
 
+/* lbm_set_source -- the acoustic point source of section 5.1: before the
+ * collision of every later lbm_step, node (x, y) is set to the equilibrium
+ * at rest with density rho0 + amplitude * sin(2 pi t / period), t the
+ * lattice time at the start of that step (0 after init).  amplitude = 0
+ * removes the source.  Steps of a lattice with a source are launched one by
+ * one (the forcing changes every step), not from a CUDA graph.  Errors:
+ * LBM_EINVAL (node outside the lattice, period <= 0, batch member). */
+int lbm_set_source(lbm_handle h, int x, int y, double amplitude, double period);
+
 /* lbm_tune -- time the launch variants of the step kernel on this lattice
  * (LBM_TUNE_VARIANTS register caps of the deviation-storage kernel) and keep
  * the fastest for later steps.  Trial launches read the current state and

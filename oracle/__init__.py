@@ -40,6 +40,10 @@ def load():
         lib.orc_meq.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
         lib.orc_matrices.argtypes = [dp, dp]
         lib.orc_velocities.argtypes = [ctypes.POINTER(ctypes.c_int)] * 2
+        lib.orc_run_source.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_long,
+                                       ctypes.c_long, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        lib.orc_run_source.restype = ctypes.c_int
         lib.orc_set_threads.argtypes = [ctypes.c_int]
         lib.orc_get_threads.restype = ctypes.c_int
         _lib = lib
@@ -112,6 +116,21 @@ def run(f, s, nsteps):
     rc = load().orc_run(nx, ny, _p(s), _p(f), int(nsteps))
     if rc != 0:
         raise RuntimeError("orc_run failed (%d)" % rc)
+    return f
+
+
+def run_source(f, s, nsteps, source, t0=0, rho0=1.0):
+    """orc_run with the point source of section 5.1: source = (x, y,
+    amplitude, period); the node is reset to f^eq(rho0 + amplitude
+    sin(2 pi t / period), 0) before each step's collision."""
+    f = np.array(f, dtype=np.float64, order="C")
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    _, ny, nx = f.shape
+    x, y, amp, period = source
+    rc = load().orc_run_source(nx, ny, _p(s), _p(f), int(nsteps), int(t0), int(x), int(y),
+                               float(rho0), float(amp), float(period))
+    if rc != 0:
+        raise RuntimeError("orc_run_source failed (%d)" % rc)
     return f
 
 

@@ -161,6 +161,39 @@ int orc_run(int nx, int ny, const double s[Q], double *f, long nsteps) {
     return 0;
 }
 
+/* f^eq(rho, u) = M^-1 m^eq(rho, rho u) at one node */
+static void feq_node(const double *Minv, double rho, double ux, double uy, double f[Q]) {
+    double meq[Q];
+    orc_meq(rho, rho * ux, rho * uy, meq);
+    for (int i = 0; i < Q; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < Q; ++k) acc += Minv[i * Q + k] * meq[k];
+        f[i] = acc;
+    }
+}
+
+/* As orc_run, with the acoustic point source of section 5.1: before the
+   collision of every step (lattice time t = t0, t0 + 1, ...) the node
+   (sx, sy) is set to the equilibrium at rest with density
+   rho0 + amp sin(2 pi t / period). */
+int orc_run_source(int nx, int ny, const double s[Q], double *f, long nsteps, long t0,
+                   int sx, int sy, double rho0, double amp, double period) {
+    if (sx < 0 || sx >= nx || sy < 0 || sy >= ny || !(period > 0)) return -1;
+    const double PI = 3.14159265358979323846;
+    double M[Q * Q], Minv[Q * Q];
+    orc_matrices(M, Minv);
+    size_t plane = (size_t)nx * (size_t)ny;
+    for (long k = 0; k < nsteps; ++k) {
+        double fs[Q];
+        double rho_t = rho0 + amp * sin(2.0 * PI * (double)(t0 + k) / period);
+        feq_node(Minv, rho_t, 0.0, 0.0, fs);
+        for (int i = 0; i < Q; ++i) f[i * plane + (size_t)sy * nx + sx] = fs[i];
+        int rc = orc_run(nx, ny, s, f, 1);
+        if (rc != 0) return rc;
+    }
+    return 0;
+}
+
 /* f = f^eq(rho, u) = M^-1 m^eq(rho, rho u) at every node */
 void orc_init_eq(int nx, int ny, const double *rho, const double *ux,
                  const double *uy, double *f) {

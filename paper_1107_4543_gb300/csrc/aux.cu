@@ -110,14 +110,17 @@ struct AnalyticParams { double p[8]; };
 
 // f = f^eq(field) at node x.  Population i of node x goes to slot x - c_i,
 // where the next step's pull (f_i(x) = P_i(x - c_i)) reads it.
+// bad (may be null) counts nodes whose field is not finite or has rho <= 0
 __global__ void k_init_eq(AuxView a, const double *rho, const double *ux, const double *uy,
-                          int kind, AnalyticParams ap) {
+                          int kind, AnalyticParams ap, unsigned int *bad) {
   const long long N = (long long)a.g.nx * a.g.ny;
+  unsigned int nbad = 0;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(n % a.g.nx), y = (int)(n / a.g.nx);
     double r, u, v, f[9];
     field_at(a, rho, ux, uy, kind, ap.p, x, y, r, u, v);
+    if (!(r > 0.0) || !isfinite(r) || !isfinite(u) || !isfinite(v)) ++nbad;
     feq_canonical(r, u, v, f);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -125,6 +128,28 @@ __global__ void k_init_eq(AuxView a, const double *rho, const double *ux, const 
       store_value(a, (long long)i * a.g.plane + (long long)ys * a.g.pitch + xs, i, f[i]);
     }
   }
+  if (bad && nbad) atomicAdd(bad, nbad);
+}
+
+// Point source: set the pre-collision populations of node (x, y) to fs by
+// writing the 9 slots the next step's pull reads for that node.
+struct NodePops { double f[9]; };
+
+__global__ void k_force_node(AuxView a, int x, int y, NodePops fs) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.ny);
+    store_value(a, (long long)i * a.g.plane + (long long)ys * a.g.pitch + xs, i, fs.f[i]);
+  }
+}
+
+cudaError_t launch_force_node(const AuxView &a, int x, int y, const double fs[9],
+                              cudaStream_t st) {
+  NodePops p;
+  for (int i = 0; i < 9; ++i) p.f[i] = fs[i];
+  k_force_node<<<1, 32, 0, st>>>(a, x, y, p);
+  return cudaGetLastError();
 }
 
 __global__ void k_maxdev_eq(AuxView a, const double *rho, const double *ux, const double *uy,
@@ -337,9 +362,14 @@ static AnalyticParams make_ap(const double *p) {
 }
 
 cudaError_t launch_init_eq(const AuxView &a, const double *rho, const double *ux,
-                           const double *uy, int kind, const double *params, cudaStream_t st) {
+                           const double *uy, int kind, const double *params, cudaStream_t st,
+                           unsigned int *bad) {
   const long long N = (long long)a.g.nx * a.g.ny;
-  k_init_eq<<<grid_for(N), 256, 0, st>>>(a, rho, ux, uy, kind, make_ap(params));
+  if (bad) {
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+  }
+  k_init_eq<<<grid_for(N), 256, 0, st>>>(a, rho, ux, uy, kind, make_ap(params), bad);
   return cudaGetLastError();
 }
 

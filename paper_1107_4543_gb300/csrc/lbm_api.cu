@@ -115,6 +115,10 @@ struct lbm_ctx {
   int grid_cap = 0;
   bool tuned = false;
   lbm_batch_ctx *batch = nullptr;
+  // acoustic point source (lbm_set_source)
+  bool src_on = false;
+  int sx = 0, sy = 0;
+  double s_amp = 0, s_period = 1;
 };
 
 #define CK(call)                                                            \
@@ -337,9 +341,10 @@ static int check_rates(const double S[9]) {
   return 1;
 }
 
-// init f = f^eq(field) (kind 0: device arrays; else analytic)
+// init f = f^eq(field) (kind 0: device arrays; else analytic).  With bad
+// set, the init kernel counts invalid nodes there (read after a sync).
 static int do_init(lbm_ctx *h, const double *rho, const double *ux, const double *uy, int kind,
-                   const double *params) {
+                   const double *params, unsigned int *bad = nullptr) {
   if (h->batch) {
     set_error("lattice is a batch member");
     return LBM_EINVAL;
@@ -356,7 +361,7 @@ static int do_init(lbm_ctx *h, const double *rho, const double *ux, const double
     set_qscale(h, (double)m);
     a = aux_view(h);
   }
-  CK(launch_init_eq(a, rho, ux, uy, kind, params, h->stream));
+  CK(launch_init_eq(a, rho, ux, uy, kind, params, h->stream, bad));
   h->t = 0;
   return LBM_OK;
 }
@@ -550,18 +555,22 @@ int lbm_init_field(lbm_handle h, const double *rho, const double *ux, const doub
   REQUIRE(h && rho && ux && uy, "null argument");
   DevGuard g(h->device);
   const size_t n = (size_t)h->L.g.nx * h->L.g.ny;
-  for (size_t k = 0; k < n; ++k)
-    REQUIRE(rho[k] > 0.0 && isfinite(rho[k]) && isfinite(ux[k]) && isfinite(uy[k]),
-            "fields must be finite with rho > 0");
   int rc = ensure_stage(h);
   if (rc != LBM_OK) return rc;
   CK(cudaMemcpyAsync(h->stage, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->stage + n, ux, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->stage + 2 * n, uy, n * sizeof(double), cudaMemcpyHostToDevice,
                      h->stream));
-  rc = do_init(h, h->stage, h->stage + n, h->stage + 2 * n, 0, nullptr);
+  // the fields are validated on the device, inside the init kernel
+  rc = do_init(h, h->stage, h->stage + n, h->stage + 2 * n, 0, nullptr, h->maxbits);
   if (rc != LBM_OK) return rc;
+  unsigned int bad = 0;
+  CK(cudaMemcpyAsync(&bad, h->maxbits, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (bad) {
+    set_error(std::to_string(bad) + " nodes with non-finite fields or rho <= 0");
+    return LBM_EINVAL;
+  }
   return LBM_OK;
 }
 
@@ -583,6 +592,20 @@ int lbm_step(lbm_handle h, long n) {
     int rc = maybe_autotune(h);
     if (rc != LBM_OK) return rc;
   }
+  if (h->src_on) {
+    // the forcing changes every step: direct launches, no graph
+    const double PI = 3.14159265358979323846;
+    for (; n > 0; --n) {
+      double fs[9];
+      const double rho_t = h->rho0 + h->s_amp * sin(2.0 * PI * (double)h->t / h->s_period);
+      host_feq_j(rho_t, 0.0, 0.0, fs);
+      CK(launch_force_node(aux_view(h), h->sx, h->sy, fs, h->stream));
+      CK(launch_one(h, h->L.cur, h->stream));
+      h->L.cur ^= 1;
+      h->t += 1;
+    }
+    return LBM_OK;
+  }
   const int G = 64;  // steps per captured graph (even)
   while (n > 0) {
     if (h->L.cur == 0 && n >= G) {
@@ -600,6 +623,19 @@ int lbm_step(lbm_handle h, long n) {
       h->t += 1;
     }
   }
+  return LBM_OK;
+}
+
+int lbm_set_source(lbm_handle h, int x, int y, double amplitude, double period) {
+  REQUIRE(h != nullptr, "null handle");
+  REQUIRE(x >= 0 && x < h->L.g.nx && y >= 0 && y < h->L.g.ny, "source outside the lattice");
+  REQUIRE(isfinite(amplitude) && isfinite(period) && period > 0, "bad source amplitude or period");
+  REQUIRE(h->batch == nullptr, "lattice is a batch member");
+  h->src_on = amplitude != 0.0;
+  h->sx = x;
+  h->sy = y;
+  h->s_amp = amplitude;
+  h->s_period = period;
   return LBM_OK;
 }
 
@@ -756,6 +792,16 @@ static cudaError_t batch_launch_all(lbm_batch_ctx *b, int parity, cudaStream_t s
   return cudaSuccess;
 }
 
+static std::map<std::string, int> g_batch_tune_cache;
+
+static std::string batch_key(const lbm_batch_ctx *b) {
+  std::string k;
+  for (auto *m : b->members)
+    k += std::to_string(m->L.dtype) + ":" + std::to_string(m->L.g.nx) + "x" +
+         std::to_string(m->L.g.ny) + ",";
+  return k;
+}
+
 // As tune_handle, for the whole batch: trial launches at the current parity
 // write only the idle buffers.
 static int tune_batch(lbm_batch_ctx *b, double *times) {
@@ -783,6 +829,29 @@ static int tune_batch(lbm_batch_ctx *b, double *times) {
     }
   }
   b->tuned = true;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_batch_tune_cache[batch_key(b)] = bv;
+  return LBM_OK;
+}
+
+// First step of a large batch: reuse the choice made for a batch of the
+// same composition (storage types and sizes, in order) or tune now.
+static int maybe_autotune_batch(lbm_batch_ctx *b) {
+  if (b->nodes >= (1LL << 20) && autotune_enabled()) {
+    int cached = -1;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_batch_tune_cache.find(batch_key(b));
+      if (it != g_batch_tune_cache.end()) cached = it->second;
+    }
+    if (cached >= 0) {
+      b->variant = cached;
+    } else {
+      int rc = tune_batch(b, nullptr);
+      if (rc != LBM_OK) return rc;
+    }
+  }
+  b->tuned = true;
   return LBM_OK;
 }
 
@@ -806,11 +875,8 @@ int batch_step_ragged(lbm_batch_ctx *b, const long *steps, long n) {
   REQUIRE(n <= 0x3fffffffL, "too many steps for one generation");
   DevGuard g(b->device);
   if (n > 0 && !b->tuned) {
-    if (b->nodes >= (1LL << 20) && autotune_enabled()) {
-      int rc = tune_batch(b, nullptr);
-      if (rc != LBM_OK) return rc;
-    }
-    b->tuned = true;
+    int rc = maybe_autotune_batch(b);
+    if (rc != LBM_OK) return rc;
   }
   const size_t nm = b->members.size();
   std::vector<std::vector<int>> lim(b->groups.size());
@@ -998,11 +1064,8 @@ int lbm_batch_step(lbm_batch b, long n) {
     REQUIRE(b->members[k]->L.cur == (b->offs[k] ^ b->parity),
             "a member was modified outside the batch");
   if (n > 0 && !b->tuned) {
-    if (b->nodes >= (1LL << 20) && autotune_enabled()) {
-      int rc = tune_batch(b, nullptr);
-      if (rc != LBM_OK) return rc;
-    }
-    b->tuned = true;
+    int rc = maybe_autotune_batch(b);
+    if (rc != LBM_OK) return rc;
   }
   const int G = 64;
   long done = 0;

@@ -100,12 +100,14 @@ struct AuxView {
 };
 cudaError_t launch_init_eq(const AuxView &a, const double *rho, const double *ux,
                            const double *uy, int analytic_kind, const double *params,
-                           cudaStream_t st);
+                           cudaStream_t st, unsigned int *bad = nullptr);
 cudaError_t launch_maxdev_eq(const AuxView &a, const double *rho, const double *ux,
                              const double *uy, int analytic_kind, const double *params,
                              unsigned int *max_bits, cudaStream_t st);
 cudaError_t launch_moments(const AuxView &a, double *rho, double *ux, double *uy,
                            cudaStream_t st);
+cudaError_t launch_force_node(const AuxView &a, int x, int y, const double fs[9],
+                              cudaStream_t st);
 cudaError_t launch_get_pop(const AuxView &a, double *f, cudaStream_t st);
 cudaError_t launch_set_pop(const AuxView &a, const double *f, cudaStream_t st);
 cudaError_t launch_maxdev_pop(const AuxView &a, const double *f, unsigned int *max_bits,

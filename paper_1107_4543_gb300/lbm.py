@@ -57,6 +57,8 @@ _SIGS = {
     "lbm_init_analytic": (ctypes.c_int, [_vp, ctypes.c_int, _dp]),
     "lbm_step": (ctypes.c_int, [_vp, ctypes.c_long]),
     "lbm_tune": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_set_source": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double]),
     "lbm_batch_tune": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_int)]),
     "lbm_moments": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
     "lbm_moments_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -188,6 +190,11 @@ def lbm_init_analytic(h, kind, params):
 
 def lbm_step(h, n):
     _ck(load().lbm_step(h, int(n)), "lbm_step")
+
+
+def lbm_set_source(h, x, y, amplitude, period):
+    _ck(load().lbm_set_source(h, int(x), int(y), float(amplitude), float(period)),
+        "lbm_set_source")
 
 
 LBM_TUNE_VARIANTS = 3

@@ -306,6 +306,42 @@ def test_bgk_rates_match_oracle(L, dtype, tol):
         assert np.array_equal(f, f_o)
 
 
+def point_source_rates(name):
+    """The three schemes of section 5.1 with Table 4's s_e = s_nu: BGK (all
+    rates s_nu), the original MRT (Lallemand-Luo s_eps, s_q) and the
+    optimized one (Table 4 group A)."""
+    t = inp.TABLE4["A"]
+    if name == "BGK":
+        return dict(s_e=t["s_nu"], s_eps=t["s_nu"], s_q=t["s_nu"], s_nu=t["s_nu"])
+    if name == "original":
+        return dict(s_e=t["s_e"], s_eps=inp.LL["s_eps"], s_q=inp.LL["s_q"], s_nu=t["s_nu"])
+    return inp.rates("OPT-Z")
+
+
+@pytest.mark.parametrize("name", ["BGK", "original", "optimized"])
+@pytest.mark.parametrize("dtype,tol", [("f64", 0.0), ("f32", 1e-6)])
+def test_point_source_matches_oracle(L, name, dtype, tol):
+    """Section 5.1: 101 x 101 periodic lattice, source at the centre,
+    rho_s = 0.01, period T = 20 (the paper leaves T unstated), t = 80."""
+    n, rs, T, steps = 101, 0.01, 20.0, 80
+    r = point_source_rates(name)
+    h = L.lbm_create(n, n, inp.s_ll(r), 1.0, (0.0, 0.0), L.DTYPES[dtype])
+    try:
+        L.lbm_set_source(h, 50, 50, rs, T)
+        L.lbm_step(h, steps)
+        rho = L.lbm_moments(h)[0]
+        f = L.lbm_get_populations(h)
+    finally:
+        L.lbm_destroy(h)
+    f0 = orc.init_eq(np.ones((n, n)), np.zeros((n, n)), np.zeros((n, n)))
+    f_o = orc.run_source(f0, inp.s_paper(r), steps, (50, 50, rs, T))
+    rho_o = orc.moments(f_o)[0]
+    assert np.max(np.abs(rho_o - 1.0)) > 1e-3 * rs
+    assert np.max(np.abs(rho - rho_o)) <= tol * rs
+    if dtype == "f64":
+        assert np.array_equal(f, f_o)
+
+
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
 def test_tuning_leaves_state_unchanged(L, dtype):
     """Trial launches of the tuner write only the idle buffer; every launch

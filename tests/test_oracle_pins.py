@@ -326,6 +326,31 @@ def test_oracle_pulse_follows_linear_acoustics():
     assert np.linalg.norm(got - free) / np.linalg.norm(free) > err
 
 
+@pytest.mark.parametrize("name", ["BGK", "LL", "OPT-Z"])
+def test_point_source_radiates_at_cs_times_period(name):
+    """The harmonic point source of section 5.1 (density rho0 + rho_s
+    sin(2 pi t / T) forced at one node, u = 0) radiates at the sound speed:
+    the dominant wavenumber of the far field along the source row is
+    2 pi / (c_s T)."""
+    n, T, rs, steps = 161, 20.0, 0.01, 120
+    if name == "BGK":
+        sv = 1.0 / (0.5 + 3e-3)
+        r = dict(s_e=sv, s_eps=sv, s_q=sv, s_nu=sv)
+    else:
+        r = inp.rates(name, nu=1e-3)
+    f = orc.init_eq(np.ones((n, n)), np.zeros((n, n)), np.zeros((n, n)))
+    f = orc.run_source(f, inp.s_paper(r), steps, (80, 80, rs, T))
+    rho = orc.moments(f)[0] - 1.0
+    x = np.arange(100, 145)  # 20 .. 64 nodes from the source, inside the front
+    line = rho[80, 100:145]
+    ks = np.linspace(0.3, 0.8, 501)
+    power = [abs(np.sum((line - line.mean()) * np.exp(-1j * k * x))) for k in ks]
+    k_fit = ks[int(np.argmax(power))]
+    assert abs(k_fit / (2 * math.pi / (vn.CS * T)) - 1) < 0.02
+    # nothing has reached the corners yet (front at c_s t = 69)
+    assert np.max(np.abs(rho[:5, :5])) < 1e-3 * rs
+
+
 # ----------------------------------------------------- printed parameters
 @pytest.fixture(scope="module")
 def golden():
