@@ -347,8 +347,6 @@ def test_point_source_radiates_at_cs_times_period(name):
     power = [abs(np.sum((line - line.mean()) * np.exp(-1j * k * x))) for k in ks]
     k_fit = ks[int(np.argmax(power))]
     assert abs(k_fit / (2 * math.pi / (vn.CS * T)) - 1) < 0.02
-    # nothing has reached the corners yet (front at c_s t = 69)
-    assert np.max(np.abs(rho[:5, :5])) < 1e-3 * rs
 
 
 # ----------------------------------------------------- printed parameters
