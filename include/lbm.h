@@ -222,6 +222,23 @@ int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void *ctx);
 const char *lbm_strerror(int code);
 const char *lbm_last_error(void);
 
+/* ------------------------------------------------- von Neumann analysis */
+/* lbm_vn_eigs -- eigenvalues of the von Neumann amplification matrix of
+ * section 4.1, G(k) = diag(exp(-i k.c_j)) M^-1 Psi M, with Psi the
+ * linearized relaxation of section 2.3 about rho = 1 and the mean flow
+ * (U, V), for n cases on the GPU (one thread per case, FP64: Householder
+ * Hessenberg reduction and shifted QR).  Host arrays, caller-owned:
+ *   kx, ky, U, V  n each;  S  9 n, case c's rates in Lallemand-Luo order at
+ *   S[9c .. 9c+8];  eig  18 n, the 9 eigenvalues of case c as (re, im)
+ *   pairs at eig[18c ..], in no particular order.
+ * lambda = exp(-i omega): damping per step -ln|lambda|, phase speed
+ * -arg(lambda)/|k|.  *unconverged (may be NULL) counts eigenvalues whose QR
+ * iteration reached its limit of 60 sweeps (returns LBM_ETIMEOUT then).
+ * Synchronizes; allocates device memory for the call. */
+int lbm_vn_eigs(int n, const double *kx, const double *ky, const double *U,
+                const double *V, const double *S, double *eig,
+                int *unconverged);
+
 /* ------------------------------------------------------------- batches */
 /* Many independent lattices advanced together: every time step is ONE
  * kernel launch per storage type over a flattened (lattice, row group,

@@ -26,6 +26,7 @@ UNITS = {
     "aux.cu": ["-fmad=false"],
     "serve.cu": [],
     "drift_noalloc.cu": [],
+    "vn.cu": [],
 }
 HEADERS = ["lbm_internal.h", "d2q9_pull.cuh", "collide.cuh", "step_impl.cuh"]
 

@@ -1,0 +1,291 @@
+// Batched von Neumann analysis of the linearized D2Q9 MRT scheme on the
+// device (lbm_vn_eigs in include/lbm.h).
+//
+// For every case the kernel builds the amplification matrix of section 4.1,
+//   G(k) = diag(exp(-i k.c_j)) M^-1 Psi M,
+// with Psi the linearized relaxation of section 2.3 about rho = 1 and the
+// mean flow (U, V) (Psi = I - S + S J, J the Jacobian of the equilibrium
+// moments with respect to rho, jx, jy), and returns its 9 eigenvalues
+// lambda = exp(-i omega): per-step damping -ln|lambda| and phase speed
+// -arg(lambda) / |k|.  One thread per case, FP64 complex arithmetic:
+// Householder reduction to upper Hessenberg form, then shifted QR sweeps
+// (Givens rotations, Wilkinson shifts, deflation on negligible subdiagonal
+// entries) with a bounded number of sweeps per eigenvalue.
+#include <math.h>
+
+#include <new>
+#include <string>
+
+#include "lbm_internal.h"
+
+namespace {
+
+struct cplx {
+  double re, im;
+};
+__device__ __forceinline__ cplx mk(double r, double i) { return cplx{r, i}; }
+__device__ __forceinline__ cplx add(cplx a, cplx b) { return mk(a.re + b.re, a.im + b.im); }
+__device__ __forceinline__ cplx sub(cplx a, cplx b) { return mk(a.re - b.re, a.im - b.im); }
+__device__ __forceinline__ cplx mul(cplx a, cplx b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+__device__ __forceinline__ cplx conj(cplx a) { return mk(a.re, -a.im); }
+__device__ __forceinline__ cplx scale(cplx a, double s) { return mk(a.re * s, a.im * s); }
+__device__ __forceinline__ double cabs(cplx a) { return hypot(a.re, a.im); }
+__device__ cplx csqrt(cplx a) {
+  const double r = cabs(a);
+  if (r == 0.0) return mk(0, 0);
+  double x = sqrt(0.5 * (r + fabs(a.re)));
+  double y = a.im / (2.0 * x);
+  if (a.re >= 0) return mk(x, y);
+  return mk(fabs(y), a.im >= 0 ? x : -x);
+}
+
+constexpr int N = 9;
+
+// Lallemand-Luo D2Q9 moment matrix in the paper's row order and row norms
+__device__ __forceinline__ int mrow(int k, int j) {
+  constexpr int T[9][9] = {
+      {1, 1, 1, 1, 1, 1, 1, 1, 1},     {0, 1, 0, -1, 0, 1, -1, -1, 1},
+      {0, 0, 1, 0, -1, 1, 1, -1, -1},  {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+      {4, -2, -2, -2, -2, 1, 1, 1, 1}, {0, -2, 0, 2, 0, 1, -1, -1, 1},
+      {0, 0, -2, 0, 2, 1, 1, -1, -1},  {0, 1, -1, 1, -1, 0, 0, 0, 0},
+      {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+  return T[k][j];
+}
+__device__ __forceinline__ double rnorm(int k) {
+  return k == 0 ? 9.0 : (k <= 2 ? 6.0 : (k <= 4 ? 36.0 : (k <= 6 ? 12.0 : 4.0)));
+}
+
+// Psi about rho = 1, j = (U, V): rows 0..2 identity; row k >= 3 has 1 - s_k
+// on the diagonal and s_k dm^eq_k / d(rho, jx, jy) in columns 0..2.
+__device__ void build_psi(const double s[9], double U, double V, double P[9][9]) {
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) P[i][j] = (i == j) ? 1.0 : 0.0;
+  const double u2 = U * U + V * V;
+  // Jacobian of {-2 rho + 3|j|^2/rho, rho - 3|j|^2/rho, -jx, -jy,
+  // (jx^2 - jy^2)/rho, jx jy/rho} at (1, U, V)
+  const double J[6][3] = {{-2.0 - 3.0 * u2, 6.0 * U, 6.0 * V},
+                          {1.0 + 3.0 * u2, -6.0 * U, -6.0 * V},
+                          {0.0, -1.0, 0.0},
+                          {0.0, 0.0, -1.0},
+                          {-(U * U - V * V), 2.0 * U, -2.0 * V},
+                          {-U * V, V, U}};
+  for (int r = 0; r < 6; ++r) {
+    const int k = 3 + r;
+    P[k][k] = 1.0 - s[k];
+    for (int c = 0; c < 3; ++c) P[k][c] = s[k] * J[r][c];
+  }
+}
+
+// Householder reduction of A to upper Hessenberg form, in place
+__device__ void hessenberg(cplx A[9][9]) {
+  for (int k = 0; k < N - 2; ++k) {
+    double nrm = 0;
+    for (int i = k + 1; i < N; ++i) nrm += A[i][k].re * A[i][k].re + A[i][k].im * A[i][k].im;
+    nrm = sqrt(nrm);
+    if (nrm == 0.0) continue;
+    const cplx x0 = A[k + 1][k];
+    const double a0 = cabs(x0);
+    const cplx ph = a0 > 0 ? scale(x0, 1.0 / a0) : mk(1, 0);
+    cplx v[9];
+    for (int i = 0; i < N; ++i) v[i] = mk(0, 0);
+    // v = x + e^{i arg x0} ||x|| e1, normalized
+    v[k + 1] = add(x0, scale(ph, nrm));
+    for (int i = k + 2; i < N; ++i) v[i] = A[i][k];
+    double vn = 0;
+    for (int i = k + 1; i < N; ++i) vn += v[i].re * v[i].re + v[i].im * v[i].im;
+    vn = sqrt(vn);
+    if (vn == 0.0) continue;
+    for (int i = k + 1; i < N; ++i) v[i] = scale(v[i], 1.0 / vn);
+    // A <- (I - 2 v v^H) A
+    for (int j = 0; j < N; ++j) {
+      cplx d = mk(0, 0);
+      for (int i = k + 1; i < N; ++i) d = add(d, mul(conj(v[i]), A[i][j]));
+      for (int i = k + 1; i < N; ++i) A[i][j] = sub(A[i][j], scale(mul(v[i], d), 2.0));
+    }
+    // A <- A (I - 2 v v^H)
+    for (int i = 0; i < N; ++i) {
+      cplx d = mk(0, 0);
+      for (int j = k + 1; j < N; ++j) d = add(d, mul(A[i][j], v[j]));
+      for (int j = k + 1; j < N; ++j) A[i][j] = sub(A[i][j], scale(mul(d, conj(v[j])), 2.0));
+    }
+    for (int i = k + 2; i < N; ++i) A[i][k] = mk(0, 0);
+  }
+}
+
+// Eigenvalues of the Hessenberg matrix H by shifted QR; returns the number
+// of eigenvalues that did not converge within the sweep limit (reported as
+// the current diagonal entries).
+__device__ int hqr(cplx H[9][9], cplx ev[9]) {
+  const double eps = 2.220446049250313e-16;
+  int hi = N - 1, iter = 0, failed = 0;
+  while (hi >= 0) {
+    if (hi == 0) {
+      ev[0] = H[0][0];
+      break;
+    }
+    int l = hi;
+    for (; l > 0; --l) {
+      const double s = cabs(H[l - 1][l - 1]) + cabs(H[l][l]);
+      if (cabs(H[l][l - 1]) <= eps * (s > 0 ? s : 1.0)) {
+        H[l][l - 1] = mk(0, 0);
+        break;
+      }
+    }
+    if (l == hi) {  // one eigenvalue deflates
+      ev[hi] = H[hi][hi];
+      --hi;
+      iter = 0;
+      continue;
+    }
+    if (iter >= 60) {  // give up on this one, keep going
+      ev[hi] = H[hi][hi];
+      ++failed;
+      --hi;
+      iter = 0;
+      continue;
+    }
+    // Wilkinson shift from the trailing 2x2 block; an exceptional shift
+    // every 11 sweeps breaks cycles
+    cplx mu;
+    if (iter > 0 && iter % 11 == 0) {
+      mu = add(H[hi][hi], mk(fabs(H[hi][hi - 1].re) + fabs(H[hi - 1][hi > 1 ? hi - 2 : 0].re), 0));
+    } else {
+      const cplx a = H[hi - 1][hi - 1], b = H[hi - 1][hi], c = H[hi][hi - 1], d = H[hi][hi];
+      const cplx half_tr = scale(add(a, d), 0.5);
+      const cplx det = sub(mul(a, d), mul(b, c));
+      const cplx disc = csqrt(sub(mul(half_tr, half_tr), det));
+      const cplx m1 = add(half_tr, disc), m2 = sub(half_tr, disc);
+      mu = cabs(sub(m1, d)) < cabs(sub(m2, d)) ? m1 : m2;
+    }
+    ++iter;
+    // one QR sweep on rows/columns l..hi of H - mu I
+    double gc[9];
+    cplx gs[9];
+    for (int i = l; i <= hi; ++i) H[i][i] = sub(H[i][i], mu);
+    for (int k = l; k < hi; ++k) {
+      const cplx x = H[k][k], y = H[k + 1][k];
+      const double ax = cabs(x), r = hypot(ax, cabs(y));
+      double c;
+      cplx s;
+      if (r == 0.0) {
+        c = 1.0;
+        s = mk(0, 0);
+      } else if (ax == 0.0) {
+        c = 0.0;  // x = 0: swap the rows (s = 1)
+        s = mk(1, 0);
+      } else {
+        c = ax / r;
+        s = scale(mul(scale(x, 1.0 / ax), conj(y)), 1.0 / r);
+      }
+      gc[k] = c;
+      gs[k] = s;
+      for (int j = k; j <= hi; ++j) {
+        const cplx hk = H[k][j], hk1 = H[k + 1][j];
+        H[k][j] = add(scale(hk, c), mul(s, hk1));
+        H[k + 1][j] = sub(scale(hk1, c), mul(conj(s), hk));
+      }
+    }
+    for (int k = l; k < hi; ++k) {
+      const double c = gc[k];
+      const cplx s = gs[k];
+      const int top = k + 2 < hi ? k + 2 : hi;
+      for (int i = l; i <= top; ++i) {
+        const cplx hk = H[i][k], hk1 = H[i][k + 1];
+        H[i][k] = add(scale(hk, c), mul(hk1, conj(s)));
+        H[i][k + 1] = sub(scale(hk1, c), mul(hk, s));
+      }
+    }
+    for (int i = l; i <= hi; ++i) H[i][i] = add(H[i][i], mu);
+  }
+  return failed;
+}
+
+struct VnCase {
+  double kx, ky, U, V;
+  double s[9];  // paper order
+};
+
+__global__ void k_vn_eigs(const VnCase *__restrict__ cases, int n, double *__restrict__ out,
+                          int *__restrict__ failed) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const VnCase K = cases[c];
+  double P[9][9];
+  build_psi(K.s, K.U, K.V, P);
+  // C = M^-1 Psi M = M^T D^-1 Psi M
+  double PM[9][9];
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      double acc = 0;
+      for (int k = 0; k < N; ++k) acc += P[i][k] * mrow(k, j);
+      PM[i][j] = acc;
+    }
+  cplx G[9][9];
+  for (int i = 0; i < N; ++i) {
+    // phase of streaming direction i: exp(-i k.c_i)
+    const double ph = -(K.kx * lbm::CXd(i) + K.ky * lbm::CYd(i));
+    const cplx e = mk(cos(ph), sin(ph));
+    for (int j = 0; j < N; ++j) {
+      double acc = 0;
+      for (int k = 0; k < N; ++k) acc += (mrow(k, i) / rnorm(k)) * PM[k][j];
+      G[i][j] = scale(e, acc);
+    }
+  }
+  hessenberg(G);
+  cplx ev[9];
+  const int f = hqr(G, ev);
+  for (int i = 0; i < N; ++i) {
+    out[(long long)c * 18 + 2 * i] = ev[i].re;
+    out[(long long)c * 18 + 2 * i + 1] = ev[i].im;
+  }
+  if (f) atomicAdd(failed, f);
+}
+
+}  // namespace
+
+extern "C" int lbm_vn_eigs(int n, const double *kx, const double *ky, const double *U,
+                           const double *V, const double *S, double *eig, int *unconverged) {
+  using namespace lbm;
+  if (n < 0 || (n > 0 && (!kx || !ky || !U || !V || !S || !eig))) {
+    set_error("lbm_vn_eigs: bad arguments");
+    return LBM_EINVAL;
+  }
+  if (unconverged) *unconverged = 0;
+  if (n == 0) return LBM_OK;
+  const int ll_of_paper[9] = {0, 3, 5, 1, 2, 4, 6, 7, 8};
+  VnCase *h = new (std::nothrow) VnCase[n];
+  if (!h) return LBM_ENOMEM;
+  for (int c = 0; c < n; ++c) {
+    h[c].kx = kx[c];
+    h[c].ky = ky[c];
+    h[c].U = U[c];
+    h[c].V = V[c];
+    for (int k = 0; k < 9; ++k) h[c].s[k] = S[9 * c + ll_of_paper[k]];
+  }
+  VnCase *d_cases = (VnCase *)dev_alloc(sizeof(VnCase) * n);
+  double *d_out = (double *)dev_alloc(sizeof(double) * 18 * n);
+  int *d_fail = (int *)dev_alloc(sizeof(int));
+  cudaError_t e = (!d_cases || !d_out || !d_fail) ? cudaErrorMemoryAllocation : cudaSuccess;
+  if (e == cudaSuccess) e = cudaMemcpy(d_cases, h, sizeof(VnCase) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(d_fail, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    k_vn_eigs<<<(n + 127) / 128, 128>>>(d_cases, n, d_out, d_fail);
+    e = cudaGetLastError();
+  }
+  int fails = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(eig, d_out, sizeof(double) * 18 * n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&fails, d_fail, sizeof(int), cudaMemcpyDeviceToHost);
+  dev_free(d_cases);
+  dev_free(d_out);
+  dev_free(d_fail);
+  delete[] h;
+  if (e != cudaSuccess) {
+    set_error(std::string("lbm_vn_eigs: ") + cudaGetErrorString(e));
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+  }
+  if (unconverged) *unconverged = fails;
+  return fails ? LBM_ETIMEOUT : LBM_OK;
+}

@@ -75,6 +75,8 @@ _SIGS = {
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+    "lbm_vn_eigs": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp,
+                                   ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_step": (ctypes.c_int, [_vp, ctypes.c_long]),
     "lbm_batch_drift": (ctypes.c_int, [_vp, _dp]),
     "lbm_batch_destroy": (ctypes.c_int, [_vp]),
@@ -283,6 +285,20 @@ def lbm_set_allocator(alloc_fn=None, free_fn=None, ctx=None):
     a = ctypes.cast(alloc_fn, _vp) if alloc_fn is not None else None
     f = ctypes.cast(free_fn, _vp) if free_fn is not None else None
     _ck(load().lbm_set_allocator(a, f, ctx), "lbm_set_allocator")
+
+
+def lbm_vn_eigs(kx, ky, U, V, S):
+    """Eigenvalues (n, 9) complex of G(k) for n cases; S is (n, 9) or (9,)
+    in Lallemand-Luo order.  Raises if some QR iteration did not converge."""
+    kx = _f64(np.atleast_1d(kx))
+    n = kx.size
+    ky, U, V = (_f64(np.broadcast_to(np.asarray(a, dtype=np.float64), (n,))) for a in (ky, U, V))
+    S = _f64(np.broadcast_to(np.asarray(S, dtype=np.float64), (n, 9)))
+    out = np.empty((n, 18))
+    bad = ctypes.c_int()
+    _ck(load().lbm_vn_eigs(n, _ptr(kx), _ptr(ky), _ptr(U), _ptr(V), _ptr(S), _ptr(out),
+                           ctypes.byref(bad)), "lbm_vn_eigs")
+    return out[:, 0::2] + 1j * out[:, 1::2]
 
 
 def lbm_batch_create(handles):

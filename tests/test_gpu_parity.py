@@ -273,10 +273,11 @@ def test_translation_shifts_the_result(L, dtype):
     assert np.array_equal(np.roll(rho_a, (5, 11), axis=(0, 1)), rho_b)
 
 
-@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-6)])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-11), ("f32", 1e-6)])
 def test_centred_pulse_keeps_d4_symmetry(L, dtype, tol):
     """A pulse centred on a node of a square lattice at rest stays symmetric
-    under the 8 symmetries of the square (up to rounding)."""
+    under the 8 symmetries of the square, up to rounding: mirrored nodes
+    add their populations in different orders (FP64: ~1e-15 on rho ~ 1)."""
     n, steps, amp = 48, 120, 1e-3
     r = inp.rates("LL", nu=1e-3)
     fields = inp.gaussian_pulse(n, n, amp, 4.0, 24.0, 24.0)

@@ -151,3 +151,56 @@ def test_plane_wave_damping_and_speed(L, dtype):
         print("  %.1f %-5s %3d  %.4e  %.4e  %.6f  %.6f" % row)
     assert worst_c < 1e-4
     assert worst_d < 0.05
+
+
+# ------------------------------------------------ batched VN sweep on GPU
+def match_err(a, b):
+    """Largest distance between the eigenvalue multisets a and b."""
+    b = list(b)
+    err = 0.0
+    for x in a:
+        j = int(np.argmin([abs(x - y) for y in b]))
+        err = max(err, abs(x - b[j]))
+        b.pop(j)
+    return err
+
+
+def test_gpu_vn_eigenvalues_match_numpy(L):
+    """lbm_vn_eigs against numpy's eigvals of oracle.vn's independently built
+    G(k): random wavevectors, mean flows and rate sets, plus k = 0."""
+    rng = np.random.default_rng(7)
+    names = ["LL", "OPT", "OPT-Z", "LL*", "OPT-B"]
+    n = 400
+    kx = rng.uniform(-np.pi, np.pi, n)
+    ky = rng.uniform(-np.pi, np.pi, n)
+    U = rng.uniform(-0.2, 0.2, n)
+    V = rng.uniform(-0.2, 0.2, n)
+    kx[:3] = 0.0
+    ky[:3] = 0.0
+    sets = [inp.rates(names[i % len(names)], nu=1e-3) for i in range(n)]
+    S = np.array([inp.s_ll(r) for r in sets])
+    got = L.lbm_vn_eigs(kx, ky, U, V, S)
+    worst = 0.0
+    for c in range(n):
+        want = vn.eigs(kx[c], ky[c], U[c], V[c], inp.s_paper(sets[c]))
+        worst = max(worst, match_err(got[c], want))
+    assert worst < 1e-11
+
+
+@pytest.mark.parametrize("theta", [math.pi / 6, math.pi / 4])
+def test_gpu_vn_sweep_unstable_band(L, theta):
+    """Section 4.2 through the GPU sweep: at sigma_e = sigma_nu = 0.0025 the
+    original free rates have a growing mode for 0.75 < k < 1.75 off the axes
+    and the optimized Table 1 group A rates have none."""
+    t = inp.TABLE1["A"]
+    opt = {k_: 1.0 / (t["sigma_" + k_[2:]] + 0.5) for k_ in ("s_e", "s_eps", "s_q", "s_nu")}
+    orig = dict(opt, s_eps=inp.LL["s_eps"], s_q=inp.LL["s_q"])
+    k = np.linspace(0.01, 3.1, 311)
+    for rates, unstable in ((orig, True), (opt, False)):
+        lam = L.lbm_vn_eigs(k * math.cos(theta), k * math.sin(theta), 0.0, 0.0, inp.s_ll(rates))
+        growth = np.max(np.abs(lam), axis=1)
+        band = (k > 0.8) & (k < 1.6)
+        if unstable:
+            assert np.max(growth[band]) > 1.005
+        else:
+            assert np.max(growth[band]) < 1.0 + 1e-12
