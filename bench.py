@@ -51,7 +51,8 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="batched", choices=["batched", "large", "serving"])
+    p.add_argument("--workload", default="batched",
+                   choices=["batched", "large", "serving", "vn"])
     p.add_argument("--lattices", type=int, default=512)
     p.add_argument("--lbm-steps", type=int, default=500)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -460,6 +461,44 @@ def bench_serving(args, L, torch):
             "server": st}
 
 
+def bench_vn(args, L, torch):
+    """Von Neumann sweep (sections 4.1-4.2): eigenvalues of G(k) on a grid
+    of 256 |k| x 64 directions x U in {0, 0.1} x 4 rate sets."""
+    import oracle.vn as ovn
+
+    kk = np.linspace(0.0, math.pi, 257)[1:]
+    th = np.linspace(0.0, 2 * math.pi, 64, endpoint=False)
+    K, T = np.meshgrid(kk, th, indexing="ij")
+    kx, ky = (K * np.cos(T)).ravel(), (K * np.sin(T)).ravel()
+    cases = []
+    for U in (0.0, 0.1):
+        for name in ("LL", "LL*", "OPT", "OPT-Z"):
+            cases.append((U, inp.rates(name, nu=1e-3)))
+    n = kx.size * len(cases)
+    KX = np.tile(kx, len(cases))
+    KY = np.tile(ky, len(cases))
+    UU = np.repeat([c[0] for c in cases], kx.size)
+    SS = np.repeat(np.array([inp.s_ll(c[1]) for c in cases]), kx.size, axis=0)
+    L.lbm_vn_eigs(KX[:1000], KY[:1000], UU[:1000], 0.0, SS[:1000])  # warm-up
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        L.lbm_vn_eigs(KX, KY, UU, 0.0, SS)
+        times.append(time.perf_counter() - t0)
+    gpu = n / min(times)
+    # CPU baseline: numpy eigvals of the oracle's matrices for one rate set
+    t0 = time.perf_counter()
+    G = ovn.amplification(kx, ky, 0.1, 0.0, inp.s_paper(cases[-1][1]))
+    np.linalg.eigvals(G)
+    cpu = kx.size / (time.perf_counter() - t0)
+    return {"metric": "von Neumann eigenproblems (9x9 complex) per second",
+            "value": round(gpu, 1), "unit": "problems/s", "higher_is_better": True,
+            "config": {"workload": "vn-sweep-%d-cases" % n},
+            "note": "host arrays in and out, device allocation per call included",
+            "cpu_baseline": {"value": round(cpu, 1), "unit": "problems/s", "cores": 1,
+                             "kind": "oracle", "sample": "%d cases, numpy eigvals" % kx.size}}
+
+
 def reference_arm(args):
     """The CPU oracle timed as the reference implementation."""
     specs = inp.batch_specs(args.lattices, seed=1107 + 4, steps=args.lbm_steps)
@@ -512,6 +551,10 @@ def main():
     if args.workload == "serving":
         if rank == 0:
             print(json.dumps(bench_serving(args, L, torch)))
+        return
+    if args.workload == "vn":
+        if rank == 0:
+            print(json.dumps(bench_vn(args, L, torch)))
         return
     line, specs = bench_batched(args, L, torch, rank, ws)
     if rank == 0:
