@@ -161,6 +161,12 @@ struct Geom {
   int nchunks;      // vectors per row: ceil(nx / V)
   long long plane;  // pitch * ny
   long long tasks;  // warp tasks per step: ceil(nchunks * ny / 32)
+  // row = chunk / nchunks as (chunk * dmul) >> dshift, exact for chunk
+  // indices below 2^31 (dshift = 31 + ceil(log2 nchunks), dmul =
+  // ceil(2^dshift / nchunks)); small = the lattice's chunks (+ one warp) fit
+  unsigned long long dmul;
+  int dshift;
+  int small;
 };
 
 // Position of this lane for task `task` of a lattice.
@@ -175,8 +181,16 @@ __device__ __forceinline__ LanePos lane_pos(const Geom &g, long long task, int l
   LanePos p;
   const long long c = task * 32 + lane;
   p.active = c < (long long)g.nchunks * g.ny;
-  const int y = p.active ? (int)(c / g.nchunks) : 0;
-  const int xc = p.active ? (int)(c - (long long)y * g.nchunks) : 0;
+  int y, xc;
+  if (g.small) {  // multiply-shift division
+    const unsigned cu = (unsigned)c;
+    y = (int)(((unsigned long long)cu * g.dmul) >> g.dshift);
+    xc = (int)(cu - (unsigned)y * (unsigned)g.nchunks);
+  } else {
+    y = (int)(c / g.nchunks);
+    xc = (int)(c - (long long)y * g.nchunks);
+  }
+  if (!p.active) y = xc = 0;
   p.y = y;
   p.x0 = xc * V;
   p.first = lane == 0 || xc == 0;

@@ -79,6 +79,11 @@ static Geom make_geom(int nx, int ny, int V, int esize) {
   g.nchunks = (nx + V - 1) / V;
   g.plane = (long long)g.pitch * ny;
   g.tasks = ((long long)g.nchunks * ny + 31) / 32;
+  int k = 31;
+  while ((1LL << (k - 31)) < (long long)g.nchunks) ++k;  // 31 + ceil(log2 nchunks)
+  g.dshift = k;
+  g.dmul = ((1ULL << k) + (unsigned long long)g.nchunks - 1) / (unsigned long long)g.nchunks;
+  g.small = g.tasks * 32 < (1LL << 31) ? 1 : 0;
   return g;
 }
 
