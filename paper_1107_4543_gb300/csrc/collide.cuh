@@ -31,9 +31,11 @@ struct DevParams {
   float scale, inv_scale;        // FP16 storage: stored = f' * scale
 };
 
-// a * (h + l) with the low part folded in by one FMA
+// a * (h + l) with the low part folded in by one FMA, or a * h alone when
+// the low parts are not wanted
+template <bool PRECISE>
 __device__ __forceinline__ float mul_hl(float a, float h, float l) {
-  return fmaf(a, h, a * l);
+  return PRECISE ? fmaf(a, h, a * l) : a * h;
 }
 
 // Deviation form: f' = f - f^eq(rho0, j0); the base carries the moments
@@ -50,6 +52,15 @@ __device__ __forceinline__ float mul_hl(float a, float h, float l) {
 // Measured against the FP64 oracle this keeps the 2000-step plane wave of
 // the optimized sets within ~5e-7 of the amplitude (3.5e-6 with the
 // straightforward FP32 formulation).
+//
+// PRECISE: carry the rates and reference-state constants as hi + lo pairs
+// (FP32 storage); the 16-bit storage types round far more than the lo parts
+// correct and use the hi parts alone.
+// SCALED: f holds f' * scale (FP16 storage) and stays in those units: the
+// step is linear in f' except for the three quadratic terms and rho'/rho,
+// which take the factor inv_scale; with power-of-two scales this equals
+// collide-then-rescale bit for bit and saves the per-population rescaling.
+template <bool PRECISE, bool SCALED>
 __device__ __forceinline__ void collide_dev(float &f0, float &f1, float &f2, float &f3,
                                             float &f4, float &f5, float &f6, float &f7,
                                             float &f8, const DevParams &P) {
@@ -66,13 +77,20 @@ __device__ __forceinline__ void collide_dev(float &f0, float &f1, float &f2, flo
   const float jy_p = d24 + dyd;
 
   // m^eq(rho, j) - m^eq(rho0, j0) for the three quadratic terms
-  const float c = rho_p / (P.rho0 + rho_p);  // rho'/rho
-  const float tx = fmaf(2.0f * P.jx0, jx_p, jx_p * jx_p);  // jx^2 - jx0^2
-  const float ty = fmaf(2.0f * P.jy0, jy_p, jy_p * jy_p);
-  const float txy = fmaf(P.jx0, jy_p, fmaf(jx_p, P.jy0, jx_p * jy_p));  // jx jy - jx0 jy0
-  const float nj = mul_hl(fmaf(P.rho0, tx + ty, -mul_hl(rho_p, P.q0h, P.q0l)), P.i2h, P.i2l);
-  const float np = mul_hl(fmaf(P.rho0, tx - ty, -mul_hl(rho_p, P.d0h, P.d0l)), P.i2h, P.i2l);
-  const float nx = mul_hl(fmaf(P.rho0, txy, -mul_hl(rho_p, P.x0h, P.x0l)), P.i2h, P.i2l);
+  const float rho_phys = SCALED ? rho_p * P.inv_scale : rho_p;
+  const float c = rho_phys / (P.rho0 + rho_phys);  // rho'/rho
+  const float jxx = SCALED ? (jx_p * jx_p) * P.inv_scale : jx_p * jx_p;
+  const float jyy = SCALED ? (jy_p * jy_p) * P.inv_scale : jy_p * jy_p;
+  const float jxy = SCALED ? (jx_p * jy_p) * P.inv_scale : jx_p * jy_p;
+  const float tx = fmaf(2.0f * P.jx0, jx_p, jxx);  // jx^2 - jx0^2
+  const float ty = fmaf(2.0f * P.jy0, jy_p, jyy);
+  const float txy = fmaf(P.jx0, jy_p, fmaf(jx_p, P.jy0, jxy));  // jx jy - jx0 jy0
+  const float nj =
+      mul_hl<PRECISE>(fmaf(P.rho0, tx + ty, -mul_hl<PRECISE>(rho_p, P.q0h, P.q0l)), P.i2h, P.i2l);
+  const float np =
+      mul_hl<PRECISE>(fmaf(P.rho0, tx - ty, -mul_hl<PRECISE>(rho_p, P.d0h, P.d0l)), P.i2h, P.i2l);
+  const float nx =
+      mul_hl<PRECISE>(fmaf(P.rho0, txy, -mul_hl<PRECISE>(rho_p, P.x0h, P.x0l)), P.i2h, P.i2l);
   const float djsq = fmaf(-nj, c, nj);  // |j|^2/rho - |j0|^2/rho0
   const float dpxx = fmaf(-np, c, np);  // (jx^2 - jy^2)/rho - (..)0/rho0
   const float dpxy = fmaf(-nx, c, nx);  // jx jy / rho - jx0 jy0 / rho0
@@ -84,12 +102,12 @@ __device__ __forceinline__ void collide_dev(float &f0, float &f1, float &f2, flo
   const float n6 = fmaf(2.0f, dyd, -d24);                            // qy' + jy'
   const float n7 = (s13 - s24) - dpxx;
   const float n8 = (s57 - s68) - dpxy;
-  const float r3 = mul_hl(n3, P.k3, P.l3);
-  const float r4 = mul_hl(n4, P.k4, P.l4);
-  const float r5 = mul_hl(n5, P.k5, P.l5);
-  const float r6 = mul_hl(n6, P.k6, P.l6);
-  const float r7 = mul_hl(n7, P.k7, P.l7);
-  const float r8 = mul_hl(n8, P.k8, P.l8);
+  const float r3 = mul_hl<PRECISE>(n3, P.k3, P.l3);
+  const float r4 = mul_hl<PRECISE>(n4, P.k4, P.l4);
+  const float r5 = mul_hl<PRECISE>(n5, P.k5, P.l5);
+  const float r6 = mul_hl<PRECISE>(n6, P.k6, P.l6);
+  const float r7 = mul_hl<PRECISE>(n7, P.k7, P.l7);
+  const float r8 = mul_hl<PRECISE>(n8, P.k8, P.l8);
 
   // f <- f - M^T r: columns of M for each velocity
   const float a = fmaf(2.0f, r4, r3);     // axis velocities: -r3 - 2 r4

@@ -21,15 +21,18 @@ __device__ __forceinline__ void step_task(const T *__restrict__ src, T *__restri
                                           const Geom &g, const DevParams &P,
                                           long long task, int lane) {
   constexpr int V = Elem<T>::V;
-  constexpr bool SCALED = std::is_same<T, __half>::value;  // only FP16 is scaled
+  // FP16 is stored scaled and collided in the scaled units; FP32 carries
+  // hi + lo constants (see collide_dev)
+  constexpr bool SCALED = std::is_same<T, __half>::value;
+  constexpr bool PRECISE = std::is_same<T, float>::value;
   LanePos p = lane_pos<V>(g, task, lane);
   float f[9][V];
-  pull9<T, SCALED>(src, g, p, P.inv_scale, f);
+  pull9<T, false>(src, g, p, 1.0f, f);
 #pragma unroll
   for (int e = 0; e < V; ++e)
-    collide_dev(f[0][e], f[1][e], f[2][e], f[3][e], f[4][e], f[5][e], f[6][e], f[7][e],
-                f[8][e], P);
-  store9<T, SCALED>(dst, g, p, P.scale, f);
+    collide_dev<PRECISE, SCALED>(f[0][e], f[1][e], f[2][e], f[3][e], f[4][e], f[5][e], f[6][e],
+                                 f[7][e], f[8][e], P);
+  store9<T, false>(dst, g, p, 1.0f, f);
 }
 
 // MINB: minimum resident 256-thread blocks per SM asked of the compiler,
