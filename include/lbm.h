@@ -134,6 +134,10 @@ int lbm_set_source(lbm_handle h, int x, int y, double amplitude, double period);
  * within the process.  LBM_F64 has one variant (times -1).  Synchronizes. */
 #define LBM_TUNE_VARIANTS 3
 int lbm_tune(lbm_handle h, double *times_ms, int *chosen);
+/* Use launch variant `variant` (0 .. LBM_TUNE_VARIANTS-1) for later steps,
+ * without timing (no automatic tuning afterwards).  Every variant computes
+ * the same result; they differ only in speed. */
+int lbm_set_variant(lbm_handle h, int variant);
 
 /* lbm_moments -- rho, ux, uy (host, ny x nx) at the current time: the
  * moments of the pre-collision populations, u = j / rho.  Synchronizes. */
@@ -257,8 +261,15 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out);
 int lbm_batch_step(lbm_batch b, long n);
 /* As lbm_tune for the batch's launches (one variant for all its storage
  * types; the first lbm_batch_step of a batch of >= 2^20 nodes tunes unless
- * LBM_AUTOTUNE=0).  Members' states do not change. */
+ * LBM_AUTOTUNE=0).  Batches have LBM_BATCH_TUNE_VARIANTS variants: the
+ * three register caps with one warp per task, then the same caps with a
+ * persistent grid in which each warp takes a contiguous range of tasks.
+ * times_ms receives LBM_BATCH_TUNE_VARIANTS entries.  Members' states do
+ * not change. */
+#define LBM_BATCH_TUNE_VARIANTS 6
 int lbm_batch_tune(lbm_batch b, double *times_ms, int *chosen);
+/* As lbm_set_variant for a batch (0 .. LBM_BATCH_TUNE_VARIANTS-1). */
+int lbm_batch_set_variant(lbm_batch b, int variant);
 /* The sums of lbm_drift for every member at once (out: 4 doubles per member,
  * in member order): one reduction launch pair for the whole batch,
  * reproducible per member.  Synchronizes the batch stream; returns

@@ -644,6 +644,15 @@ int lbm_set_source(lbm_handle h, int x, int y, double amplitude, double period) 
   return LBM_OK;
 }
 
+int lbm_set_variant(lbm_handle h, int variant) {
+  REQUIRE(h != nullptr, "null handle");
+  REQUIRE(variant >= 0 && variant < kStepVariants, "no such launch variant");
+  if (h->L.variant != variant) free_graph(h);
+  h->L.variant = variant;
+  h->tuned = true;
+  return LBM_OK;
+}
+
 int lbm_tune(lbm_handle h, double *times_ms, int *chosen) {
   REQUIRE(h != nullptr, "null handle");
   REQUIRE(h->batch == nullptr, "lattice is a batch member; tune the batch");
@@ -815,7 +824,7 @@ static int tune_batch(lbm_batch_ctx *b, double *times) {
   const int reps = tune_reps(bytes);
   double best = 1e300;
   int bv = b->variant;
-  for (int v = 0; v < kStepVariants; ++v) {
+  for (int v = 0; v < kBatchVariants; ++v) {
     double ms = 0;
     int rc = time_launches(b->stream, reps,
                            [&](int) { return batch_launch_all(b, b->parity, b->stream, v); }, &ms);
@@ -864,7 +873,7 @@ namespace lbm {
 // Pin a batch's launch variant (no automatic tuning); -1 leaves it to the
 // tuner.  Used by the server, which tunes once and reuses the choice.
 void batch_pin_variant(lbm_batch_ctx *b, int variant) {
-  if (variant < 0 || variant >= kStepVariants) return;
+  if (variant < 0 || variant >= kBatchVariants) return;
   if (b->variant != variant && b->graph) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -1115,6 +1124,13 @@ int lbm_batch_step(lbm_batch b, long n) {
   return LBM_OK;
 }
 
+
+int lbm_batch_set_variant(lbm_batch b, int variant) {
+  REQUIRE(b != nullptr, "null batch");
+  REQUIRE(variant >= 0 && variant < kBatchVariants, "no such launch variant");
+  batch_pin_variant(b, variant);
+  return LBM_OK;
+}
 
 int lbm_batch_tune(lbm_batch b, double *times_ms, int *chosen) {
   REQUIRE(b != nullptr, "null batch");

@@ -36,6 +36,9 @@ struct BatchEntry {
 // `variant` selects the register cap of the deviation step kernels
 // (0, 1, 2: at least 1, 2, 3 resident 256-thread blocks per SM).
 constexpr int kStepVariants = 3;
+// batched launches add kStepVariants persistent variants (the same register
+// caps, contiguous task ranges per warp)
+constexpr int kBatchVariants = 2 * kStepVariants;
 cudaError_t launch_step_dev_f32(const Lattice &L, const void *src, void *dst, cudaStream_t st,
                                 int block, int variant);
 cudaError_t launch_step_dev_f16(const Lattice &L, const void *src, void *dst, cudaStream_t st,

@@ -73,6 +73,49 @@ k_step_batch(const BatchEntry *__restrict__ ents, int n, const int *__restrict__
 
 static inline long long n_tasks(const Geom &g) { return g.tasks; }
 
+// Persistent batched variant: a grid of a few blocks per SM; warp w takes
+// the contiguous tasks [w * per_warp, (w + 1) * per_warp), finds its first
+// lattice by binary search and walks forward, keeping the current lattice's
+// entry in shared memory, so the descriptor lookup happens once per lattice
+// instead of once per task.
+template <typename T, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+k_step_batch_persist(const BatchEntry *__restrict__ ents, int n, long long ntasks, int parity,
+                     const int *__restrict__ limits, int k, long long per_warp) {
+  __shared__ BatchEntry cur[8];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long t0 = warp * per_warp;
+  const long long t1 = t0 + per_warp < ntasks ? t0 + per_warp : ntasks;
+  if (t0 >= t1) return;  // warp-uniform
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ents[mid].task0 <= t0) lo = mid; else hi = mid - 1;
+  }
+  int l = lo;
+  long long next0 = l + 1 < n ? ents[l + 1].task0 : ntasks;
+  if (lane == 0) cur[wib] = ents[l];
+  __syncwarp();
+  for (long long task = t0; task < t1; ++task) {
+    if (task >= next0) {
+      while (task >= next0) {
+        ++l;
+        next0 = l + 1 < n ? ents[l + 1].task0 : ntasks;
+      }
+      __syncwarp();
+      if (lane == 0) cur[wib] = ents[l];
+      __syncwarp();
+    }
+    if (limits != nullptr && k >= limits[l]) continue;  // warp-uniform
+    const BatchEntry &E = cur[wib];
+    const int from = parity ^ E.off;
+    step_task<T>(static_cast<const T *>(E.buf[from]), static_cast<T *>(E.buf[from ^ 1]), E.g,
+                 E.dp, task - E.task0, lane);
+  }
+}
+
 template <typename T>
 cudaError_t launch_step_dev_t(const Lattice &L, const void *src, void *dst, cudaStream_t st,
                               int block, int variant) {
@@ -97,6 +140,28 @@ cudaError_t launch_step_batch_t(const BatchEntry *ents, int n, const int *block_
   const int wpb = block / 32;
   const long long grid = (ntasks + wpb - 1) / wpb;
   if (grid < 1) return cudaSuccess;
+  if (variant >= kStepVariants) {
+    // persistent: MINB resident blocks per SM, contiguous task ranges
+    const int minb = variant - kStepVariants + 1;
+    long long pgrid = (long long)sm_count() * minb;
+    if (pgrid > grid) pgrid = grid;
+    const long long per_warp = (ntasks + pgrid * wpb - 1) / (pgrid * wpb);
+    switch (minb) {
+      case 1:
+        k_step_batch_persist<T, 1><<<(unsigned)pgrid, block, 0, st>>>(ents, n, ntasks, parity,
+                                                                     limits, k, per_warp);
+        break;
+      case 2:
+        k_step_batch_persist<T, 2><<<(unsigned)pgrid, block, 0, st>>>(ents, n, ntasks, parity,
+                                                                     limits, k, per_warp);
+        break;
+      default:
+        k_step_batch_persist<T, 3><<<(unsigned)pgrid, block, 0, st>>>(ents, n, ntasks, parity,
+                                                                     limits, k, per_warp);
+        break;
+    }
+    return cudaGetLastError();
+  }
   switch (variant) {
     case 0:
       k_step_batch<T, 1><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity,

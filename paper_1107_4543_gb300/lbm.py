@@ -60,6 +60,8 @@ _SIGS = {
     "lbm_set_source": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_double]),
     "lbm_batch_tune": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "lbm_batch_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_moments": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
     "lbm_moments_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lbm_destroy": (ctypes.c_int, [_vp]),
@@ -210,8 +212,19 @@ def lbm_tune(h):
     return t, c.value
 
 
+LBM_BATCH_TUNE_VARIANTS = 6
+
+
+def lbm_set_variant(h, variant):
+    _ck(load().lbm_set_variant(h, int(variant)), "lbm_set_variant")
+
+
+def lbm_batch_set_variant(b, variant):
+    _ck(load().lbm_batch_set_variant(b, int(variant)), "lbm_batch_set_variant")
+
+
 def lbm_batch_tune(b):
-    t = np.zeros(LBM_TUNE_VARIANTS)
+    t = np.zeros(LBM_BATCH_TUNE_VARIANTS)
     c = ctypes.c_int()
     _ck(load().lbm_batch_tune(b, _ptr(t), ctypes.byref(c)), "lbm_batch_tune")
     return t, c.value

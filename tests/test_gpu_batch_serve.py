@@ -74,6 +74,32 @@ def test_batch_member_equals_alone(L, steps):
         assert np.array_equal(got[k], want, equal_nan=True), (k, dt, spec["nx"], spec["ny"])
 
 
+@pytest.mark.parametrize("variant", range(6))
+def test_every_batch_launch_variant_equals_alone(L, variant):
+    """All launch variants (register caps; one warp per task or persistent
+    contiguous task ranges) give the standalone result bit for bit."""
+    specs = small_specs(20, seed=14)
+    dtypes = ["f32", "f16", "bf16"] * 7
+    hs = []
+    try:
+        for spec, dt in zip(specs, dtypes):
+            h = L.lbm_create(spec["nx"], spec["ny"], inp.s_ll(spec["rates"]), 1.0, (0.0, 0.0),
+                             L.DTYPES[dt])
+            L.lbm_init_field(h, *inp.batch_fields(spec))
+            hs.append(h)
+        b = L.lbm_batch_create(hs)
+        L.lbm_batch_set_variant(b, variant)
+        L.lbm_batch_step(b, 70)
+        got = [L.lbm_get_populations(h) for h in hs]
+        L.lbm_batch_destroy(b)
+    finally:
+        for h in hs:
+            L.lbm_destroy(h)
+    for k, (spec, dt) in enumerate(zip(specs, dtypes)):
+        want, _ = alone(L, spec, dt, 70)
+        assert np.array_equal(got[k], want, equal_nan=True), (variant, k, dt)
+
+
 def test_batch_results_match_oracle(L):
     specs = small_specs(6, seed=12)
     hs = []
