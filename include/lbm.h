@@ -259,6 +259,19 @@ int lbm_vn_eigs(int n, const double *kx, const double *ky, const double *U,
 typedef struct lbm_batch_ctx *lbm_batch;
 int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out);
 int lbm_batch_step(lbm_batch b, long n);
+/* Host I/O for the whole batch with one synchronization: the arrays hold
+ * one pointer per member (member order), each to a host ny x nx float64
+ * array as for lbm_init_field / lbm_moments.  All copies and kernels are
+ * enqueued back to back on the batch stream.  lbm_batch_init_fields sets
+ * f = f^eq(rho, u) for every member (t reset to 0; FP16 members re-choose
+ * their storage scale) and keeps the batch usable; LBM_EINVAL if any
+ * member's field has non-finite values or rho <= 0.  lbm_batch_moments
+ * returns every member's rho, ux, uy. */
+int lbm_batch_init_fields(lbm_batch b, const double *const *rho,
+                          const double *const *ux, const double *const *uy);
+int lbm_batch_moments(lbm_batch b, double *const *rho, double *const *ux,
+                      double *const *uy);
+
 /* As lbm_tune for the batch's launches (one variant for all its storage
  * types; the first lbm_batch_step of a batch of >= 2^20 nodes tunes unless
  * LBM_AUTOTUNE=0).  Batches have LBM_BATCH_TUNE_VARIANTS variants: the

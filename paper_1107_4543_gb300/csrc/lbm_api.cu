@@ -787,6 +787,7 @@ struct lbm_batch_ctx {
   std::vector<cudaStream_t> saved_streams;
   AuxView *views[2] = {nullptr, nullptr}; // drift views at batch parity 0 / 1
   double *dpart = nullptr, *dout = nullptr;
+  unsigned int *dflags = nullptr;         // per-member counters (2 per member)
   int parity = 0;                        // steps taken mod 2
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
@@ -930,6 +931,7 @@ static void batch_free(lbm_batch_ctx *b) {
   dev_free(b->views[1]);
   dev_free(b->dpart);
   dev_free(b->dout);
+  dev_free(b->dflags);
   for (size_t k = 0; k < b->members.size(); ++k) {
     auto *m = b->members[k];
     if (m->batch == b) m->batch = nullptr;
@@ -1050,7 +1052,8 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
     b->views[1] = (AuxView *)dev_alloc(sizeof(AuxView) * n);
     b->dpart = (double *)dev_alloc(sizeof(double) * batch_drift_partials(n));
     b->dout = (double *)dev_alloc(sizeof(double) * 4 * n);
-    if (!b->views[0] || !b->views[1] || !b->dpart || !b->dout ||
+    b->dflags = (unsigned int *)dev_alloc(sizeof(unsigned int) * 2 * n);
+    if (!b->views[0] || !b->views[1] || !b->dpart || !b->dout || !b->dflags ||
         cudaMemcpyAsync(b->views[0], v0.data(), sizeof(AuxView) * n, cudaMemcpyHostToDevice,
                         b->stream) != cudaSuccess ||
         cudaMemcpyAsync(b->views[1], v1.data(), sizeof(AuxView) * n, cudaMemcpyHostToDevice,
@@ -1124,6 +1127,127 @@ int lbm_batch_step(lbm_batch b, long n) {
   return LBM_OK;
 }
 
+
+// Refresh the device copies of the members' step parameters (after the
+// FP16 storage scale of a member changed).
+static int batch_refresh_params(lbm_batch_ctx *b) {
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    auto &gr = b->groups[gi];
+    std::vector<BatchEntry> ents((size_t)gr.n);
+    CK(cudaMemcpyAsync(ents.data(), gr.ents, sizeof(BatchEntry) * gr.n, cudaMemcpyDeviceToHost,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    for (size_t mi = 0; mi < b->members.size(); ++mi)
+      if (b->member_group[mi] == (int)gi) ents[b->member_local[mi]].dp = b->members[mi]->L.dp;
+    CK(cudaMemcpyAsync(gr.ents, ents.data(), sizeof(BatchEntry) * gr.n, cudaMemcpyHostToDevice,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+  }
+  const int n = (int)b->members.size();
+  for (int par = 0; par < 2; ++par) {
+    std::vector<AuxView> v((size_t)n);
+    for (int k = 0; k < n; ++k) {
+      auto *m = b->members[k];
+      v[k] = aux_view(m);
+      v[k].buf = m->L.buf[b->offs[k] ^ par];
+    }
+    CK(cudaMemcpyAsync(b->views[par], v.data(), sizeof(AuxView) * n, cudaMemcpyHostToDevice,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_init_fields(lbm_batch b, const double *const *rho, const double *const *ux,
+                          const double *const *uy) {
+  REQUIRE(b != nullptr && rho && ux && uy, "null argument");
+  REQUIRE(!b->spent, "batch ran a ragged generation; create a new batch");
+  DevGuard g(b->device);
+  const size_t nm = b->members.size();
+  for (size_t k = 0; k < nm; ++k) REQUIRE(rho[k] && ux[k] && uy[k], "null field pointer");
+  for (auto *m : b->members) {
+    int rc = ensure_stage(m);
+    if (rc != LBM_OK) return rc;
+  }
+  // every upload first, back to back
+  for (size_t k = 0; k < nm; ++k) {
+    auto *m = b->members[k];
+    const size_t n = (size_t)m->L.g.nx * m->L.g.ny;
+    CK(cudaMemcpyAsync(m->stage, rho[k], n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(m->stage + n, ux[k], n * sizeof(double), cudaMemcpyHostToDevice,
+                       b->stream));
+    CK(cudaMemcpyAsync(m->stage + 2 * n, uy[k], n * sizeof(double), cudaMemcpyHostToDevice,
+                       b->stream));
+  }
+  // FP16 members choose their storage scale from the new fields (device
+  // counters gathered in dflags, read back by one copy)
+  std::vector<unsigned int> bits(2 * nm, 0);
+  bool any16 = false;
+  for (size_t k = 0; k < nm; ++k) {
+    auto *m = b->members[k];
+    if (m->L.dtype != LBM_F16DEV) continue;
+    any16 = true;
+    const size_t n = (size_t)m->L.g.nx * m->L.g.ny;
+    CK(launch_maxdev_eq(aux_view(m), m->stage, m->stage + n, m->stage + 2 * n, 0, nullptr,
+                        b->dflags + k, b->stream));
+  }
+  if (any16) {
+    CK(cudaMemcpyAsync(bits.data(), b->dflags, sizeof(unsigned int) * nm, cudaMemcpyDeviceToHost,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    for (size_t k = 0; k < nm; ++k)
+      if (b->members[k]->L.dtype == LBM_F16DEV) {
+        float mx;
+        memcpy(&mx, &bits[k], sizeof(mx));
+        set_qscale(b->members[k], (double)mx);
+      }
+    int rc = batch_refresh_params(b);
+    if (rc != LBM_OK) return rc;
+  }
+  // equilibria into each member's current buffer (the batch's bookkeeping
+  // of buffers stays valid), fields validated on the device
+  std::vector<unsigned int> bad(nm, 0);
+  for (size_t k = 0; k < nm; ++k) {
+    auto *m = b->members[k];
+    const size_t n = (size_t)m->L.g.nx * m->L.g.ny;
+    CK(launch_init_eq(aux_view(m), m->stage, m->stage + n, m->stage + 2 * n, 0, nullptr,
+                      b->stream, b->dflags + nm + k));
+  }
+  CK(cudaMemcpyAsync(bad.data(), b->dflags + nm, sizeof(unsigned int) * nm,
+                     cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  for (auto *m : b->members) m->t = 0;
+  for (size_t k = 0; k < nm; ++k)
+    if (bad[k]) {
+      set_error("member " + std::to_string(k) + ": " + std::to_string(bad[k]) +
+                " nodes with non-finite fields or rho <= 0");
+      return LBM_EINVAL;
+    }
+  return LBM_OK;
+}
+
+int lbm_batch_moments(lbm_batch b, double *const *rho, double *const *ux, double *const *uy) {
+  REQUIRE(b != nullptr && rho && ux && uy, "null argument");
+  DevGuard g(b->device);
+  const size_t nm = b->members.size();
+  for (size_t k = 0; k < nm; ++k) REQUIRE(rho[k] && ux[k] && uy[k], "null output pointer");
+  for (auto *m : b->members) {
+    int rc = ensure_stage(m);
+    if (rc != LBM_OK) return rc;
+  }
+  for (size_t k = 0; k < nm; ++k) {
+    auto *m = b->members[k];
+    const size_t n = (size_t)m->L.g.nx * m->L.g.ny;
+    CK(launch_moments(aux_view(m), m->stage, m->stage + n, m->stage + 2 * n, b->stream));
+    CK(cudaMemcpyAsync(rho[k], m->stage, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(ux[k], m->stage + n, n * sizeof(double), cudaMemcpyDeviceToHost,
+                       b->stream));
+    CK(cudaMemcpyAsync(uy[k], m->stage + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost,
+                       b->stream));
+  }
+  CK(cudaStreamSynchronize(b->stream));
+  return LBM_OK;
+}
 
 int lbm_batch_set_variant(lbm_batch b, int variant) {
   REQUIRE(b != nullptr, "null batch");

@@ -81,6 +81,10 @@ _SIGS = {
                                    ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_step": (ctypes.c_int, [_vp, ctypes.c_long]),
     "lbm_batch_drift": (ctypes.c_int, [_vp, _dp]),
+    "lbm_batch_init_fields": (ctypes.c_int, [_vp, ctypes.POINTER(_dp), ctypes.POINTER(_dp),
+                                             ctypes.POINTER(_dp)]),
+    "lbm_batch_moments": (ctypes.c_int, [_vp, ctypes.POINTER(_dp), ctypes.POINTER(_dp),
+                                         ctypes.POINTER(_dp)]),
     "lbm_batch_destroy": (ctypes.c_int, [_vp]),
     "lbm_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_long, ctypes.POINTER(_vp)]),
     "lbm_submit": (ctypes.c_int, [_vp, ctypes.POINTER(lbm_request),
@@ -332,6 +336,36 @@ def lbm_batch_drift(b, n):
     if rc not in (LBM_OK, LBM_EUNSTABLE):
         raise LbmError(rc, "lbm_batch_drift")
     return out
+
+
+def _ptr_array(arrays):
+    return (_dp * len(arrays))(*[_ptr(a) for a in arrays])
+
+
+def lbm_batch_init_fields(b, fields):
+    """fields: one (rho, ux, uy) triple of C-contiguous float64 (ny, nx)
+    arrays per member, in member order."""
+    for f in fields:
+        for a in f:
+            if a.dtype != np.float64 or not a.flags.c_contiguous:
+                raise ValueError("fields must be contiguous float64 arrays")
+    _ck(load().lbm_batch_init_fields(b, _ptr_array([f[0] for f in fields]),
+                                     _ptr_array([f[1] for f in fields]),
+                                     _ptr_array([f[2] for f in fields])),
+        "lbm_batch_init_fields")
+
+
+def lbm_batch_moments(b, outs):
+    """outs: one (rho, ux, uy) triple of writable contiguous float64 (ny, nx)
+    arrays per member, filled in place."""
+    for f in outs:
+        for a in f:
+            if a.dtype != np.float64 or not a.flags.c_contiguous:
+                raise ValueError("outputs must be contiguous float64 arrays")
+    _ck(load().lbm_batch_moments(b, _ptr_array([f[0] for f in outs]),
+                                 _ptr_array([f[1] for f in outs]),
+                                 _ptr_array([f[2] for f in outs])), "lbm_batch_moments")
+    return outs
 
 
 def lbm_batch_destroy(b):
