@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--max-nodes", type=int, default=0, help="server resident-node cap")
     p.add_argument("--size", type=int, default=8192, help="side of the large lattice")
     p.add_argument("--dtypes", default="f32,f16,bf16,f64", help="storage types (large)")
+    p.add_argument("--batch-variant", type=int, default=-1,
+                   help="pin the batched launch variant (default: tuned)")
     return p.parse_args()
 
 
@@ -270,6 +272,8 @@ def bench_batched(args, L, torch, rank, ws):
     hs, fields = setup_batch(L, torch, specs, "f32", stream)
     nodes = sum(s["nx"] * s["ny"] for s in specs)
     b = L.lbm_batch_create(hs)
+    if args.batch_variant >= 0:
+        L.lbm_batch_set_variant(b, args.batch_variant)
     lbm_steps = args.lbm_steps
 
     def one_step():
@@ -279,6 +283,7 @@ def bench_batched(args, L, torch, rank, ws):
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
+    variant = L.lbm_batch_get_variant(b)
     if ws > 1:
         torch.distributed.barrier()
     clocks = Clocks(dev)
@@ -350,7 +355,8 @@ def bench_batched(args, L, torch, rank, ws):
                 # ncu DRAM bytes per lattice update of a smaller capture of the
                 # same kernel, scaled to this launch's lattice updates
                 "traffic": (round(tr["dram_bytes_per_lu"] * nodes) if tr else None),
-                "kernel": "k_step_batch<float>", "peak_source": peak_kind,
+                "kernel": "k_step_batch<float> (launch variant %d)" % variant,
+                "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": BYTES_PER_LU["f32"] * nodes,
                 "avg_launch_ms": round(launch_ms, 4)}
     line = {

@@ -281,8 +281,11 @@ int lbm_batch_moments(lbm_batch b, double *const *rho, double *const *ux,
  * not change. */
 #define LBM_BATCH_TUNE_VARIANTS 6
 int lbm_batch_tune(lbm_batch b, double *times_ms, int *chosen);
-/* As lbm_set_variant for a batch (0 .. LBM_BATCH_TUNE_VARIANTS-1). */
+/* As lbm_set_variant for a batch (0 .. LBM_BATCH_TUNE_VARIANTS-1); get
+ * reports the variant in use (-1 before the first step of an untuned
+ * batch). */
 int lbm_batch_set_variant(lbm_batch b, int variant);
+int lbm_batch_get_variant(lbm_batch b, int *variant);
 /* The sums of lbm_drift for every member at once (out: 4 doubles per member,
  * in member order): one reduction launch pair for the whole batch,
  * reproducible per member.  Synchronizes the batch stream; returns

@@ -1249,6 +1249,12 @@ int lbm_batch_moments(lbm_batch b, double *const *rho, double *const *ux, double
   return LBM_OK;
 }
 
+int lbm_batch_get_variant(lbm_batch b, int *variant) {
+  REQUIRE(b != nullptr && variant != nullptr, "null argument");
+  *variant = b->tuned ? b->variant : -1;
+  return LBM_OK;
+}
+
 int lbm_batch_set_variant(lbm_batch b, int variant) {
   REQUIRE(b != nullptr, "null batch");
   REQUIRE(variant >= 0 && variant < kBatchVariants, "no such launch variant");

@@ -62,6 +62,7 @@ _SIGS = {
     "lbm_batch_tune": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_int)]),
     "lbm_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_batch_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "lbm_batch_get_variant": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "lbm_moments": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
     "lbm_moments_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lbm_destroy": (ctypes.c_int, [_vp]),
@@ -225,6 +226,12 @@ def lbm_set_variant(h, variant):
 
 def lbm_batch_set_variant(b, variant):
     _ck(load().lbm_batch_set_variant(b, int(variant)), "lbm_batch_set_variant")
+
+
+def lbm_batch_get_variant(b):
+    v = ctypes.c_int()
+    _ck(load().lbm_batch_get_variant(b, ctypes.byref(v)), "lbm_batch_get_variant")
+    return v.value
 
 
 def lbm_batch_tune(b):
