@@ -383,3 +383,35 @@ def test_analytic_init_matches_host_fields(L):
         L.lbm_destroy(h)
     want = inp.gaussian_pulse(nx, ny, *params)[0]
     assert np.max(np.abs(rho - want)) < 1e-15 * 4
+
+
+def test_torch_caching_allocator_through_lbm_set_allocator(L):
+    """The library's device memory can come from torch's caching allocator
+    (lbm_set_allocator with ctypes callbacks); results are unchanged."""
+    import ctypes
+
+    import torch
+
+    calls = {"alloc": 0, "free": 0}
+
+    @ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+    def alloc(nbytes, ctx):
+        calls["alloc"] += 1
+        return torch.cuda.caching_allocator_alloc(int(nbytes))
+
+    @ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+    def free(ptr, ctx):
+        calls["free"] += 1
+        torch.cuda.caching_allocator_delete(ptr)
+
+    nx, ny = 70, 50
+    r = inp.rates("OPT")
+    fields = inp.gaussian_pulse(nx, ny, 1e-3, 4.0)
+    (want, _, _), _ = run_gpu(L, nx, ny, r, 40, L.LBM_F32DEV, fields=fields)
+    L.lbm_set_allocator(alloc, free)
+    try:
+        (got, _, _), _ = run_gpu(L, nx, ny, r, 40, L.LBM_F32DEV, fields=fields)
+    finally:
+        L.lbm_set_allocator(None, None)
+    assert calls["alloc"] > 0 and calls["free"] == calls["alloc"]
+    assert np.array_equal(got, want)
