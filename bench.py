@@ -2,7 +2,7 @@
 """Throughput benchmark of the D2Q9 MRT lattice Boltzmann library on GB300.
 
 Default workload (one JSON line): 512 independent periodic lattices, areas
-log-uniform in [32^2, 1024^2] (7.7e7 nodes), per-lattice relaxation rates,
+log-uniform in [32^2, 1024^2] (6.7e7 nodes), per-lattice relaxation rates,
 Gaussian pulses, FP32 deviation storage.  One benchmark step = the whole
 batch advanced 500 time steps (500 batched fused step launches replayed from
 CUDA graphs) followed by the FP64 drift check of every lattice (one batched
@@ -10,8 +10,8 @@ reduction).
 
   value      MLUPS with the populations resident in HBM
   e2e        MLUPS through the C ABI with host buffers: every step uploads
-             the initial fields (rho, ux, uy) from pinned host memory,
-             steps, and downloads rho, ux, uy
+             the initial fields (rho, ux, uy) from pinned host memory
+             (packed batch I/O), steps, and downloads rho, ux, uy
   roofline   the batched step kernel: algorithmic 72 B per lattice update
              over its average launch time against the measured HBM copy
              bandwidth
@@ -309,21 +309,22 @@ def bench_batched(args, L, torch, rank, ws):
     launch_ms = float(np.mean(step_ms)) / lbm_steps  # one batched kernel per time step
     launches = args.steps * (lbm_steps + 2)  # batched steps + one drift launch pair
 
-    # e2e: host fields in, moments out, through the public API (the
-    # batch-level calls enqueue every member's copies with one sync each)
-    outs = []
-    for spec in specs:
-        o = []
-        for _ in range(3):
-            t = torch.empty((spec["ny"], spec["nx"]), dtype=torch.float64, pin_memory=True)
-            o.append(t.numpy())
-        outs.append(o)
+    # e2e: host fields in, moments out, through the public API: the packed
+    # batch I/O calls (page-locked host arrays of all members' fields, moved
+    # in a few large copies overlapped with the init / moments kernels)
+    def pinned_flat():
+        return torch.empty(nodes, dtype=torch.float64, pin_memory=True).numpy()
+
+    fin = [pinned_flat() for _ in range(3)]
+    for c in range(3):
+        np.concatenate([f[c].ravel() for f in fields], out=fin[c])
+    fout = tuple(pinned_flat() for _ in range(3))
 
     def e2e_step():
-        L.lbm_batch_init_fields(b, fields)
+        L.lbm_batch_init_packed(b, *fin)
         L.lbm_batch_step(b, lbm_steps)
         L.lbm_batch_drift(b, len(hs))
-        L.lbm_batch_moments(b, outs)
+        L.lbm_batch_moments_packed(b, fout)
 
     e2e_step()
     torch.cuda.synchronize()

@@ -261,16 +261,33 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out);
 int lbm_batch_step(lbm_batch b, long n);
 /* Host I/O for the whole batch with one synchronization: the arrays hold
  * one pointer per member (member order), each to a host ny x nx float64
- * array as for lbm_init_field / lbm_moments.  All copies and kernels are
- * enqueued back to back on the batch stream.  lbm_batch_init_fields sets
- * f = f^eq(rho, u) for every member (t reset to 0; FP16 members re-choose
- * their storage scale) and keeps the batch usable; LBM_EINVAL if any
- * member's field has non-finite values or rho <= 0.  lbm_batch_moments
- * returns every member's rho, ux, uy. */
+ * array as for lbm_init_field / lbm_moments.  The copies run on a copy
+ * stream of the batch, overlapped with the batch stream's kernels of the
+ * neighbouring members; the call returns when all of them are done and the
+ * host arrays may be reused.  lbm_batch_init_fields sets f = f^eq(rho, u)
+ * for every member (t reset to 0; FP16 members re-choose their storage
+ * scale) and keeps the batch usable; LBM_EINVAL if any member's field has
+ * non-finite values or rho <= 0.  lbm_batch_moments returns every member's
+ * rho, ux, uy.  Page-locked host memory gives the full link rate. */
 int lbm_batch_init_fields(lbm_batch b, const double *const *rho,
                           const double *const *ux, const double *const *uy);
 int lbm_batch_moments(lbm_batch b, double *const *rho, double *const *ux,
                       double *const *uy);
+/* members: number of members; nodes: their total node count, sum of nx*ny
+ * (either pointer may be NULL). */
+int lbm_batch_size(lbm_batch b, int *members, long long *nodes);
+/* The same host I/O with packed arrays: rho, ux, uy each hold `nodes`
+ * float64 values (lbm_batch_size), member k's ny x nx row-major field
+ * starting at the sum of nx*ny of members 0..k-1.  The copies go in groups
+ * of consecutive members of about 2^23 nodes, so a batch of many small
+ * lattices still moves its fields in few large copies (many small host
+ * copies run well below the link rate on some hosts).  The first call
+ * allocates a device staging buffer of 3 x nodes doubles, kept until
+ * lbm_batch_destroy.  Results equal those of the per-member calls bit for
+ * bit. */
+int lbm_batch_init_packed(lbm_batch b, const double *rho, const double *ux,
+                          const double *uy);
+int lbm_batch_moments_packed(lbm_batch b, double *rho, double *ux, double *uy);
 
 /* As lbm_tune for the batch's launches (one variant for all its storage
  * types; the first lbm_batch_step of a batch of >= 2^20 nodes tunes unless

@@ -24,6 +24,7 @@ UNITS = {
     "step_bf16.cu": [],
     "step_f64.cu": ["-fmad=false"],
     "aux.cu": ["-fmad=false"],
+    "io_dev.cu": [],
     "serve.cu": [],
     "drift_noalloc.cu": [],
     "vn.cu": [],

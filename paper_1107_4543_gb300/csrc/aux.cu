@@ -244,6 +244,66 @@ constexpr int DRIFT_BLOCKS = 1024;
 constexpr int DRIFT_THREADS = 256;
 int drift_blocks() { return DRIFT_BLOCKS; }
 
+// s + e = a + b exactly (Knuth's TwoSum; this file is built without FMA
+// contraction, which the identity needs)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// float-float accumulator: hi + lo carries about 48 significant bits
+struct FF {
+  float hi, lo;
+  __device__ __forceinline__ void add(float a) {
+    float t;
+    two_sum(hi, a, hi, t);
+    lo += t;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Mass and momentum deviations of one node's 9 stored populations (the
+// node's own slots, which is all a lattice-wide sum needs), non-finite
+// values counted in bad and taken as zero.  FP64 storage sums in FP64; the
+// deviation types sum their FP32 values as float-float (GB300 runs FP32 at
+// many times its FP64 rate, and the 9-term sums keep ~48 bits).
+__device__ __forceinline__ void node_sums(const AuxView &a, long long off, double &r, double &jx,
+                                          double &jy, double &bad) {
+  if (a.dtype == LBM_F64) {
+    double f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      f[i] = static_cast<const double *>(a.buf)[(long long)i * a.g.plane + off];
+      if (!isfinite(f[i])) { bad += 1.0; f[i] = 0.0; }
+    }
+    r = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8] - a.rho0;
+    jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8] - a.jx0;
+    jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8] - a.jy0;
+    return;
+  }
+  float f[9];
+  const float inv = (float)(1.0 / a.scale);  // a power of two
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const long long idx = (long long)i * a.g.plane + off;
+    float v;
+    if (a.dtype == LBM_F32DEV) v = static_cast<const float *>(a.buf)[idx];
+    else if (a.dtype == LBM_F16DEV) v = __half2float(static_cast<const __half *>(a.buf)[idx]) * inv;
+    else v = __bfloat162float(static_cast<const __nv_bfloat16 *>(a.buf)[idx]);
+    if (!isfinite(v)) { bad += 1.0; v = 0.0f; }
+    f[i] = v;
+  }
+  FF s0{f[0], 0.0f}, s1{f[1], 0.0f}, s2{f[2], 0.0f};
+#pragma unroll
+  for (int i = 1; i < 9; ++i) s0.add(f[i]);
+  s1.add(-f[3]); s1.add(f[5]); s1.add(-f[6]); s1.add(-f[7]); s1.add(f[8]);
+  s2.add(-f[4]); s2.add(f[5]); s2.add(f[6]); s2.add(-f[7]); s2.add(-f[8]);
+  r = s0.value();
+  jx = s1.value();
+  jy = s2.value();
+}
+
 __global__ void __launch_bounds__(DRIFT_THREADS) k_drift1(AuxView a, double *partials) {
   __shared__ double sh[4][DRIFT_THREADS];
   const long long N = (long long)a.g.nx * a.g.ny;
@@ -251,17 +311,8 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift1(AuxView a, double *par
   for (long long n = blockIdx.x * (long long)DRIFT_THREADS + threadIdx.x; n < N;
        n += (long long)DRIFT_BLOCKS * DRIFT_THREADS) {
     const int x = (int)(n % a.g.nx), y = (int)(n / a.g.nx);
-    const long long off = (long long)y * a.g.pitch + x;
-    double f[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      f[i] = load_stored(a, (long long)i * a.g.plane + off);
-      if (!isfinite(f[i])) { bad += 1.0; f[i] = 0.0; }
-    }
-    double r = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
-    double jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
-    double jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
-    if (a.dtype == LBM_F64) { r -= a.rho0; jx -= a.jx0; jy -= a.jy0; }
+    double r, jx, jy;
+    node_sums(a, (long long)y * a.g.pitch + x, r, jx, jy, bad);
     s0 += r; s1 += jx; s2 += jy;
   }
   sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = s1;
@@ -303,16 +354,9 @@ k_batch_drift1(const AuxView *__restrict__ views, double *partials) {
   for (long long n = blockIdx.x * (long long)DRIFT_THREADS + threadIdx.x; n < N;
        n += (long long)BD_BLOCKS * DRIFT_THREADS) {
     const int x = (int)(n % a.g.nx), y = (int)(n / a.g.nx);
-    const long long off = (long long)y * a.g.pitch + x;
-    double f[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      f[i] = load_stored(a, (long long)i * a.g.plane + off);
-      if (!isfinite(f[i])) { bad += 1.0; f[i] = 0.0; }
-    }
-    s0 += f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
-    s1 += f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
-    s2 += f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+    double r, jx, jy;
+    node_sums(a, (long long)y * a.g.pitch + x, r, jx, jy, bad);
+    s0 += r; s1 += jx; s2 += jy;
   }
   sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = s1;
   sh[2][threadIdx.x] = s2; sh[3][threadIdx.x] = bad;
@@ -364,6 +408,7 @@ static AnalyticParams make_ap(const double *p) {
 cudaError_t launch_init_eq(const AuxView &a, const double *rho, const double *ux,
                            const double *uy, int kind, const double *params, cudaStream_t st,
                            unsigned int *bad) {
+  if (kind == 0 && a.dtype != LBM_F64) return launch_init_dev(a, rho, ux, uy, st, bad);
   const long long N = (long long)a.g.nx * a.g.ny;
   if (bad) {
     cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), st);
@@ -376,6 +421,7 @@ cudaError_t launch_init_eq(const AuxView &a, const double *rho, const double *ux
 cudaError_t launch_maxdev_eq(const AuxView &a, const double *rho, const double *ux,
                              const double *uy, int kind, const double *params,
                              unsigned int *max_bits, cudaStream_t st) {
+  if (kind == 0 && a.dtype != LBM_F64) return launch_maxdev_dev(a, rho, ux, uy, max_bits, st);
   const long long N = (long long)a.g.nx * a.g.ny;
   cudaError_t e = cudaMemsetAsync(max_bits, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
@@ -385,6 +431,7 @@ cudaError_t launch_maxdev_eq(const AuxView &a, const double *rho, const double *
 
 cudaError_t launch_moments(const AuxView &a, double *rho, double *ux, double *uy,
                            cudaStream_t st) {
+  if (a.dtype != LBM_F64) return launch_moments_dev(a, rho, ux, uy, st);
   const long long N = (long long)a.g.nx * a.g.ny;
   k_moments<<<grid_for(N), 256, 0, st>>>(a, rho, ux, uy);
   return cudaGetLastError();

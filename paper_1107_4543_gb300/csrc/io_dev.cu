@@ -1,0 +1,219 @@
+// Field I/O kernels of the deviation storage types (FP32, FP16, BF16):
+// equilibrium initialisation from device fields, the largest deviation that
+// sets the FP16 storage scale, and the moments.  The FP64 storage type keeps
+// the canonical kernels of aux.cu (bit parity with a plain FP64 version).
+//
+// The equilibrium of section 2.3, f^eq = M^-1 m^eq, equals the second-order
+// polynomial  w_i [rho + 3 c_i.j + 9/2 (c_i.j)^2 / rho - 3/2 |j|^2 / rho]
+// with weights 4/9, 1/9 (axis) and 1/36 (diagonal).  What is stored is the
+// deviation f^eq(rho, j) - f^eq(rho0, j0), formed here from the differences
+// rho - rho0, j - j0, jx^2/rho - jx0^2/rho0, jy^2/rho - jy0^2/rho0 and
+// jx jy/rho - jx0 jy0/rho0: every term is of the size of the perturbation,
+// so nothing of order one is subtracted after rounding, and a node costs
+// one FP64 division and a few dozen FP64 operations (GB300's FP64 rate is
+// what bounds these kernels, not their 60 bytes per node).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+// reference state and its quadratic terms (host-computed)
+struct RefState {
+  double rho0, jx0, jy0;
+  double axx0, ayy0, axy0;  // jx0^2/rho0, jy0^2/rho0, jx0 jy0/rho0
+};
+
+RefState make_ref(const AuxView &a) {
+  RefState r;
+  r.rho0 = a.rho0;
+  r.jx0 = a.jx0;
+  r.jy0 = a.jy0;
+  r.axx0 = a.jx0 * a.jx0 / a.rho0;
+  r.ayy0 = a.jy0 * a.jy0 / a.rho0;
+  r.axy0 = a.jx0 * a.jy0 / a.rho0;
+  return r;
+}
+
+__device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// f^eq_i(rho, rho u) - f^eq_i(rho0, j0), i = 0..8
+__device__ __forceinline__ void feq_deviation(const RefState &R, double r, double u, double v,
+                                              double d[9]) {
+  const double jx = r * u, jy = r * v;
+  const double inv = 1.0 / r;
+  const double dr = r - R.rho0;
+  const double ex = 3.0 * (jx - R.jx0), ey = 3.0 * (jy - R.jy0);
+  const double A = jx * jx * inv - R.axx0;
+  const double B = jy * jy * inv - R.ayy0;
+  const double C = jx * jy * inv - R.axy0;
+  const double t1 = dr + 3.0 * A - 1.5 * B;  // axis x: 9/2 A - 3/2 (A + B)
+  const double t2 = dr + 3.0 * B - 1.5 * A;  // axis y
+  const double t5 = dr + 3.0 * (A + B);      // diagonals: 9/2 (A + B +- 2C) - 3/2 (A + B)
+  const double p = t5 + 9.0 * C, q = t5 - 9.0 * C;
+  constexpr double w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w5 = 1.0 / 36.0;
+  d[0] = w0 * (dr - 1.5 * (A + B));
+  d[1] = w1 * (t1 + ex);
+  d[2] = w1 * (t2 + ey);
+  d[3] = w1 * (t1 - ex);
+  d[4] = w1 * (t2 - ey);
+  d[5] = w5 * (p + ex + ey);
+  d[6] = w5 * (q - ex + ey);
+  d[7] = w5 * (p - ex - ey);
+  d[8] = w5 * (q + ex - ey);
+}
+
+template <typename T>
+__device__ __forceinline__ T encode(double d, double scale);
+template <>
+__device__ __forceinline__ float encode<float>(double d, double) {
+  return (float)d;
+}
+template <>
+__device__ __forceinline__ __half encode<__half>(double d, double scale) {
+  return __float2half_rn((float)(d * scale));
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 encode<__nv_bfloat16>(double d, double) {
+  return __float2bfloat16_rn((float)d);
+}
+
+template <typename T>
+__device__ __forceinline__ double decode(T s, double inv_scale);
+template <>
+__device__ __forceinline__ double decode<float>(float s, double) {
+  return (double)s;
+}
+template <>
+__device__ __forceinline__ double decode<__half>(__half s, double inv_scale) {
+  return (double)__half2float(s) * inv_scale;  // the scale is a power of two
+}
+template <>
+__device__ __forceinline__ double decode<__nv_bfloat16>(__nv_bfloat16 s, double) {
+  return (double)__bfloat162float(s);
+}
+
+// Population i of node x goes to slot x - c_i, where the next step's pull
+// (f_i(x) = P_i(x - c_i)) reads it.  bad counts nodes whose field is not
+// finite or has rho <= 0.
+template <typename T>
+__global__ void __launch_bounds__(256) k_init_dev(AuxView a, RefState R, const double *rho,
+                                                  const double *ux, const double *uy,
+                                                  unsigned int *bad) {
+  const int nx = a.g.nx, ny = a.g.ny;
+  const long long N = (long long)nx * ny;
+  T *buf = static_cast<T *>(a.buf);
+  unsigned int nbad = 0;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(n / nx), x = (int)(n - (long long)y * nx);
+    const double r = rho[n], u = ux[n], v = uy[n];
+    if (!(r > 0.0) || !isfinite(r) || !isfinite(u) || !isfinite(v)) ++nbad;
+    double d[9];
+    feq_deviation(R, r, u, v, d);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int xs = wrap(x - CXd(i), nx), ys = wrap(y - CYd(i), ny);
+      buf[(long long)i * a.g.plane + (long long)ys * a.g.pitch + xs] = encode<T>(d[i], a.scale);
+    }
+  }
+  if (bad && nbad) atomicAdd(bad, nbad);
+}
+
+__global__ void __launch_bounds__(256) k_maxdev_dev(AuxView a, RefState R, const double *rho,
+                                                    const double *ux, const double *uy,
+                                                    unsigned int *max_bits) {
+  const long long N = (long long)a.g.nx * a.g.ny;
+  float m = 0.0f;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    double d[9];
+    feq_deviation(R, rho[n], ux[n], uy[n], d);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) m = fmaxf(m, (float)fabs(d[i]));
+  }
+  atomicMax(max_bits, __float_as_uint(m));
+}
+
+// rho = rho0 + sum f', j = j0 + sum c f' of the pre-collision populations
+// f_i(x) = P_i(x - c_i); u = j / rho
+template <typename T>
+__global__ void __launch_bounds__(256) k_moments_dev(AuxView a, double *rho, double *ux,
+                                                     double *uy) {
+  const int nx = a.g.nx, ny = a.g.ny;
+  const long long N = (long long)nx * ny;
+  const T *buf = static_cast<const T *>(a.buf);
+  const double inv_scale = 1.0 / a.scale;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(n / nx), x = (int)(n - (long long)y * nx);
+    double f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int xs = wrap(x - CXd(i), nx), ys = wrap(y - CYd(i), ny);
+      f[i] = decode<T>(buf[(long long)i * a.g.plane + (long long)ys * a.g.pitch + xs], inv_scale);
+    }
+    const double r = a.rho0 + (f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8]);
+    const double jx = a.jx0 + (f[1] - f[3] + f[5] - f[6] - f[7] + f[8]);
+    const double jy = a.jy0 + (f[2] - f[4] + f[5] + f[6] - f[7] - f[8]);
+    const double inv = 1.0 / r;
+    rho[n] = r;
+    ux[n] = jx * inv;
+    uy[n] = jy * inv;
+  }
+}
+
+unsigned grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  long long cap = (long long)sm_count() * 16;
+  return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+}  // namespace
+
+cudaError_t launch_init_dev(const AuxView &a, const double *rho, const double *ux,
+                            const double *uy, cudaStream_t st, unsigned int *bad) {
+  const long long N = (long long)a.g.nx * a.g.ny;
+  if (bad) {
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+  }
+  const RefState R = make_ref(a);
+  const unsigned grid = grid_for(N);
+  switch (a.dtype) {
+    case LBM_F32DEV: k_init_dev<float><<<grid, 256, 0, st>>>(a, R, rho, ux, uy, bad); break;
+    case LBM_F16DEV: k_init_dev<__half><<<grid, 256, 0, st>>>(a, R, rho, ux, uy, bad); break;
+    case LBM_BF16DEV:
+      k_init_dev<__nv_bfloat16><<<grid, 256, 0, st>>>(a, R, rho, ux, uy, bad);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maxdev_dev(const AuxView &a, const double *rho, const double *ux,
+                              const double *uy, unsigned int *max_bits, cudaStream_t st) {
+  const long long N = (long long)a.g.nx * a.g.ny;
+  cudaError_t e = cudaMemsetAsync(max_bits, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  k_maxdev_dev<<<grid_for(N), 256, 0, st>>>(a, make_ref(a), rho, ux, uy, max_bits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments_dev(const AuxView &a, double *rho, double *ux, double *uy,
+                               cudaStream_t st) {
+  const long long N = (long long)a.g.nx * a.g.ny;
+  const unsigned grid = grid_for(N);
+  switch (a.dtype) {
+    case LBM_F32DEV: k_moments_dev<float><<<grid, 256, 0, st>>>(a, rho, ux, uy); break;
+    case LBM_F16DEV: k_moments_dev<__half><<<grid, 256, 0, st>>>(a, rho, ux, uy); break;
+    case LBM_BF16DEV: k_moments_dev<__nv_bfloat16><<<grid, 256, 0, st>>>(a, rho, ux, uy); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

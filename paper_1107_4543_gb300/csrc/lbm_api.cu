@@ -795,7 +795,28 @@ struct lbm_batch_ctx {
   int variant = 2;                       // launch variant (tuner)
   bool tuned = false;
   long long nodes = 0;
+  // host<->device copies of the batch-level field I/O run on their own
+  // stream, member by member, so that they overlap the kernels of the
+  // members before (init) or after (moments) them
+  cudaStream_t io = nullptr;
+  cudaEvent_t io_ev = nullptr;
+  // packed host I/O: member k's fields start at poff[k] of a packed array;
+  // pstage holds rho, ux, uy of all members (3 x nodes doubles, lazily)
+  std::vector<size_t> poff;
+  double *pstage = nullptr;
 };
+
+static int ensure_io(lbm_batch_ctx *b) {
+  if (b->io) return LBM_OK;
+  CK(cudaStreamCreateWithFlags(&b->io, cudaStreamNonBlocking));
+  cudaError_t e = cudaEventCreateWithFlags(&b->io_ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(b->io);
+    b->io = nullptr;
+    CK(e);
+  }
+  return LBM_OK;
+}
 
 static cudaError_t batch_launch_all(lbm_batch_ctx *b, int parity, cudaStream_t st,
                                     int variant) {
@@ -922,6 +943,12 @@ long long batch_nodes(const lbm_batch_ctx *b) { return b->nodes; }
 
 static void batch_free(lbm_batch_ctx *b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->io) {
+    cudaStreamSynchronize(b->io);
+    cudaStreamDestroy(b->io);
+    cudaEventDestroy(b->io_ev);
+  }
+  dev_free(b->pstage);
   for (auto &gr : b->groups) {
     dev_free(gr.ents);
     dev_free(gr.block_first);
@@ -939,6 +966,163 @@ static void batch_free(lbm_batch_ctx *b) {
   }
   cudaGetLastError();
   delete b;
+}
+
+// Refresh the device copies of the members' step parameters (after the
+// FP16 storage scale of a member changed).
+static int batch_refresh_params(lbm_batch_ctx *b) {
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    auto &gr = b->groups[gi];
+    std::vector<BatchEntry> ents((size_t)gr.n);
+    CK(cudaMemcpyAsync(ents.data(), gr.ents, sizeof(BatchEntry) * gr.n, cudaMemcpyDeviceToHost,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    for (size_t mi = 0; mi < b->members.size(); ++mi)
+      if (b->member_group[mi] == (int)gi) ents[b->member_local[mi]].dp = b->members[mi]->L.dp;
+    CK(cudaMemcpyAsync(gr.ents, ents.data(), sizeof(BatchEntry) * gr.n, cudaMemcpyHostToDevice,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+  }
+  const int n = (int)b->members.size();
+  for (int par = 0; par < 2; ++par) {
+    std::vector<AuxView> v((size_t)n);
+    for (int k = 0; k < n; ++k) {
+      auto *m = b->members[k];
+      v[k] = aux_view(m);
+      v[k].buf = m->L.buf[b->offs[k] ^ par];
+    }
+    CK(cudaMemcpyAsync(b->views[par], v.data(), sizeof(AuxView) * n, cudaMemcpyHostToDevice,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+  }
+  return LBM_OK;
+}
+
+// ------------------------------------------------- batch-level host I/O
+// Members are visited in copy groups: group g covers members
+// [ends[g-1], ends[g]).  A group's copies run on the copy stream while the
+// batch stream works on the previous group's members (init) or the copy
+// stream downloads a group while the batch stream computes the next one
+// (moments).  The staging buffers belong to these synchronous calls alone,
+// so uploads need not wait for work already queued on the batch stream.
+
+// init: upload(g) enqueues group g's copies; fields(k, r, u, v) gives member
+// k's staged fields.  FP16 members first take their storage scale from the
+// new fields (device counters in dflags, one read-back); the others are
+// initialised as their group lands.
+template <class Upload, class Fields>
+static int batch_init_common(lbm_batch_ctx *b, const std::vector<size_t> &ends, Upload upload,
+                             Fields fields) {
+  int rc = ensure_io(b);
+  if (rc != LBM_OK) return rc;
+  const size_t nm = b->members.size();
+  bool any16 = false;
+  size_t k = 0;
+  for (size_t gi = 0; gi < ends.size(); ++gi) {
+    CK(upload(gi));
+    CK(cudaEventRecord(b->io_ev, b->io));
+    CK(cudaStreamWaitEvent(b->stream, b->io_ev, 0));
+    for (; k < ends[gi]; ++k) {
+      auto *m = b->members[k];
+      const double *r, *u, *v;
+      fields(k, r, u, v);
+      if (m->L.dtype == LBM_F16DEV) {
+        any16 = true;
+        CK(launch_maxdev_eq(aux_view(m), r, u, v, 0, nullptr, b->dflags + k, b->stream));
+      } else {
+        CK(launch_init_eq(aux_view(m), r, u, v, 0, nullptr, b->stream, b->dflags + nm + k));
+      }
+    }
+  }
+  if (any16) {
+    std::vector<unsigned int> bits(nm, 0);
+    CK(cudaMemcpyAsync(bits.data(), b->dflags, sizeof(unsigned int) * nm, cudaMemcpyDeviceToHost,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    for (size_t j = 0; j < nm; ++j)
+      if (b->members[j]->L.dtype == LBM_F16DEV) {
+        float mx;
+        memcpy(&mx, &bits[j], sizeof(mx));
+        set_qscale(b->members[j], (double)mx);
+      }
+    rc = batch_refresh_params(b);
+    if (rc != LBM_OK) return rc;
+    for (size_t j = 0; j < nm; ++j) {
+      auto *m = b->members[j];
+      if (m->L.dtype != LBM_F16DEV) continue;
+      const double *r, *u, *v;
+      fields(j, r, u, v);
+      CK(launch_init_eq(aux_view(m), r, u, v, 0, nullptr, b->stream, b->dflags + nm + j));
+    }
+  }
+  // equilibria are in each member's current buffer (the batch's bookkeeping
+  // of buffers stays valid); the fields were validated on the device
+  std::vector<unsigned int> bad(nm, 0);
+  CK(cudaMemcpyAsync(bad.data(), b->dflags + nm, sizeof(unsigned int) * nm,
+                     cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  for (auto *m : b->members) m->t = 0;
+  for (size_t j = 0; j < nm; ++j)
+    if (bad[j]) {
+      set_error("member " + std::to_string(j) + ": " + std::to_string(bad[j]) +
+                " nodes with non-finite fields or rho <= 0");
+      return LBM_EINVAL;
+    }
+  return LBM_OK;
+}
+
+// moments: fields(k, r, u, v) gives member k's staging; download(g)
+// enqueues group g's copies to the host
+template <class Download, class Fields>
+static int batch_moments_common(lbm_batch_ctx *b, const std::vector<size_t> &ends,
+                                Download download, Fields fields) {
+  int rc = ensure_io(b);
+  if (rc != LBM_OK) return rc;
+  size_t k = 0;
+  for (size_t gi = 0; gi < ends.size(); ++gi) {
+    for (; k < ends[gi]; ++k) {
+      double *r, *u, *v;
+      fields(k, r, u, v);
+      CK(launch_moments(aux_view(b->members[k]), r, u, v, b->stream));
+    }
+    CK(cudaEventRecord(b->io_ev, b->stream));
+    CK(cudaStreamWaitEvent(b->io, b->io_ev, 0));
+    CK(download(gi));
+  }
+  CK(cudaStreamSynchronize(b->io));
+  return LBM_OK;
+}
+
+// packed layout: member offsets and the batch-wide staging buffer
+static int ensure_packed(lbm_batch_ctx *b) {
+  if (b->pstage) return LBM_OK;
+  const size_t nm = b->members.size();
+  b->poff.assign(nm + 1, 0);
+  for (size_t k = 0; k < nm; ++k)
+    b->poff[k + 1] = b->poff[k] + (size_t)b->members[k]->L.g.nx * b->members[k]->L.g.ny;
+  b->pstage = (double *)dev_alloc(3 * b->poff[nm] * sizeof(double));
+  if (!b->pstage) {
+    set_error("out of device memory for the packed staging buffer");
+    return LBM_ENOMEM;
+  }
+  return LBM_OK;
+}
+
+// copy groups of the packed arrays: consecutive members up to about 2^23
+// nodes (64 MiB per field) per group, so that every copy is large (many
+// small host copies run far below the link rate on some hosts) while the
+// copies still overlap the kernels of the neighbouring group
+static std::vector<size_t> packed_groups(const lbm_batch_ctx *b) {
+  const size_t kGroupNodes = (size_t)1 << 23;
+  const size_t nm = b->members.size();
+  std::vector<size_t> ends;
+  size_t start = 0;
+  for (size_t k = 0; k < nm; ++k)
+    if (b->poff[k + 1] - b->poff[start] >= kGroupNodes || k + 1 == nm) {
+      ends.push_back(k + 1);
+      start = k + 1;
+    }
+  return ends;
 }
 
 extern "C" {
@@ -1128,35 +1312,6 @@ int lbm_batch_step(lbm_batch b, long n) {
 }
 
 
-// Refresh the device copies of the members' step parameters (after the
-// FP16 storage scale of a member changed).
-static int batch_refresh_params(lbm_batch_ctx *b) {
-  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
-    auto &gr = b->groups[gi];
-    std::vector<BatchEntry> ents((size_t)gr.n);
-    CK(cudaMemcpyAsync(ents.data(), gr.ents, sizeof(BatchEntry) * gr.n, cudaMemcpyDeviceToHost,
-                       b->stream));
-    CK(cudaStreamSynchronize(b->stream));
-    for (size_t mi = 0; mi < b->members.size(); ++mi)
-      if (b->member_group[mi] == (int)gi) ents[b->member_local[mi]].dp = b->members[mi]->L.dp;
-    CK(cudaMemcpyAsync(gr.ents, ents.data(), sizeof(BatchEntry) * gr.n, cudaMemcpyHostToDevice,
-                       b->stream));
-    CK(cudaStreamSynchronize(b->stream));
-  }
-  const int n = (int)b->members.size();
-  for (int par = 0; par < 2; ++par) {
-    std::vector<AuxView> v((size_t)n);
-    for (int k = 0; k < n; ++k) {
-      auto *m = b->members[k];
-      v[k] = aux_view(m);
-      v[k].buf = m->L.buf[b->offs[k] ^ par];
-    }
-    CK(cudaMemcpyAsync(b->views[par], v.data(), sizeof(AuxView) * n, cudaMemcpyHostToDevice,
-                       b->stream));
-    CK(cudaStreamSynchronize(b->stream));
-  }
-  return LBM_OK;
-}
 
 int lbm_batch_init_fields(lbm_batch b, const double *const *rho, const double *const *ux,
                           const double *const *uy) {
@@ -1169,61 +1324,27 @@ int lbm_batch_init_fields(lbm_batch b, const double *const *rho, const double *c
     int rc = ensure_stage(m);
     if (rc != LBM_OK) return rc;
   }
-  // every upload first, back to back
-  for (size_t k = 0; k < nm; ++k) {
+  std::vector<size_t> ends(nm);
+  for (size_t k = 0; k < nm; ++k) ends[k] = k + 1;  // one copy group per member
+  auto fields = [&](size_t k, const double *&r, const double *&u, const double *&v) {
+    const size_t n = (size_t)b->members[k]->L.g.nx * b->members[k]->L.g.ny;
+    r = b->members[k]->stage;
+    u = r + n;
+    v = r + 2 * n;
+  };
+  auto upload = [&](size_t k) -> cudaError_t {
     auto *m = b->members[k];
     const size_t n = (size_t)m->L.g.nx * m->L.g.ny;
-    CK(cudaMemcpyAsync(m->stage, rho[k], n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
-    CK(cudaMemcpyAsync(m->stage + n, ux[k], n * sizeof(double), cudaMemcpyHostToDevice,
-                       b->stream));
-    CK(cudaMemcpyAsync(m->stage + 2 * n, uy[k], n * sizeof(double), cudaMemcpyHostToDevice,
-                       b->stream));
-  }
-  // FP16 members choose their storage scale from the new fields (device
-  // counters gathered in dflags, read back by one copy)
-  std::vector<unsigned int> bits(2 * nm, 0);
-  bool any16 = false;
-  for (size_t k = 0; k < nm; ++k) {
-    auto *m = b->members[k];
-    if (m->L.dtype != LBM_F16DEV) continue;
-    any16 = true;
-    const size_t n = (size_t)m->L.g.nx * m->L.g.ny;
-    CK(launch_maxdev_eq(aux_view(m), m->stage, m->stage + n, m->stage + 2 * n, 0, nullptr,
-                        b->dflags + k, b->stream));
-  }
-  if (any16) {
-    CK(cudaMemcpyAsync(bits.data(), b->dflags, sizeof(unsigned int) * nm, cudaMemcpyDeviceToHost,
-                       b->stream));
-    CK(cudaStreamSynchronize(b->stream));
-    for (size_t k = 0; k < nm; ++k)
-      if (b->members[k]->L.dtype == LBM_F16DEV) {
-        float mx;
-        memcpy(&mx, &bits[k], sizeof(mx));
-        set_qscale(b->members[k], (double)mx);
-      }
-    int rc = batch_refresh_params(b);
-    if (rc != LBM_OK) return rc;
-  }
-  // equilibria into each member's current buffer (the batch's bookkeeping
-  // of buffers stays valid), fields validated on the device
-  std::vector<unsigned int> bad(nm, 0);
-  for (size_t k = 0; k < nm; ++k) {
-    auto *m = b->members[k];
-    const size_t n = (size_t)m->L.g.nx * m->L.g.ny;
-    CK(launch_init_eq(aux_view(m), m->stage, m->stage + n, m->stage + 2 * n, 0, nullptr,
-                      b->stream, b->dflags + nm + k));
-  }
-  CK(cudaMemcpyAsync(bad.data(), b->dflags + nm, sizeof(unsigned int) * nm,
-                     cudaMemcpyDeviceToHost, b->stream));
-  CK(cudaStreamSynchronize(b->stream));
-  for (auto *m : b->members) m->t = 0;
-  for (size_t k = 0; k < nm; ++k)
-    if (bad[k]) {
-      set_error("member " + std::to_string(k) + ": " + std::to_string(bad[k]) +
-                " nodes with non-finite fields or rho <= 0");
-      return LBM_EINVAL;
-    }
-  return LBM_OK;
+    cudaError_t e = cudaMemcpyAsync(m->stage, rho[k], n * sizeof(double),
+                                    cudaMemcpyHostToDevice, b->io);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(m->stage + n, ux[k], n * sizeof(double), cudaMemcpyHostToDevice, b->io);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(m->stage + 2 * n, uy[k], n * sizeof(double), cudaMemcpyHostToDevice,
+                          b->io);
+    return e;
+  };
+  return batch_init_common(b, ends, upload, fields);
 }
 
 int lbm_batch_moments(lbm_batch b, double *const *rho, double *const *ux, double *const *uy) {
@@ -1235,18 +1356,85 @@ int lbm_batch_moments(lbm_batch b, double *const *rho, double *const *ux, double
     int rc = ensure_stage(m);
     if (rc != LBM_OK) return rc;
   }
-  for (size_t k = 0; k < nm; ++k) {
+  std::vector<size_t> ends(nm);
+  for (size_t k = 0; k < nm; ++k) ends[k] = k + 1;
+  auto fields = [&](size_t k, double *&r, double *&u, double *&v) {
+    const size_t n = (size_t)b->members[k]->L.g.nx * b->members[k]->L.g.ny;
+    r = b->members[k]->stage;
+    u = r + n;
+    v = r + 2 * n;
+  };
+  auto download = [&](size_t k) -> cudaError_t {
     auto *m = b->members[k];
     const size_t n = (size_t)m->L.g.nx * m->L.g.ny;
-    CK(launch_moments(aux_view(m), m->stage, m->stage + n, m->stage + 2 * n, b->stream));
-    CK(cudaMemcpyAsync(rho[k], m->stage, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
-    CK(cudaMemcpyAsync(ux[k], m->stage + n, n * sizeof(double), cudaMemcpyDeviceToHost,
-                       b->stream));
-    CK(cudaMemcpyAsync(uy[k], m->stage + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost,
-                       b->stream));
-  }
-  CK(cudaStreamSynchronize(b->stream));
+    cudaError_t e = cudaMemcpyAsync(rho[k], m->stage, n * sizeof(double),
+                                    cudaMemcpyDeviceToHost, b->io);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ux[k], m->stage + n, n * sizeof(double), cudaMemcpyDeviceToHost, b->io);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(uy[k], m->stage + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost,
+                          b->io);
+    return e;
+  };
+  return batch_moments_common(b, ends, download, fields);
+}
+
+int lbm_batch_size(lbm_batch b, int *members, long long *nodes) {
+  REQUIRE(b != nullptr, "null batch");
+  if (members) *members = (int)b->members.size();
+  if (nodes) *nodes = b->nodes;
   return LBM_OK;
+}
+
+int lbm_batch_init_packed(lbm_batch b, const double *rho, const double *ux, const double *uy) {
+  REQUIRE(b != nullptr && rho && ux && uy, "null argument");
+  REQUIRE(!b->spent, "batch ran a ragged generation; create a new batch");
+  DevGuard g(b->device);
+  int rc = ensure_packed(b);
+  if (rc != LBM_OK) return rc;
+  const size_t T = (size_t)b->nodes;
+  const std::vector<size_t> ends = packed_groups(b);
+  auto fields = [&](size_t k, const double *&r, const double *&u, const double *&v) {
+    r = b->pstage + b->poff[k];
+    u = r + T;
+    v = r + 2 * T;
+  };
+  auto upload = [&](size_t gi) -> cudaError_t {
+    const size_t k0 = gi == 0 ? 0 : ends[gi - 1];
+    const size_t o = b->poff[k0], cnt = b->poff[ends[gi]] - o;
+    cudaError_t e = cudaSuccess;
+    const double *src[3] = {rho, ux, uy};
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c)
+      e = cudaMemcpyAsync(b->pstage + c * T + o, src[c] + o, cnt * sizeof(double),
+                          cudaMemcpyHostToDevice, b->io);
+    return e;
+  };
+  return batch_init_common(b, ends, upload, fields);
+}
+
+int lbm_batch_moments_packed(lbm_batch b, double *rho, double *ux, double *uy) {
+  REQUIRE(b != nullptr && rho && ux && uy, "null argument");
+  DevGuard g(b->device);
+  int rc = ensure_packed(b);
+  if (rc != LBM_OK) return rc;
+  const size_t T = (size_t)b->nodes;
+  const std::vector<size_t> ends = packed_groups(b);
+  auto fields = [&](size_t k, double *&r, double *&u, double *&v) {
+    r = b->pstage + b->poff[k];
+    u = r + T;
+    v = r + 2 * T;
+  };
+  auto download = [&](size_t gi) -> cudaError_t {
+    const size_t k0 = gi == 0 ? 0 : ends[gi - 1];
+    const size_t o = b->poff[k0], cnt = b->poff[ends[gi]] - o;
+    cudaError_t e = cudaSuccess;
+    double *dst[3] = {rho, ux, uy};
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c)
+      e = cudaMemcpyAsync(dst[c] + o, b->pstage + c * T + o, cnt * sizeof(double),
+                          cudaMemcpyDeviceToHost, b->io);
+    return e;
+  };
+  return batch_moments_common(b, ends, download, fields);
 }
 
 int lbm_batch_get_variant(lbm_batch b, int *variant) {

@@ -109,6 +109,14 @@ cudaError_t launch_maxdev_eq(const AuxView &a, const double *rho, const double *
                              unsigned int *max_bits, cudaStream_t st);
 cudaError_t launch_moments(const AuxView &a, double *rho, double *ux, double *uy,
                            cudaStream_t st);
+// deviation storage types: equilibrium deviations formed from the
+// O(perturbation) differences to the reference state (io_dev.cu)
+cudaError_t launch_init_dev(const AuxView &a, const double *rho, const double *ux,
+                            const double *uy, cudaStream_t st, unsigned int *bad);
+cudaError_t launch_maxdev_dev(const AuxView &a, const double *rho, const double *ux,
+                              const double *uy, unsigned int *max_bits, cudaStream_t st);
+cudaError_t launch_moments_dev(const AuxView &a, double *rho, double *ux, double *uy,
+                               cudaStream_t st);
 cudaError_t launch_force_node(const AuxView &a, int x, int y, const double fs[9],
                               cudaStream_t st);
 cudaError_t launch_get_pop(const AuxView &a, double *f, cudaStream_t st);

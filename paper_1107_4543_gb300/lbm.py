@@ -63,6 +63,10 @@ _SIGS = {
     "lbm_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_batch_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_batch_get_variant": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_size": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_longlong)]),
+    "lbm_batch_init_packed": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
+    "lbm_batch_moments_packed": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
     "lbm_moments": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
     "lbm_moments_dev": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lbm_destroy": (ctypes.c_int, [_vp]),
@@ -373,6 +377,39 @@ def lbm_batch_moments(b, outs):
                                  _ptr_array([f[1] for f in outs]),
                                  _ptr_array([f[2] for f in outs])), "lbm_batch_moments")
     return outs
+
+
+def lbm_batch_size(b):
+    """(members, total nodes) of the batch."""
+    m, n = ctypes.c_int(), ctypes.c_longlong()
+    _ck(load().lbm_batch_size(b, ctypes.byref(m), ctypes.byref(n)), "lbm_batch_size")
+    return m.value, n.value
+
+
+def _packed(b, arrays, what):
+    n = lbm_batch_size(b)[1]
+    for a in arrays:
+        if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != n:
+            raise ValueError("%s must be contiguous float64 arrays of %d values" % (what, n))
+
+
+def lbm_batch_init_packed(b, rho, ux, uy):
+    """rho, ux, uy: contiguous float64 arrays of lbm_batch_size(b)[1] values,
+    member k's (ny, nx) field at the sum of nx*ny of the members before it."""
+    _packed(b, (rho, ux, uy), "fields")
+    _ck(load().lbm_batch_init_packed(b, _ptr(rho), _ptr(ux), _ptr(uy)), "lbm_batch_init_packed")
+
+
+def lbm_batch_moments_packed(b, out=None):
+    """Every member's rho, ux, uy in packed arrays (filled in place if out is
+    given)."""
+    if out is None:
+        n = lbm_batch_size(b)[1]
+        out = tuple(np.empty(n) for _ in range(3))
+    _packed(b, out, "outputs")
+    _ck(load().lbm_batch_moments_packed(b, _ptr(out[0]), _ptr(out[1]), _ptr(out[2])),
+        "lbm_batch_moments_packed")
+    return out
 
 
 def lbm_batch_destroy(b):

@@ -136,6 +136,46 @@ def test_batch_host_io_equals_member_calls(L):
         assert np.array_equal(outs[k][0], rho, equal_nan=True), (k, dt)
 
 
+def test_batch_packed_io_equals_per_member_io(L):
+    """lbm_batch_init_packed / lbm_batch_moments_packed give bit for bit what
+    the per-member calls give, across several copy groups (over 2^23 nodes)
+    with mixed storage types; the packed arrays are checked for size."""
+    specs = inp.batch_specs(9, seed=16, amin=700 * 700, amax=1800 * 1800)
+    specs[1].update(nx=33, ny=17)  # a ragged small member between large ones
+    dtypes = ["f32", "f16", "bf16"] * 3
+    fields = [inp.batch_fields(sp) for sp in specs]
+    total = sum(sp["nx"] * sp["ny"] for sp in specs)
+    assert total > 2 ** 23  # at least two copy groups
+
+    def make():
+        return [L.lbm_create(sp["nx"], sp["ny"], inp.s_ll(sp["rates"]), 1.0, (0.0, 0.0),
+                             L.DTYPES[dt]) for sp, dt in zip(specs, dtypes)]
+
+    ha, hb = make(), make()
+    try:
+        ba, bb = L.lbm_batch_create(ha), L.lbm_batch_create(hb)
+        assert L.lbm_batch_size(bb) == (9, total)
+        packed = [np.concatenate([f[c].ravel() for f in fields]) for c in range(3)]
+        for rep in range(2):
+            L.lbm_batch_init_fields(ba, fields)
+            L.lbm_batch_init_packed(bb, *packed)
+            L.lbm_batch_step(ba, 5 + rep)
+            L.lbm_batch_step(bb, 5 + rep)
+            outs = [tuple(np.empty((sp["ny"], sp["nx"])) for _ in range(3)) for sp in specs]
+            L.lbm_batch_moments(ba, outs)
+            got = L.lbm_batch_moments_packed(bb)
+            for c in range(3):
+                want = np.concatenate([o[c].ravel() for o in outs])
+                assert np.array_equal(got[c], want), (rep, c)
+        with pytest.raises(ValueError):
+            L.lbm_batch_init_packed(bb, packed[0][:-1], packed[1], packed[2])
+        L.lbm_batch_destroy(ba)
+        L.lbm_batch_destroy(bb)
+    finally:
+        for h in ha + hb:
+            L.lbm_destroy(h)
+
+
 def test_batch_results_match_oracle(L):
     specs = small_specs(6, seed=12)
     hs = []
