@@ -78,7 +78,11 @@ __device__ __forceinline__ void collide_dev(float &f0, float &f1, float &f2, flo
 
   // m^eq(rho, j) - m^eq(rho0, j0) for the three quadratic terms
   const float rho_phys = SCALED ? rho_p * P.inv_scale : rho_p;
-  const float c = rho_phys / (P.rho0 + rho_phys);  // rho'/rho
+  // rho'/rho by the hardware reciprocal (within 2 ulp): c only scales the
+  // O(amplitude^2) quadratic terms below, and unlike an IEEE division it has
+  // no slow path for non-finite operands, so a lattice that has gone
+  // unstable costs no more per node than a healthy one
+  const float c = __fdividef(rho_phys, P.rho0 + rho_phys);
   const float jxx = SCALED ? (jx_p * jx_p) * P.inv_scale : jx_p * jx_p;
   const float jyy = SCALED ? (jy_p * jy_p) * P.inv_scale : jy_p * jy_p;
   const float jxy = SCALED ? (jx_p * jy_p) * P.inv_scale : jx_p * jy_p;

@@ -150,20 +150,25 @@ template <> struct Elem<double> {
   static __device__ __forceinline__ double one(const double *p) { return __ldg(p); }
 };
 
-// Work mapping: the lattice's rows of ceil(nx / V) chunks form one row-major
-// sequence of chunks and warp task k takes chunks 32k .. 32k+31, so every
-// lane has work whatever nx is (a warp may span rows); a lane whose
-// neighbouring chunk lies in another row loads the edge element itself.
+// Work mapping: the lattice's rows of cpr = pitch / V chunk slots (the
+// ceil(nx / V) real chunks, then the padding up to the 128-byte row pitch)
+// form one row-major sequence and warp task k takes slots 32k .. 32k+31.
+// Every task then starts on a 128-byte line in all 9 planes (the y-shifted
+// rows too, the pitch being whole lines), and a warp may span rows, so
+// lanes have work whatever nx is; padding slots are inactive lanes.  A lane
+// whose neighbouring chunk is not in the neighbouring lane loads the edge
+// element itself.
 
 // geometry of one lattice as the step kernels see it
 struct Geom {
   int nx, ny, pitch;
-  int nchunks;      // vectors per row: ceil(nx / V)
+  int nchunks;      // real vectors per row: ceil(nx / V)
+  int cpr;          // chunk slots per row: pitch / V (>= nchunks)
   long long plane;  // pitch * ny
-  long long tasks;  // warp tasks per step: ceil(nchunks * ny / 32)
-  // row = chunk / nchunks as (chunk * dmul) >> dshift, exact for chunk
-  // indices below 2^31 (dshift = 31 + ceil(log2 nchunks), dmul =
-  // ceil(2^dshift / nchunks)); small = the lattice's chunks (+ one warp) fit
+  long long tasks;  // warp tasks per step: ceil(cpr * ny / 32)
+  // row = slot / cpr as (slot * dmul) >> dshift, exact for slot indices
+  // below 2^31 (dshift = 31 + ceil(log2 cpr), dmul = ceil(2^dshift / cpr));
+  // small = the lattice's slots (+ one warp) fit
   unsigned long long dmul;
   int dshift;
   int small;
@@ -173,23 +178,23 @@ struct Geom {
 struct LanePos {
   int y, x0;         // row, first node of the chunk
   bool first, last;  // the row's previous / next chunk is not in the previous / next lane
-  bool active;       // the chunk exists (task * 32 + lane < nchunks * ny)
+  bool active;       // a real chunk: slot in the lattice and xc < nchunks
 };
 
 template <int V>
 __device__ __forceinline__ LanePos lane_pos(const Geom &g, long long task, int lane) {
   LanePos p;
   const long long c = task * 32 + lane;
-  p.active = c < (long long)g.nchunks * g.ny;
   int y, xc;
   if (g.small) {  // multiply-shift division
     const unsigned cu = (unsigned)c;
     y = (int)(((unsigned long long)cu * g.dmul) >> g.dshift);
-    xc = (int)(cu - (unsigned)y * (unsigned)g.nchunks);
+    xc = (int)(cu - (unsigned)y * (unsigned)g.cpr);
   } else {
-    y = (int)(c / g.nchunks);
-    xc = (int)(c - (long long)y * g.nchunks);
+    y = (int)(c / g.cpr);
+    xc = (int)(c - (long long)y * g.cpr);
   }
+  p.active = y < g.ny && xc < g.nchunks;
   if (!p.active) y = xc = 0;
   p.y = y;
   p.x0 = xc * V;

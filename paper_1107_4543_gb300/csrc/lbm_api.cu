@@ -77,12 +77,13 @@ static Geom make_geom(int nx, int ny, int V, int esize) {
   const int align = std::max(V, 128 / esize);  // rows start on 128-byte lines
   g.pitch = (nx + align - 1) / align * align;
   g.nchunks = (nx + V - 1) / V;
+  g.cpr = g.pitch / V;  // a multiple of 128 bytes of chunks: tasks start on lines
   g.plane = (long long)g.pitch * ny;
-  g.tasks = ((long long)g.nchunks * ny + 31) / 32;
+  g.tasks = ((long long)g.cpr * ny + 31) / 32;
   int k = 31;
-  while ((1LL << (k - 31)) < (long long)g.nchunks) ++k;  // 31 + ceil(log2 nchunks)
+  while ((1LL << (k - 31)) < (long long)g.cpr) ++k;  // 31 + ceil(log2 cpr)
   g.dshift = k;
-  g.dmul = ((1ULL << k) + (unsigned long long)g.nchunks - 1) / (unsigned long long)g.nchunks;
+  g.dmul = ((1ULL << k) + (unsigned long long)g.cpr - 1) / (unsigned long long)g.cpr;
   g.small = g.tasks * 32 < (1LL << 31) ? 1 : 0;
   return g;
 }
