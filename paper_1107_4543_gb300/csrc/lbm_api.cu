@@ -777,8 +777,9 @@ struct lbm_batch_ctx {
     int dtype;
     int n;
     long long ntasks;
+    long long nblocks;
     BatchEntry *ents = nullptr;
-    int *block_first = nullptr;
+    BlockRec *blocks = nullptr;
     int *limits = nullptr;  // per-entry step limits of a ragged generation
   };
   std::vector<int> member_group, member_local;  // member -> (group, entry)
@@ -819,11 +820,20 @@ static int ensure_io(lbm_batch_ctx *b) {
   return LBM_OK;
 }
 
+static BatchList batch_list(const lbm_batch_ctx::Group &gr) {
+  BatchList bl;
+  bl.ents = gr.ents;
+  bl.n = gr.n;
+  bl.blocks = gr.blocks;
+  bl.nblocks = gr.nblocks;
+  bl.ntasks = gr.ntasks;
+  return bl;
+}
+
 static cudaError_t batch_launch_all(lbm_batch_ctx *b, int parity, cudaStream_t st,
                                     int variant) {
   for (auto &gr : b->groups) {
-    cudaError_t e = launch_step_batch(gr.dtype, gr.ents, gr.n, gr.block_first, gr.ntasks, parity,
-                                      st, b->block, variant);
+    cudaError_t e = launch_step_batch(gr.dtype, batch_list(gr), parity, st, b->block, variant);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -928,8 +938,8 @@ int batch_step_ragged(lbm_batch_ctx *b, const long *steps, long n) {
                        cudaMemcpyHostToDevice, b->stream));
   for (long k = 0; k < n; ++k)
     for (auto &gr : b->groups)
-      CK(launch_step_batch(gr.dtype, gr.ents, gr.n, gr.block_first, gr.ntasks, (int)(k & 1),
-                           b->stream, b->block, b->variant, gr.limits, (int)k));
+      CK(launch_step_batch(gr.dtype, batch_list(gr), (int)(k & 1), b->stream, b->block,
+                           b->variant, gr.limits, (int)k));
   for (size_t mi = 0; mi < nm; ++mi) {
     b->members[mi]->L.cur = b->offs[mi] ^ (int)(take[mi] & 1);
     b->members[mi]->t += take[mi];
@@ -952,7 +962,7 @@ static void batch_free(lbm_batch_ctx *b) {
   dev_free(b->pstage);
   for (auto &gr : b->groups) {
     dev_free(gr.ents);
-    dev_free(gr.block_first);
+    dev_free(gr.blocks);
     dev_free(gr.limits);
   }
   dev_free(b->views[0]);
@@ -1163,6 +1173,7 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
   b->member_local.assign(b->members.size(), -1);
   for (int dt : {LBM_F32DEV, LBM_F16DEV, LBM_BF16DEV}) {
     std::vector<BatchEntry> ents;
+    std::vector<BlockRec> bl;  // the plain grid's blocks
     long long t0 = 0;
     for (size_t mi = 0; mi < b->members.size(); ++mi) {
       auto *m = b->members[mi];
@@ -1177,6 +1188,16 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
       e.off = m->L.cur;
       e.task0 = t0;
       t0 += m->L.g.tasks;
+      for (long long tb = 0; tb < m->L.g.tasks; tb += wpb) {
+        BlockRec r;
+        r.g = e.g;
+        r.buf[0] = e.buf[0];
+        r.buf[1] = e.buf[1];
+        r.task_base = tb;
+        r.lat = (int)ents.size();
+        r.off = e.off;
+        bl.push_back(r);
+      }
       ents.push_back(e);
     }
     if (ents.empty()) continue;
@@ -1184,26 +1205,19 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
     gr.dtype = dt;
     gr.n = (int)ents.size();
     gr.ntasks = t0;
-    const long long nblocks = (t0 + wpb - 1) / wpb;
-    std::vector<int> bf((size_t)nblocks);
-    int l = 0;
-    for (long long blk = 0; blk < nblocks; ++blk) {
-      const long long task = blk * wpb;
-      while (l + 1 < gr.n && ents[l + 1].task0 <= task) ++l;
-      bf[(size_t)blk] = l;
-    }
+    gr.nblocks = (long long)bl.size();
     gr.ents = (BatchEntry *)dev_alloc(sizeof(BatchEntry) * ents.size());
-    gr.block_first = (int *)dev_alloc(sizeof(int) * bf.size());
+    gr.blocks = (BlockRec *)dev_alloc(sizeof(BlockRec) * bl.size());
     gr.limits = (int *)dev_alloc(sizeof(int) * ents.size());
     b->groups.push_back(gr);
-    if (!gr.ents || !gr.block_first || !gr.limits) {
+    if (!gr.ents || !gr.blocks || !gr.limits) {
       set_error("cannot allocate batch tables");
       batch_free(b);
       return LBM_ENOMEM;
     }
     if (cudaMemcpyAsync(gr.ents, ents.data(), sizeof(BatchEntry) * ents.size(),
                         cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
-        cudaMemcpyAsync(gr.block_first, bf.data(), sizeof(int) * bf.size(),
+        cudaMemcpyAsync(gr.blocks, bl.data(), sizeof(BlockRec) * bl.size(),
                         cudaMemcpyHostToDevice, b->stream) != cudaSuccess) {
       set_error("cannot upload batch tables");
       cudaGetLastError();

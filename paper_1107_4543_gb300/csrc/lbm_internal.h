@@ -32,6 +32,28 @@ struct BatchEntry {
   long long task0;   // first task of this lattice in the flattened list
 };
 
+// One block of a batch's plain grid: every lattice starts on a block
+// boundary, and each block carries its lattice's geometry and buffers, so a
+// warp finds its work with one load and no search; the relaxation
+// parameters (needed only by the collision) come from the lattice's entry.
+struct BlockRec {
+  Geom g;
+  void *buf[2];
+  long long task_base;  // lattice task of the block's warp 0
+  int lat;              // lattice index in the entry list
+  int off;              // as BatchEntry::off
+};
+
+// Device work list of one storage type's batch members.  The persistent
+// grids walk the flattened task list (BatchEntry::task0).
+struct BatchList {
+  const BatchEntry *ents;
+  int n;
+  const BlockRec *blocks;  // the plain grid's blocks
+  long long nblocks;       // sum over lattices of ceil(tasks / warps per block)
+  long long ntasks;        // sum of the lattices' tasks
+};
+
 // launch helpers (step_f32.cu, step_f16.cu, step_bf16.cu, step_f64.cu).
 // `variant` selects the register cap of the deviation step kernels
 // (0, 1, 2: at least 1, 2, 3 resident 256-thread blocks per SM).
@@ -45,14 +67,11 @@ cudaError_t launch_step_dev_f16(const Lattice &L, const void *src, void *dst, cu
                                 int block, int variant);
 cudaError_t launch_step_dev_bf16(const Lattice &L, const void *src, void *dst, cudaStream_t st,
                                  int block, int variant);
-cudaError_t launch_step_batch_f32(const BatchEntry *ents, int n, const int *block_first,
-                                  long long ntasks, int parity, cudaStream_t st, int block,
+cudaError_t launch_step_batch_f32(const BatchList &bl, int parity, cudaStream_t st, int block,
                                   int variant, const int *limits, int k);
-cudaError_t launch_step_batch_f16(const BatchEntry *ents, int n, const int *block_first,
-                                  long long ntasks, int parity, cudaStream_t st, int block,
+cudaError_t launch_step_batch_f16(const BatchList &bl, int parity, cudaStream_t st, int block,
                                   int variant, const int *limits, int k);
-cudaError_t launch_step_batch_bf16(const BatchEntry *ents, int n, const int *block_first,
-                                   long long ntasks, int parity, cudaStream_t st, int block,
+cudaError_t launch_step_batch_bf16(const BatchList &bl, int parity, cudaStream_t st, int block,
                                    int variant, const int *limits, int k);
 cudaError_t launch_step_f64(const Lattice &L, const void *src, void *dst,
                             cudaStream_t st, int block, int grid_cap);
@@ -67,20 +86,13 @@ inline cudaError_t launch_step_dev(const Lattice &L, const void *src, void *dst,
   }
 }
 
-inline cudaError_t launch_step_batch(int dtype, const BatchEntry *ents, int n,
-                                     const int *block_first, long long ntasks, int parity,
-                                     cudaStream_t st, int block, int variant,
-                                     const int *limits = nullptr, int k = 0) {
+inline cudaError_t launch_step_batch(int dtype, const BatchList &bl, int parity, cudaStream_t st,
+                                     int block, int variant, const int *limits = nullptr,
+                                     int k = 0) {
   switch (dtype) {
-    case LBM_F32DEV:
-      return launch_step_batch_f32(ents, n, block_first, ntasks, parity, st, block, variant,
-                                   limits, k);
-    case LBM_F16DEV:
-      return launch_step_batch_f16(ents, n, block_first, ntasks, parity, st, block, variant,
-                                   limits, k);
-    case LBM_BF16DEV:
-      return launch_step_batch_bf16(ents, n, block_first, ntasks, parity, st, block, variant,
-                                    limits, k);
+    case LBM_F32DEV: return launch_step_batch_f32(bl, parity, st, block, variant, limits, k);
+    case LBM_F16DEV: return launch_step_batch_f16(bl, parity, st, block, variant, limits, k);
+    case LBM_BF16DEV: return launch_step_batch_bf16(bl, parity, st, block, variant, limits, k);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -8,11 +8,9 @@ cudaError_t launch_step_dev_bf16(const Lattice &L, const void *src, void *dst, c
   return launch_step_dev_t<__nv_bfloat16>(L, src, dst, st, block, variant);
 }
 
-cudaError_t launch_step_batch_bf16(const BatchEntry *ents, int n, const int *block_first,
-                                long long ntasks, int parity, cudaStream_t st, int block,
-                                int variant, const int *limits, int k) {
-  return launch_step_batch_t<__nv_bfloat16>(ents, n, block_first, ntasks, parity, st, block, variant,
-                                 limits, k);
+cudaError_t launch_step_batch_bf16(const BatchList &bl, int parity, cudaStream_t st, int block,
+                                   int variant, const int *limits, int k) {
+  return launch_step_batch_t<__nv_bfloat16>(bl, parity, st, block, variant, limits, k);
 }
 
 }  // namespace lbm

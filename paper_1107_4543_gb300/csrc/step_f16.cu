@@ -8,11 +8,9 @@ cudaError_t launch_step_dev_f16(const Lattice &L, const void *src, void *dst, cu
   return launch_step_dev_t<__half>(L, src, dst, st, block, variant);
 }
 
-cudaError_t launch_step_batch_f16(const BatchEntry *ents, int n, const int *block_first,
-                                long long ntasks, int parity, cudaStream_t st, int block,
-                                int variant, const int *limits, int k) {
-  return launch_step_batch_t<__half>(ents, n, block_first, ntasks, parity, st, block, variant,
-                                 limits, k);
+cudaError_t launch_step_batch_f16(const BatchList &bl, int parity, cudaStream_t st, int block,
+                                  int variant, const int *limits, int k) {
+  return launch_step_batch_t<__half>(bl, parity, st, block, variant, limits, k);
 }
 
 }  // namespace lbm

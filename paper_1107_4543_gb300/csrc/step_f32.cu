@@ -8,11 +8,9 @@ cudaError_t launch_step_dev_f32(const Lattice &L, const void *src, void *dst, cu
   return launch_step_dev_t<float>(L, src, dst, st, block, variant);
 }
 
-cudaError_t launch_step_batch_f32(const BatchEntry *ents, int n, const int *block_first,
-                                long long ntasks, int parity, cudaStream_t st, int block,
-                                int variant, const int *limits, int k) {
-  return launch_step_batch_t<float>(ents, n, block_first, ntasks, parity, st, block, variant,
-                                 limits, k);
+cudaError_t launch_step_batch_f32(const BatchList &bl, int parity, cudaStream_t st, int block,
+                                  int variant, const int *limits, int k) {
+  return launch_step_batch_t<float>(bl, parity, st, block, variant, limits, k);
 }
 
 }  // namespace lbm

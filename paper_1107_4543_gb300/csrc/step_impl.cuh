@@ -49,26 +49,26 @@ k_step_dev(const T *__restrict__ src, T *__restrict__ dst, Geom g, DevParams P,
     step_task<T>(src, dst, g, P, task, lane);
 }
 
-// Batched: tasks of all lattices flattened; block b starts its lookup at
-// lattice block_first[b] (blocks cover consecutive tasks, so a warp walks
-// forward at most a few entries).
-// limits (may be null): lattice l takes part only while k < limits[l], so
-// members of one launch sequence can stop after different step counts.
+// Batched, plain grid: every lattice starts on a block boundary and block b
+// reads its lattice's geometry and buffers from blocks[b] (one load before
+// the pull can start; a search over the lattices' task offsets, or a
+// lattice index followed by the lattice's entry, cost 10-15% of the
+// bandwidth on batches of small lattices).  Warps past the lattice's last
+// task return.  limits (may be null): lattice l takes part only while
+// k < limits[l], so members of one launch sequence can stop after different
+// step counts.
 template <typename T, int MINB>
 __global__ void __launch_bounds__(256, MINB)
-k_step_batch(const BatchEntry *__restrict__ ents, int n, const int *__restrict__ block_first,
-             long long ntasks, int parity, const int *__restrict__ limits, int k) {
+k_step_batch(const BatchEntry *__restrict__ ents, const BlockRec *__restrict__ blocks,
+             int parity, const int *__restrict__ limits, int k) {
   const int lane = threadIdx.x & 31;
-  const long long task = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (task >= ntasks) return;  // warp-uniform
-  int l = block_first[blockIdx.x];
-  while (l + 1 < n && ents[l + 1].task0 <= task) ++l;
-  if (limits != nullptr && k >= limits[l]) return;  // warp-uniform
-  const BatchEntry &E = ents[l];
-  const int from = parity ^ E.off;
-  const T *src = static_cast<const T *>(E.buf[from]);
-  T *dst = static_cast<T *>(E.buf[from ^ 1]);
-  step_task<T>(src, dst, E.g, E.dp, task - E.task0, lane);
+  const BlockRec &B = blocks[blockIdx.x];
+  const long long task = B.task_base + (threadIdx.x >> 5);
+  if (task >= B.g.tasks) return;                         // warp-uniform
+  if (limits != nullptr && k >= limits[B.lat]) return;   // block-uniform
+  const int from = parity ^ B.off;
+  step_task<T>(static_cast<const T *>(B.buf[from]), static_cast<T *>(B.buf[from ^ 1]), B.g,
+               ents[B.lat].dp, task, lane);
 }
 
 static inline long long n_tasks(const Geom &g) { return g.tasks; }
@@ -134,46 +134,43 @@ cudaError_t launch_step_dev_t(const Lattice &L, const void *src, void *dst, cuda
 }
 
 template <typename T>
-cudaError_t launch_step_batch_t(const BatchEntry *ents, int n, const int *block_first,
-                                long long ntasks, int parity, cudaStream_t st, int block,
+cudaError_t launch_step_batch_t(const BatchList &bl, int parity, cudaStream_t st, int block,
                                 int variant, const int *limits, int k) {
   const int wpb = block / 32;
-  const long long grid = (ntasks + wpb - 1) / wpb;
-  if (grid < 1) return cudaSuccess;
+  if (bl.nblocks < 1 || bl.ntasks < 1) return cudaSuccess;
   if (variant >= kStepVariants) {
     // persistent: MINB resident blocks per SM, contiguous task ranges
     const int minb = variant - kStepVariants + 1;
+    const long long grid = (bl.ntasks + wpb - 1) / wpb;
     long long pgrid = (long long)sm_count() * minb;
     if (pgrid > grid) pgrid = grid;
-    const long long per_warp = (ntasks + pgrid * wpb - 1) / (pgrid * wpb);
+    const long long per_warp = (bl.ntasks + pgrid * wpb - 1) / (pgrid * wpb);
     switch (minb) {
       case 1:
-        k_step_batch_persist<T, 1><<<(unsigned)pgrid, block, 0, st>>>(ents, n, ntasks, parity,
-                                                                     limits, k, per_warp);
+        k_step_batch_persist<T, 1><<<(unsigned)pgrid, block, 0, st>>>(
+            bl.ents, bl.n, bl.ntasks, parity, limits, k, per_warp);
         break;
       case 2:
-        k_step_batch_persist<T, 2><<<(unsigned)pgrid, block, 0, st>>>(ents, n, ntasks, parity,
-                                                                     limits, k, per_warp);
+        k_step_batch_persist<T, 2><<<(unsigned)pgrid, block, 0, st>>>(
+            bl.ents, bl.n, bl.ntasks, parity, limits, k, per_warp);
         break;
       default:
-        k_step_batch_persist<T, 3><<<(unsigned)pgrid, block, 0, st>>>(ents, n, ntasks, parity,
-                                                                     limits, k, per_warp);
+        k_step_batch_persist<T, 3><<<(unsigned)pgrid, block, 0, st>>>(
+            bl.ents, bl.n, bl.ntasks, parity, limits, k, per_warp);
         break;
     }
     return cudaGetLastError();
   }
+  const unsigned grid = (unsigned)bl.nblocks;
   switch (variant) {
     case 0:
-      k_step_batch<T, 1><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity,
-                                                          limits, k);
+      k_step_batch<T, 1><<<grid, block, 0, st>>>(bl.ents, bl.blocks, parity, limits, k);
       break;
     case 1:
-      k_step_batch<T, 2><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity,
-                                                          limits, k);
+      k_step_batch<T, 2><<<grid, block, 0, st>>>(bl.ents, bl.blocks, parity, limits, k);
       break;
     default:
-      k_step_batch<T, 3><<<(unsigned)grid, block, 0, st>>>(ents, n, block_first, ntasks, parity,
-                                                          limits, k);
+      k_step_batch<T, 3><<<grid, block, 0, st>>>(bl.ents, bl.blocks, parity, limits, k);
       break;
   }
   return cudaGetLastError();
