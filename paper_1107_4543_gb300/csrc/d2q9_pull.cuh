@@ -31,13 +31,14 @@ __host__ __device__ constexpr int CYd(int i) {
 
 // ---------------------------------------------------------- element I/O
 // Nodes per vector for the 16-bit storage types: 8 (16-byte vectors) or 4
-// (8-byte vectors, half the registers).  Measured on GB300: FP16 streams
-// fastest with 8, BF16 (whose 8-wide kernel needs ~180 registers) with 4.
+// (8-byte vectors).  With the packed pull (pull9_packed: shifts on packed
+// words, two nodes unpacked at a time) both stream fastest with 8 on GB300:
+// 8192^2 FP16 6.46 TB/s, BF16 6.25 TB/s (4-wide: 5.55 and 5.41).
 #ifndef LBM_VF16
 #define LBM_VF16 8
 #endif
 #ifndef LBM_VBF16
-#define LBM_VBF16 4
+#define LBM_VBF16 8
 #endif
 
 template <int BYTES> struct RawOf;
@@ -105,6 +106,15 @@ template <> struct Elem<__half> {
   static __device__ __forceinline__ float one(const __half *p) {
     return __half2float(__ldg(p));
   }
+  // two packed elements <-> two floats (element 2k in the low half)
+  static __device__ __forceinline__ void unpack2(uint32_t w, float *o) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+    o[0] = f.x; o[1] = f.y;
+  }
+  static __device__ __forceinline__ uint32_t pack2(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+  }
 };
 
 template <> struct Elem<__nv_bfloat16> {
@@ -132,6 +142,14 @@ template <> struct Elem<__nv_bfloat16> {
   }
   static __device__ __forceinline__ float one(const __nv_bfloat16 *p) {
     return __bfloat162float(__ldg(p));
+  }
+  static __device__ __forceinline__ void unpack2(uint32_t w, float *o) {
+    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
+    o[0] = f.x; o[1] = f.y;
+  }
+  static __device__ __forceinline__ uint32_t pack2(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
   }
 };
 
@@ -300,6 +318,99 @@ __device__ __forceinline__ void store9(T *__restrict__ dst, const Geom &g, const
     for (int e = 0; e < V; ++e) v[e] = SCALED ? in[i][e] * scale : in[i][e];
     T *row = dst + (long long)i * g.plane + (long long)p.y * g.pitch;
     *reinterpret_cast<typename Elem<T>::R::type *>(row + p.x0) = Elem<T>::pack(v);
+  }
+}
+
+// 16-bit storage types: the same pull with the populations kept packed,
+// out[i][k] holding nodes 2k (low half) and 2k + 1 (high half) of this
+// lane's chunk.  The +-1 x-shifts are byte permutes of neighbouring words
+// (and of the neighbouring lane's edge word), which move the stored bits
+// unchanged, so the caller can unpack, collide and repack two nodes at a
+// time instead of holding 9 x V floats per lane.
+__device__ __forceinline__ uint32_t raw16(const void *p) {
+  return (uint32_t)__ldg(static_cast<const unsigned short *>(p));
+}
+
+template <typename T>
+__device__ __forceinline__ void pull9_packed(const T *__restrict__ src, const Geom &g,
+                                             const LanePos &p,
+                                             uint32_t (&out)[9][Elem<T>::V / 2]) {
+  constexpr int V = Elem<T>::V;
+  constexpr int W = V / 2;
+  static_assert(sizeof(T) == 2 && V % 2 == 0, "16-bit storage types only");
+  const int last = g.nx - 1;
+  const int e_last = (p.x0 <= last && last < p.x0 + V) ? last - p.x0 : -1;
+  const bool need_prev = p.active && p.first;
+  const int x_prev = p.x0 == 0 ? last : p.x0 - 1;
+  const bool need_next = p.active && p.last && p.x0 + V <= last;
+  const bool need_wrap = p.active && e_last >= 0;
+
+  using RawT = typename Elem<T>::R::type;
+  RawT raw[9];
+  uint32_t edge[9], wrap0[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int cx = CXd(i), cy = CYd(i);
+    int ys = p.y - cy;
+    ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
+    const T *row = src + (long long)i * g.plane + (long long)ys * g.pitch;
+    raw[i] = p.active ? __ldg(reinterpret_cast<const RawT *>(row + p.x0)) : Elem<T>::R::zero();
+    edge[i] = 0u;
+    wrap0[i] = 0u;
+    if (cx == 1) {
+      if (need_prev) edge[i] = raw16(row + x_prev);
+    } else if (cx == -1) {
+      if (need_next) edge[i] = raw16(row + p.x0 + V);
+      if (need_wrap) wrap0[i] = raw16(row);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int cx = CXd(i);
+    uint32_t v[W];
+    Elem<T>::R::words(raw[i], v);
+    if (cx == 0) {
+#pragma unroll
+      for (int k = 0; k < W; ++k) out[i][k] = v[k];
+    } else if (cx == 1) {
+      // node x pulls from x - 1: word k = (high half of v[k-1], low half of v[k])
+      uint32_t prevw = __shfl_up_sync(0xffffffffu, v[W - 1], 1);
+      if (need_prev) prevw = edge[i] << 16;
+      out[i][0] = __byte_perm(prevw, v[0], 0x5432);
+#pragma unroll
+      for (int k = 1; k < W; ++k) out[i][k] = __byte_perm(v[k - 1], v[k], 0x5432);
+    } else {
+      // node x pulls from x + 1 (column 0 for the last real node)
+      uint32_t nextw = __shfl_down_sync(0xffffffffu, v[0], 1);
+      if (need_next) nextw = edge[i];
+#pragma unroll
+      for (int k = 0; k < W - 1; ++k) out[i][k] = __byte_perm(v[k], v[k + 1], 0x5432);
+      out[i][W - 1] = __byte_perm(v[W - 1], nextw, 0x5432);
+      if (need_wrap) {
+        // the last real node's element takes column 0 (a select per word,
+        // so that the array stays in registers)
+        const int kw = e_last >> 1;
+        const uint32_t keep = (e_last & 1) ? 0xffffu : 0xffff0000u;
+        const uint32_t put = (e_last & 1) ? (wrap0[i] << 16) : wrap0[i];
+#pragma unroll
+        for (int k = 0; k < W; ++k) out[i][k] = k == kw ? ((out[i][k] & keep) | put) : out[i][k];
+      }
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store9_packed(T *__restrict__ dst, const Geom &g,
+                                              const LanePos &p,
+                                              const uint32_t (&in)[9][Elem<T>::V / 2]) {
+  if (!p.active) return;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    T *row = dst + (long long)i * g.plane + (long long)p.y * g.pitch;
+    if constexpr (Elem<T>::V == 8)
+      *reinterpret_cast<uint4 *>(row + p.x0) = make_uint4(in[i][0], in[i][1], in[i][2], in[i][3]);
+    else
+      *reinterpret_cast<uint2 *>(row + p.x0) = make_uint2(in[i][0], in[i][1]);
   }
 }
 

@@ -26,13 +26,33 @@ __device__ __forceinline__ void step_task(const T *__restrict__ src, T *__restri
   constexpr bool SCALED = std::is_same<T, __half>::value;
   constexpr bool PRECISE = std::is_same<T, float>::value;
   LanePos p = lane_pos<V>(g, task, lane);
-  float f[9][V];
-  pull9<T, false>(src, g, p, 1.0f, f);
+  if constexpr (sizeof(T) == 2) {
+    // 16-bit storage: pull packed, then unpack / collide / repack two nodes
+    // at a time (9 x V floats per lane would not fit the register budget)
+    uint32_t w[9][V / 2];
+    pull9_packed<T>(src, g, p, w);
 #pragma unroll
-  for (int e = 0; e < V; ++e)
-    collide_dev<PRECISE, SCALED>(f[0][e], f[1][e], f[2][e], f[3][e], f[4][e], f[5][e], f[6][e],
-                                 f[7][e], f[8][e], P);
-  store9<T, false>(dst, g, p, 1.0f, f);
+    for (int k = 0; k < V / 2; ++k) {
+      float f[9][2];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) Elem<T>::unpack2(w[i][k], f[i]);
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+        collide_dev<PRECISE, SCALED>(f[0][e], f[1][e], f[2][e], f[3][e], f[4][e], f[5][e],
+                                     f[6][e], f[7][e], f[8][e], P);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) w[i][k] = Elem<T>::pack2(f[i][0], f[i][1]);
+    }
+    store9_packed<T>(dst, g, p, w);
+  } else {
+    float f[9][V];
+    pull9<T, false>(src, g, p, 1.0f, f);
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+      collide_dev<PRECISE, SCALED>(f[0][e], f[1][e], f[2][e], f[3][e], f[4][e], f[5][e], f[6][e],
+                                   f[7][e], f[8][e], P);
+    store9<T, false>(dst, g, p, 1.0f, f);
+  }
 }
 
 // MINB: minimum resident 256-thread blocks per SM asked of the compiler,
