@@ -44,6 +44,12 @@ TABLE1 = {
     "C": dict(sigma_e=0.1, sigma_nu=0.1, sigma_eps=0.0, sigma_q=26.3631592758091),
     "D": dict(sigma_e=0.1, sigma_nu=0.1, sigma_eps=0.0, sigma_q=26.3520430827600),
 }
+# Reading: groups C and D print sigma_e = sigma_nu = 0.1, but their sigma_q
+# and cost values are those of sigma_e = sigma_nu = 0.01 (the cost F^o at
+# the printed optimum is 17.9107478 with 0.01 and 2.2e5 with 0.1, and
+# minimizing with 0.01 reproduces the printed sigma_q to 1e-7); read as 0.01.
+TABLE1_READ = {g: (dict(t, sigma_e=0.01, sigma_nu=0.01) if g in "CD" else dict(t))
+               for g, t in TABLE1.items()}
 TABLE2 = {
     "A": dict(sigma_e=0.001, sigma_nu=0.001, sigma_eps=0.00751873323089156,
               sigma_q=0.00171909400064198),

@@ -9,7 +9,10 @@ with the CUDA library.
   moments of section 2.3);
 * ``oracle.vn`` builds the von Neumann amplification matrix of section 4.1
   from the printed Psi of section 2.3;
-* ``oracle.pulse`` evaluates the Gaussian-pulse solution of section 5.2.
+* ``oracle.pulse`` evaluates the Gaussian-pulse solution of section 5.2;
+* ``oracle.modified`` runs the recursive algorithm of section 2.2 (the
+  modified equations of the linearized scheme) and the cost functions and
+  parameter minimization of sections 3.2 and 4.2.
 
 Relaxation rates are given here in the paper's moment order
 (rho, jx, jy, e, eps, qx, qy, pxx, pxy); ``s_paper`` builds that vector.
