@@ -18,8 +18,10 @@ reduction).
   fp64_plain the plain FP64 path on one 8192^2 lattice, for comparison
   cpu_baseline  the FP64 CPU oracle on a bounded sample of the workload
 
-Other workloads: --workload large (one 8192^2 lattice, per storage type)
-and --workload serving (Poisson request stream through lbm_submit/poll).
+Other workloads: --workload large (one 8192^2 lattice, per storage type),
+--workload serving (Poisson request stream through lbm_submit/poll),
+--workload vn (von Neumann eigenvalue sweep) and --workload opt (the
+free-parameter cost functions and their minimization).
 --impl reference times the CPU oracle on the same metric.
 """
 import argparse
@@ -52,7 +54,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="batched",
-                   choices=["batched", "large", "serving", "vn"])
+                   choices=["batched", "large", "serving", "vn", "opt"])
     p.add_argument("--lattices", type=int, default=512)
     p.add_argument("--lbm-steps", type=int, default=500)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -503,6 +505,51 @@ def bench_vn(args, L, torch):
                              "kind": "oracle", "sample": "%d cases, numpy eigvals" % kx.size}}
 
 
+def bench_opt(args, L, torch):
+    """Free-parameter optimization (sections 3.2, 4.2): calligraphic G of
+    section 3.2.3 (n = 4, flow speeds in [0, 0.2]) for a 32 x 32 grid of
+    (sigma_eps, sigma_q) candidates -- 4800 quadrature points each, one
+    modified-equation recursion per point -- and the full minimization that
+    reproduces Table 3 group A."""
+    import oracle.modified as om
+
+    t3 = inp.TABLE3["A"]
+    e = np.logspace(-5, 0, 32)
+    E, Qg = np.meshgrid(e, e, indexing="ij")
+    sig = np.column_stack([np.full(E.size, t3["sigma_e"]), E.ravel(), Qg.ravel(),
+                           np.full(E.size, t3["sigma_nu"])])
+    spec = L.cost_spec("G", 4, "all", "ns-bulk")
+    L.lbm_opt_cost(spec, sig[:8])  # warm-up
+    times = []
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        L.lbm_opt_cost(spec, sig)
+        times.append(time.perf_counter() - t0)
+    rate = sig.shape[0] / min(times)
+    t0 = time.perf_counter()
+    r, c, ev = L.lbm_opt_minimize(spec, dict(t3, sigma_eps=0.5, sigma_q=0.5),
+                                  ("sigma_eps", "sigma_q"), dict(sigma_eps=0.0, sigma_q=0.0),
+                                  dict(sigma_eps=1.0, sigma_q=1.0))
+    t_min = time.perf_counter() - t0
+    # CPU baseline: the oracle's cost (numpy, vectorized over the points)
+    t0 = time.perf_counter()
+    nc = 4
+    for k in range(nc):
+        om.cost(sig[k * 97], 4, "G", "all", 0.2, "ns-bulk")
+    cpu = nc / (time.perf_counter() - t0)
+    return {"metric": "section 3.2 cost evaluations (calligraphic G, n = 4) per second",
+            "value": round(rate, 2), "unit": "costs/s", "higher_is_better": True,
+            "config": {"workload": "opt-G-n4-%d-candidates" % sig.shape[0],
+                       "points_per_cost": 4800},
+            "minimize": {"seconds": round(t_min, 3), "evals": ev, "cost": c,
+                         "sigma_eps": r["sigma_eps"], "sigma_q": r["sigma_q"],
+                         "printed": {"sigma_eps": t3["sigma_eps"], "sigma_q": t3["sigma_q"],
+                                     "cost": 14.453655614637361}},
+            "note": "host arrays in and out, device allocation per call included",
+            "cpu_baseline": {"value": round(cpu, 3), "unit": "costs/s", "cores": 1,
+                             "kind": "oracle", "sample": "%d candidates, numpy" % nc}}
+
+
 def reference_arm(args):
     """The CPU oracle timed as the reference implementation."""
     specs = inp.batch_specs(args.lattices, seed=1107 + 4, steps=args.lbm_steps)
@@ -559,6 +606,10 @@ def main():
     if args.workload == "vn":
         if rank == 0:
             print(json.dumps(bench_vn(args, L, torch)))
+        return
+    if args.workload == "opt":
+        if rank == 0:
+            print(json.dumps(bench_opt(args, L, torch)))
         return
     line, specs = bench_batched(args, L, torch, rank, ws)
     if rank == 0:

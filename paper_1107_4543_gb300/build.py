@@ -28,6 +28,7 @@ UNITS = {
     "serve.cu": [],
     "drift_noalloc.cu": [],
     "vn.cu": [],
+    "optcost.cu": [],
 }
 HEADERS = ["lbm_internal.h", "d2q9_pull.cuh", "collide.cuh", "step_impl.cuh"]
 

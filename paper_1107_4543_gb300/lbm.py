@@ -49,6 +49,18 @@ class lbm_server_stats_t(ctypes.Structure):
                 ("busy_s", ctypes.c_double)]
 
 
+class lbm_cost_spec(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("order", ctypes.c_int), ("part", ctypes.c_int),
+                ("reference", ctypes.c_int), ("u0", ctypes.c_double),
+                ("fixed_speed", ctypes.c_int)]
+
+
+LBM_COST_F, LBM_COST_G = 0, 1
+LBM_PART_ALL, LBM_PART_ODD, LBM_PART_EVEN = 0, 1, 2
+LBM_REF_NS, LBM_REF_EULER, LBM_REF_NS_BULK = 0, 1, 2
+SIGMA_NAMES = ("sigma_e", "sigma_eps", "sigma_q", "sigma_nu")
+
+
 _SIGS = {
     "lbm_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, _dp,
                                   ctypes.c_int, ctypes.POINTER(_vp)]),
@@ -63,6 +75,9 @@ _SIGS = {
     "lbm_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_batch_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_batch_get_variant": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_opt_cost": (ctypes.c_int, [ctypes.POINTER(lbm_cost_spec), ctypes.c_int, _dp, _dp]),
+    "lbm_opt_minimize": (ctypes.c_int, [ctypes.POINTER(lbm_cost_spec), _dp, ctypes.c_uint, _dp,
+                                        _dp, _dp, _dp, ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_size": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_longlong)]),
     "lbm_batch_init_packed": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
@@ -410,6 +425,52 @@ def lbm_batch_moments_packed(b, out=None):
     _ck(load().lbm_batch_moments_packed(b, _ptr(out[0]), _ptr(out[1]), _ptr(out[2])),
         "lbm_batch_moments_packed")
     return out
+
+
+def cost_spec(kind="F", order=5, part="all", reference=None, u0=0.2, fixed_speed=False):
+    """lbm_cost_spec from names: kind 'F' / 'G', part 'all' / 'odd' / 'even',
+    reference 'ns' / 'euler' / 'ns-bulk' (default 'ns' for F, 'euler' for G)."""
+    if reference is None:
+        reference = "ns" if kind == "F" else "euler"
+    return lbm_cost_spec(
+        {"F": LBM_COST_F, "G": LBM_COST_G}[kind], int(order),
+        {"all": LBM_PART_ALL, "odd": LBM_PART_ODD, "even": LBM_PART_EVEN}[part],
+        {"ns": LBM_REF_NS, "euler": LBM_REF_EULER, "ns-bulk": LBM_REF_NS_BULK}[reference],
+        float(u0), 1 if fixed_speed else 0)
+
+
+def lbm_opt_cost(spec, sigmas):
+    """Costs of candidates: sigmas (n, 4) = (sigma_e, sigma_eps, sigma_q,
+    sigma_nu) per row -> (n,) array."""
+    sig = _f64(np.atleast_2d(np.asarray(sigmas, dtype=np.float64)))
+    if sig.ndim != 2 or sig.shape[1] != 4:
+        raise ValueError("sigmas must have shape (n, 4)")
+    out = np.empty(sig.shape[0])
+    _ck(load().lbm_opt_cost(ctypes.byref(spec), sig.shape[0], _ptr(sig), _ptr(out)),
+        "lbm_opt_cost")
+    return out
+
+
+def lbm_opt_minimize(spec, sigmas, free, lo, hi):
+    """Minimize over the sigmas named in `free` (others held at `sigmas`)
+    within [lo, hi] (dicts by name).  Returns (dict of the four sigmas,
+    cost, number of cost evaluations)."""
+    s_in = _f64(np.asarray([sigmas[k] for k in SIGMA_NAMES], dtype=np.float64))
+    mask = 0
+    lo_a = np.zeros(4)
+    hi_a = np.ones(4)
+    for i, k in enumerate(SIGMA_NAMES):
+        if k in free:
+            mask |= 1 << i
+            lo_a[i] = lo[k]
+            hi_a[i] = hi[k]
+    s_out = np.empty(4)
+    c = ctypes.c_double()
+    ev = ctypes.c_int()
+    _ck(load().lbm_opt_minimize(ctypes.byref(spec), _ptr(s_in), mask, _ptr(lo_a), _ptr(hi_a),
+                                _ptr(s_out), ctypes.byref(c), ctypes.byref(ev)),
+        "lbm_opt_minimize")
+    return dict(zip(SIGMA_NAMES, s_out.tolist())), c.value, ev.value
 
 
 def lbm_batch_destroy(b):
