@@ -140,6 +140,8 @@ def test_dev_random_populations_ragged(L, dtype, nx, ny):
     (rho, ux, uy), f = run_gpu(L, nx, ny, r, steps, L.DTYPES[dtype], pops=pops)
     (rho_o, ux_o, uy_o), f_o = run_orc(r, steps, pops=pops)
     A = np.max(np.abs(pops.sum(axis=0) - 1.0))
+    print("\n%s random populations %dx%d: max|drho'|/A = %.2e, max|df|/A = %.2e"
+          % (dtype, nx, ny, max_rel(rho, rho_o, A), max_rel(f, f_o, A)))
     assert max_rel(rho, rho_o, A) <= RANDOM_TOL[dtype]
     assert max_rel(f, f_o, A) <= RANDOM_TOL[dtype]
     assert max_rel(ux, ux_o, A) <= RANDOM_TOL[dtype]
