@@ -93,46 +93,46 @@ k_step_batch(const BatchEntry *__restrict__ ents, const BlockRec *__restrict__ b
 
 static inline long long n_tasks(const Geom &g) { return g.tasks; }
 
-// Persistent batched variant: a grid of a few blocks per SM; warp w takes
-// the contiguous tasks [w * per_warp, (w + 1) * per_warp), finds its first
-// lattice by binary search and walks forward, keeping the current lattice's
-// entry in shared memory, so the descriptor lookup happens once per lattice
-// instead of once per task.
+// Persistent batched variant: a grid of MINB blocks per SM strides over the
+// plain grid's block records (block b takes records b, b + grid, ...), so
+// at any time the grid works on a window of consecutive records, as the
+// plain grid does.  Each warp keeps its current record in shared memory and
+// fetches the next one (one word per lane, a single register) while it
+// steps the current task, so the record's latency is hidden behind the
+// step instead of opening every block.
 template <typename T, int MINB>
 __global__ void __launch_bounds__(256, MINB)
-k_step_batch_persist(const BatchEntry *__restrict__ ents, int n, long long ntasks, int parity,
-                     const int *__restrict__ limits, int k, long long per_warp) {
-  __shared__ BatchEntry cur[8];
+k_step_batch_stride(const BatchEntry *__restrict__ ents, const BlockRec *__restrict__ blocks,
+                    long long nblocks, int parity, const int *__restrict__ limits, int k) {
+  constexpr int NW = sizeof(BlockRec) / 4;
+  static_assert(sizeof(BlockRec) % 4 == 0 && NW <= 32, "a record must fit one word per lane");
+  __shared__ BlockRec rec[2][8];
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long t0 = warp * per_warp;
-  const long long t1 = t0 + per_warp < ntasks ? t0 + per_warp : ntasks;
-  if (t0 >= t1) return;  // warp-uniform
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (ents[mid].task0 <= t0) lo = mid; else hi = mid - 1;
-  }
-  int l = lo;
-  long long next0 = l + 1 < n ? ents[l + 1].task0 : ntasks;
-  if (lane == 0) cur[wib] = ents[l];
+  const int w = threadIdx.x >> 5;
+  long long b = blockIdx.x;
+  if (b >= nblocks) return;  // block-uniform
+  if (lane < NW)
+    reinterpret_cast<uint32_t *>(&rec[0][w])[lane] =
+        __ldg(reinterpret_cast<const uint32_t *>(blocks + b) + lane);
   __syncwarp();
-  for (long long task = t0; task < t1; ++task) {
-    if (task >= next0) {
-      while (task >= next0) {
-        ++l;
-        next0 = l + 1 < n ? ents[l + 1].task0 : ntasks;
-      }
-      __syncwarp();
-      if (lane == 0) cur[wib] = ents[l];
-      __syncwarp();
+  int s = 0;
+  for (;;) {
+    const long long nb = b + gridDim.x;
+    uint32_t next = 0;
+    if (nb < nblocks && lane < NW) next = __ldg(reinterpret_cast<const uint32_t *>(blocks + nb) + lane);
+    const BlockRec &B = rec[s][w];
+    const long long task = B.task_base + w;
+    if (task < B.g.tasks && !(limits != nullptr && k >= limits[B.lat])) {  // warp-uniform
+      const int from = parity ^ B.off;
+      step_task<T>(static_cast<const T *>(B.buf[from]), static_cast<T *>(B.buf[from ^ 1]), B.g,
+                   ents[B.lat].dp, task, lane);
     }
-    if (limits != nullptr && k >= limits[l]) continue;  // warp-uniform
-    const BatchEntry &E = cur[wib];
-    const int from = parity ^ E.off;
-    step_task<T>(static_cast<const T *>(E.buf[from]), static_cast<T *>(E.buf[from ^ 1]), E.g,
-                 E.dp, task - E.task0, lane);
+    if (nb >= nblocks) break;
+    __syncwarp();
+    if (lane < NW) reinterpret_cast<uint32_t *>(&rec[s ^ 1][w])[lane] = next;
+    __syncwarp();
+    s ^= 1;
+    b = nb;
   }
 }
 
@@ -159,24 +159,22 @@ cudaError_t launch_step_batch_t(const BatchList &bl, int parity, cudaStream_t st
   const int wpb = block / 32;
   if (bl.nblocks < 1 || bl.ntasks < 1) return cudaSuccess;
   if (variant >= kStepVariants) {
-    // persistent: MINB resident blocks per SM, contiguous task ranges
+    // persistent: MINB resident blocks per SM striding over the records
     const int minb = variant - kStepVariants + 1;
-    const long long grid = (bl.ntasks + wpb - 1) / wpb;
     long long pgrid = (long long)sm_count() * minb;
-    if (pgrid > grid) pgrid = grid;
-    const long long per_warp = (bl.ntasks + pgrid * wpb - 1) / (pgrid * wpb);
+    if (pgrid > bl.nblocks) pgrid = bl.nblocks;
     switch (minb) {
       case 1:
-        k_step_batch_persist<T, 1><<<(unsigned)pgrid, block, 0, st>>>(
-            bl.ents, bl.n, bl.ntasks, parity, limits, k, per_warp);
+        k_step_batch_stride<T, 1><<<(unsigned)pgrid, block, 0, st>>>(
+            bl.ents, bl.blocks, bl.nblocks, parity, limits, k);
         break;
       case 2:
-        k_step_batch_persist<T, 2><<<(unsigned)pgrid, block, 0, st>>>(
-            bl.ents, bl.n, bl.ntasks, parity, limits, k, per_warp);
+        k_step_batch_stride<T, 2><<<(unsigned)pgrid, block, 0, st>>>(
+            bl.ents, bl.blocks, bl.nblocks, parity, limits, k);
         break;
       default:
-        k_step_batch_persist<T, 3><<<(unsigned)pgrid, block, 0, st>>>(
-            bl.ents, bl.n, bl.ntasks, parity, limits, k, per_warp);
+        k_step_batch_stride<T, 3><<<(unsigned)pgrid, block, 0, st>>>(
+            bl.ents, bl.blocks, bl.nblocks, parity, limits, k);
         break;
     }
     return cudaGetLastError();
