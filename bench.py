@@ -20,8 +20,9 @@ reduction).
 
 Other workloads: --workload large (one 8192^2 lattice, per storage type),
 --workload serving (Poisson request stream through lbm_submit/poll),
---workload vn (von Neumann eigenvalue sweep) and --workload opt (the
-free-parameter cost functions and their minimization).
+--workload vn (von Neumann eigenvalue sweep), --workload opt (the
+free-parameter cost functions and their minimization) and --workload oracle
+(the CPU oracle alone: one thread and all cores).
 --impl reference times the CPU oracle on the same metric.
 """
 import argparse
@@ -54,7 +55,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="batched",
-                   choices=["batched", "large", "serving", "vn", "opt"])
+                   choices=["batched", "large", "serving", "vn", "opt", "oracle"])
     p.add_argument("--lattices", type=int, default=512)
     p.add_argument("--lbm-steps", type=int, default=500)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -550,6 +551,42 @@ def bench_opt(args, L, torch):
                              "kind": "oracle", "sample": "%d candidates, numpy" % nc}}
 
 
+def oracle_timing(args):
+    """The FP64 CPU oracle as it stands on the host cores: config 1 in full
+    with one thread and with all cores, and config 3 (8192^2) timed over 20
+    steps with all cores, extrapolated to its 1000 steps.  CPU only."""
+    import oracle as orc
+
+    cores = os.cpu_count() or 1
+    out = {"metric": "FP64 CPU oracle MLUPS", "unit": "MLUPS", "cores": cores,
+           "kind": "oracle"}
+    n, steps = 64, 200
+    fields = inp.gaussian_pulse(n, n, 1e-3, 4.0)
+    s = inp.s_paper(inp.rates("LL", nu=1e-3))
+    for threads in (1, cores):
+        orc.set_threads(threads)
+        f = orc.init_eq(*fields)
+        orc.run(f, s, 5)
+        t0 = time.perf_counter()
+        orc.run(f, s, steps)
+        dt = time.perf_counter() - t0
+        out["config1_64x64_200_steps_%d_threads" % threads] = round(n * n * steps / dt / 1e6, 2)
+    n, steps = 8192, 20
+    orc.set_threads(cores)
+    rho, ux, uy = inp.pulse_with_vortices(n, n, seed=1107 + 3)
+    f = orc.init_eq(rho, ux, uy)
+    del rho, ux, uy
+    s = inp.s_paper(inp.rates("OPT"))
+    orc.run(f, s, 1)
+    t0 = time.perf_counter()
+    orc.run(f, s, steps)
+    dt = time.perf_counter() - t0
+    out["config3_8192x8192"] = {"mlups": round(n * n * steps / dt / 1e6, 2),
+                                "seconds_per_step": round(dt / steps, 3),
+                                "extrapolated_1000_steps_s": round(1000 * dt / steps, 1)}
+    return out
+
+
 def reference_arm(args):
     """The CPU oracle timed as the reference implementation."""
     specs = inp.batch_specs(args.lattices, seed=1107 + 4, steps=args.lbm_steps)
@@ -576,6 +613,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(reference_arm(args)))
+        return
+    if args.workload == "oracle":
+        if rank == 0:
+            print(json.dumps(oracle_timing(args)))
         return
     import torch
 
