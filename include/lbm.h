@@ -295,9 +295,10 @@ int lbm_opt_minimize(const lbm_cost_spec *spec, const double sigmas_in[4],
 
 /* ------------------------------------------------------------- batches */
 /* Many independent lattices advanced together: every time step is ONE
- * kernel launch per storage type over a flattened (lattice, row group,
- * segment) work list of all members, and chunks of 64 steps are replayed
- * from a captured CUDA graph.  Members must be deviation-storage lattices
+ * kernel launch per storage type over a work list of all members (each
+ * lattice starts on a block boundary; one record per block gives its
+ * lattice, geometry and buffers), and chunks of 64 steps are replayed from a
+ * captured CUDA graph.  Members must be deviation-storage lattices
  * (LBM_F32DEV, LBM_F16DEV or LBM_BF16DEV) created on the current device,
  * none of them in another batch; they keep their own memory, rates and
  * reference state, and each advances with exactly the arithmetic of
@@ -342,8 +343,8 @@ int lbm_batch_moments_packed(lbm_batch b, double *rho, double *ux, double *uy);
 /* As lbm_tune for the batch's launches (one variant for all its storage
  * types; the first lbm_batch_step of a batch of >= 2^20 nodes tunes unless
  * LBM_AUTOTUNE=0).  Batches have LBM_BATCH_TUNE_VARIANTS variants: the
- * three register caps with one warp per task, then the same caps with a
- * persistent grid in which each warp takes a contiguous range of tasks.
+ * three register caps with one block per record, then the same caps with a
+ * persistent grid of a few blocks per SM striding over the records.
  * times_ms receives LBM_BATCH_TUNE_VARIANTS entries.  Members' states do
  * not change. */
 #define LBM_BATCH_TUNE_VARIANTS 6

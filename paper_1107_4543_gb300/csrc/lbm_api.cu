@@ -1190,7 +1190,6 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
       e.buf[0] = m->L.buf[0];
       e.buf[1] = m->L.buf[1];
       e.off = m->L.cur;
-      e.task0 = t0;
       t0 += m->L.g.tasks;
       for (long long tb = 0; tb < m->L.g.tasks; tb += wpb) {
         BlockRec r;

@@ -29,7 +29,6 @@ struct BatchEntry {
   DevParams dp;
   void *buf[2];
   int off;           // buffer index holding the state when the batch began
-  long long task0;   // first task of this lattice in the flattened list
 };
 
 // One block of a batch's plain grid: every lattice starts on a block
@@ -44,8 +43,9 @@ struct BlockRec {
   int off;              // as BatchEntry::off
 };
 
-// Device work list of one storage type's batch members.  The persistent
-// grids walk the flattened task list (BatchEntry::task0).
+// Device work list of one storage type's batch members: per-lattice
+// entries and the plain grid's block records (the persistent grids stride
+// over the same records).
 struct BatchList {
   const BatchEntry *ents;
   int n;
@@ -59,7 +59,7 @@ struct BatchList {
 // (0, 1, 2: at least 1, 2, 3 resident 256-thread blocks per SM).
 constexpr int kStepVariants = 3;
 // batched launches add kStepVariants persistent variants (the same register
-// caps, contiguous task ranges per warp)
+// caps, a grid of MINB blocks per SM striding over the block records)
 constexpr int kBatchVariants = 2 * kStepVariants;
 cudaError_t launch_step_dev_f32(const Lattice &L, const void *src, void *dst, cudaStream_t st,
                                 int block, int variant);

@@ -156,7 +156,6 @@ cudaError_t launch_step_dev_t(const Lattice &L, const void *src, void *dst, cuda
 template <typename T>
 cudaError_t launch_step_batch_t(const BatchList &bl, int parity, cudaStream_t st, int block,
                                 int variant, const int *limits, int k) {
-  const int wpb = block / 32;
   if (bl.nblocks < 1 || bl.ntasks < 1) return cudaSuccess;
   if (variant >= kStepVariants) {
     // persistent: MINB resident blocks per SM striding over the records
