@@ -136,8 +136,15 @@ int lbm_set_source(lbm_handle h, int x, int y, double amplitude, double period);
 int lbm_tune(lbm_handle h, double *times_ms, int *chosen);
 /* Use launch variant `variant` (0 .. LBM_TUNE_VARIANTS-1) for later steps,
  * without timing (no automatic tuning afterwards).  Every variant computes
- * the same result; they differ only in speed. */
+ * the same result; they differ only in speed.  lbm_get_variant reports the
+ * variant in use once chosen (by tuning, the tuning file, lbm_set_variant or
+ * a small lattice's first step), -1 before; LBM_F64 reports 0.
+ * With LBM_TUNE_CACHE=<path> in the environment the choices of lbm_step's
+ * automatic tuning and of the batches' are also read from and appended to
+ * that file (one line per choice, keyed by GPU model, storage type and
+ * size), so later processes skip the timing runs. */
 int lbm_set_variant(lbm_handle h, int variant);
+int lbm_get_variant(lbm_handle h, int *variant);
 
 /* lbm_moments -- rho, ux, uy (host, ny x nx) at the current time: the
  * moments of the pre-collision populations, u = j / rho.  Synchronizes. */

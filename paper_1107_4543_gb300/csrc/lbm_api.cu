@@ -70,28 +70,6 @@ int sm_count() {
   return n;
 }
 
-static Geom make_geom(int nx, int ny, int V, int esize) {
-  Geom g;
-  g.nx = nx;
-  g.ny = ny;
-  const int align = std::max(V, 128 / esize);  // rows start on 128-byte lines
-  g.pitch = (nx + align - 1) / align * align;
-  g.nchunks = (nx + V - 1) / V;
-  g.cpr = g.pitch / V;  // a multiple of 128 bytes of chunks: tasks start on lines
-  // row-interleaved planes: row y of planes 0..8 lie back to back, so the
-  // nine rows a warp task streams share DRAM pages (measured +0.6% on the
-  // batched step, +2% on one 8192^2 lattice against plane after plane)
-  g.plane = g.pitch;
-  g.rstride = 9LL * g.pitch;
-  g.tasks = ((long long)g.cpr * ny + 31) / 32;
-  int k = 31;
-  while ((1LL << (k - 31)) < (long long)g.cpr) ++k;  // 31 + ceil(log2 cpr)
-  g.dshift = k;
-  g.dmul = ((1ULL << k) + (unsigned long long)g.cpr - 1) / (unsigned long long)g.cpr;
-  g.small = g.tasks * 32 < (1LL << 31) ? 1 : 0;
-  return g;
-}
-
 struct DevGuard {
   int prev = -1, want;
   explicit DevGuard(int d) : want(d) {
@@ -201,6 +179,73 @@ static bool autotune_enabled() {
 // Tuner results per (dtype, nx, ny), shared by the handles of a process.
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int>, int> g_tune_cache;
+// batch choices read from the tuning file, by the hash of the composition
+static std::map<unsigned long long, int> g_batch_file_cache;
+
+// Optional tuning file (environment LBM_TUNE_CACHE = path): lines
+// "<device> L <dtype>:<nx>:<ny> <variant>" and "<device> B <hash> <variant>"
+// are read once per process and appended as new choices are made, so later
+// processes on the same GPU model skip the timing runs.  <device> is the GPU
+// name and SM count; lines of other devices and malformed lines are
+// ignored.  Called with g_tune_mu held.
+static const char *tune_file() {
+  const char *p = getenv("LBM_TUNE_CACHE");
+  return (p && p[0]) ? p : nullptr;
+}
+
+static std::string device_tag() {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string t = prop.name;
+  for (char &c : t)
+    if (c == ' ' || c == '\t') c = '_';
+  return t + "_sm" + std::to_string(prop.multiProcessorCount);
+}
+
+static unsigned long long fnv1a(const std::string &s) {
+  unsigned long long h = 1469598103934665603ULL;
+  for (unsigned char c : s) {
+    h ^= c;
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
+
+static void tune_file_load_locked() {
+  static bool loaded = false;
+  if (loaded) return;
+  loaded = true;
+  const char *path = tune_file();
+  if (!path) return;
+  FILE *fp = fopen(path, "r");
+  if (!fp) return;
+  const std::string tag = device_tag();
+  char dtag[256], kind[4], key[128];
+  int v;
+  while (fscanf(fp, "%255s %3s %127s %d", dtag, kind, key, &v) == 4) {
+    if (tag != dtag) continue;
+    if (kind[0] == 'L' && v >= 0 && v < kStepVariants) {
+      int dt, nx, ny;
+      if (sscanf(key, "%d:%d:%d", &dt, &nx, &ny) == 3) g_tune_cache[std::make_tuple(dt, nx, ny)] = v;
+    } else if (kind[0] == 'B' && v >= 0 && v < kBatchVariants) {
+      g_batch_file_cache[strtoull(key, nullptr, 16)] = v;
+    }
+  }
+  fclose(fp);
+}
+
+static void tune_file_append_locked(const char *kind, const std::string &key, int v) {
+  const char *path = tune_file();
+  if (!path) return;
+  FILE *fp = fopen(path, "a");
+  if (!fp) return;
+  fprintf(fp, "%s %s %s %d\n", device_tag().c_str(), kind, key.c_str(), v);
+  fclose(fp);
+}
 
 // Average duration of `reps` launches produced by `launch(k)` on stream st.
 template <typename F>
@@ -316,6 +361,8 @@ static int tune_handle(lbm_ctx *h, double *times) {
   h->tuned = true;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[std::make_tuple(h->L.dtype, h->L.g.nx, h->L.g.ny)] = bv;
+  tune_file_append_locked("L", std::to_string(h->L.dtype) + ":" + std::to_string(h->L.g.nx) + ":" +
+                                   std::to_string(h->L.g.ny), bv);
   return LBM_OK;
 }
 
@@ -328,6 +375,7 @@ static int maybe_autotune(lbm_ctx *h) {
   }
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_file_load_locked();
     auto it = g_tune_cache.find(std::make_tuple(h->L.dtype, h->L.g.nx, h->L.g.ny));
     if (it != g_tune_cache.end()) {
       if (it->second != h->L.variant) {
@@ -594,6 +642,7 @@ int lbm_init_analytic(lbm_handle h, int kind, const double params[8]) {
 }
 
 int lbm_step(lbm_handle h, long n) {
+  NvtxRange nvtx("lbm_step");
   REQUIRE(h != nullptr, "null handle");
   REQUIRE(n >= 0, "negative step count");
   REQUIRE(h->batch == nullptr, "lattice is a batch member; step the batch");
@@ -748,6 +797,7 @@ int lbm_set_populations(lbm_handle h, const double *f) {
 }
 
 int lbm_drift(lbm_handle h, double out[4]) {
+  NvtxRange nvtx("lbm_drift");
   REQUIRE(h && out, "null argument");
   DevGuard g(h->device);
   CK(launch_drift(aux_view(h), h->partials, h->drift_out, h->stream));
@@ -881,7 +931,11 @@ static int tune_batch(lbm_batch_ctx *b, double *times) {
   }
   b->tuned = true;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_batch_tune_cache[batch_key(b)] = bv;
+  const std::string key = batch_key(b);
+  g_batch_tune_cache[key] = bv;
+  char hex[32];
+  snprintf(hex, sizeof(hex), "%016llx", fnv1a(key));
+  tune_file_append_locked("B", hex, bv);
   return LBM_OK;
 }
 
@@ -892,8 +946,15 @@ static int maybe_autotune_batch(lbm_batch_ctx *b) {
     int cached = -1;
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
-      auto it = g_batch_tune_cache.find(batch_key(b));
-      if (it != g_batch_tune_cache.end()) cached = it->second;
+      tune_file_load_locked();
+      const std::string key = batch_key(b);
+      auto it = g_batch_tune_cache.find(key);
+      if (it != g_batch_tune_cache.end()) {
+        cached = it->second;
+      } else {
+        auto jt = g_batch_file_cache.find(fnv1a(key));
+        if (jt != g_batch_file_cache.end()) cached = jt->second;
+      }
     }
     if (cached >= 0) {
       b->variant = cached;
@@ -1028,6 +1089,7 @@ static int batch_refresh_params(lbm_batch_ctx *b) {
 template <class Upload, class Fields>
 static int batch_init_common(lbm_batch_ctx *b, const std::vector<size_t> &ends, Upload upload,
                              Fields fields) {
+  NvtxRange nvtx("batch host upload + init");
   int rc = ensure_io(b);
   if (rc != LBM_OK) return rc;
   const size_t nm = b->members.size();
@@ -1091,6 +1153,7 @@ static int batch_init_common(lbm_batch_ctx *b, const std::vector<size_t> &ends, 
 template <class Download, class Fields>
 static int batch_moments_common(lbm_batch_ctx *b, const std::vector<size_t> &ends,
                                 Download download, Fields fields) {
+  NvtxRange nvtx("batch moments + download");
   int rc = ensure_io(b);
   if (rc != LBM_OK) return rc;
   size_t k = 0;
@@ -1275,6 +1338,7 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
 }
 
 int lbm_batch_step(lbm_batch b, long n) {
+  NvtxRange nvtx("lbm_batch_step");
   REQUIRE(b != nullptr, "null batch");
   REQUIRE(n >= 0, "negative step count");
   DevGuard g(b->device);
@@ -1455,6 +1519,12 @@ int lbm_batch_moments_packed(lbm_batch b, double *rho, double *ux, double *uy) {
   return batch_moments_common(b, ends, download, fields);
 }
 
+int lbm_get_variant(lbm_handle h, int *variant) {
+  REQUIRE(h != nullptr && variant != nullptr, "null argument");
+  *variant = h->L.dtype == LBM_F64 ? 0 : (h->tuned ? h->L.variant : -1);
+  return LBM_OK;
+}
+
 int lbm_batch_get_variant(lbm_batch b, int *variant) {
   REQUIRE(b != nullptr && variant != nullptr, "null argument");
   *variant = b->tuned ? b->variant : -1;
@@ -1477,6 +1547,7 @@ int lbm_batch_tune(lbm_batch b, double *times_ms, int *chosen) {
 }
 
 int lbm_batch_drift(lbm_batch b, double *out) {
+  NvtxRange nvtx("lbm_batch_drift");
   REQUIRE(b != nullptr && out != nullptr, "null argument");
   REQUIRE(!b->spent, "batch ran a ragged generation; use lbm_drift per member");
   DevGuard g(b->device);

@@ -4,11 +4,24 @@
 
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lbm.h"
 #include "collide.cuh"
 #include "d2q9_pull.cuh"
 
 namespace lbm {
+
+// NVTX range for the lifetime of a scope: step chunks, batch steps, host I/O
+// and serving generations show up by name in a profiler's timeline
+// (header-only NVTX; without a profiler attached the calls do nothing).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 
 // Everything a step launch needs about one lattice.
 struct Lattice {

@@ -494,6 +494,7 @@ bool valid_sigmas(const double *s) {
 extern "C" {
 
 int lbm_opt_cost(const lbm_cost_spec *spec, int n, const double *sigmas, double *out) {
+  lbm::NvtxRange nvtx("lbm_opt_cost");
   if (n < 0 || (n > 0 && (!sigmas || !out))) {
     lbm::set_error("bad cost arguments");
     return LBM_EINVAL;
@@ -516,6 +517,7 @@ int lbm_opt_cost(const lbm_cost_spec *spec, int n, const double *sigmas, double 
 int lbm_opt_minimize(const lbm_cost_spec *spec, const double sigmas_in[4], unsigned free_mask,
                      const double lo[4], const double hi[4], double sigmas_out[4],
                      double *cost_out, int *evals) {
+  lbm::NvtxRange nvtx("lbm_opt_minimize");
   CostSpec cs;
   if (!sigmas_in || !sigmas_out || !lo || !hi || make_spec(spec, &cs) != LBM_OK ||
       !valid_sigmas(sigmas_in) || (free_mask & 15u) == 0 || (free_mask & ~15u) != 0) {

@@ -227,6 +227,7 @@ static void worker_loop(lbm_server_ctx *s) {
     const double t0 = now_s();
     int rc = LBM_OK;
     if (n > 0) {
+      lbm::NvtxRange nvtx("serve generation");
       std::vector<lbm_handle> hs;
       for (Req *q : run) hs.push_back(q->h);
       lbm_batch b = nullptr;

@@ -75,6 +75,7 @@ _SIGS = {
     "lbm_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_batch_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_batch_get_variant": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_get_variant": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "lbm_opt_cost": (ctypes.c_int, [ctypes.POINTER(lbm_cost_spec), ctypes.c_int, _dp, _dp]),
     "lbm_opt_minimize": (ctypes.c_int, [ctypes.POINTER(lbm_cost_spec), _dp, ctypes.c_uint, _dp,
                                         _dp, _dp, _dp, ctypes.POINTER(ctypes.c_int)]),
@@ -245,6 +246,12 @@ def lbm_set_variant(h, variant):
 
 def lbm_batch_set_variant(b, variant):
     _ck(load().lbm_batch_set_variant(b, int(variant)), "lbm_batch_set_variant")
+
+
+def lbm_get_variant(h):
+    v = ctypes.c_int()
+    _ck(load().lbm_get_variant(h, ctypes.byref(v)), "lbm_get_variant")
+    return v.value
 
 
 def lbm_batch_get_variant(b):

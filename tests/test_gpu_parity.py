@@ -417,3 +417,42 @@ def test_torch_caching_allocator_through_lbm_set_allocator(L):
         L.lbm_set_allocator(None, None)
     assert calls["alloc"] > 0 and calls["free"] == calls["alloc"]
     assert np.array_equal(got, want)
+
+
+TUNE_SCRIPT = """
+import lbm_inputs as inp
+from paper_1107_4543_gb300 import lbm as L
+L.load()
+h = L.lbm_create(1024, 1024, inp.s_ll(inp.rates("OPT")), 1.0, (0.0, 0.0), L.LBM_F32DEV)
+assert L.lbm_get_variant(h) == -1
+L.lbm_init_analytic(h, L.LBM_INIT_GAUSSIAN, (1e-3, 8.0, 512.0, 512.0))
+L.lbm_step(h, 1)
+print("VARIANT", L.lbm_get_variant(h))
+L.lbm_destroy(h)
+"""
+
+
+def test_tuning_file_is_written_and_read(L, tmp_path):
+    """LBM_TUNE_CACHE: the first process tunes a 2^20-node lattice and
+    appends its choice; a second process takes the (edited) choice from the
+    file instead of timing."""
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    path = tmp_path / "tune.txt"
+    env = dict(os.environ, LBM_TUNE_CACHE=str(path), LBM_AUTOTUNE="1")
+
+    def run():
+        r = subprocess.run([sys.executable, "-c", TUNE_SCRIPT], cwd=root, env=env,
+                           capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr[-2000:]
+        return int(r.stdout.split("VARIANT")[1].split()[0])
+
+    v = run()
+    lines = path.read_text().split("\n")
+    rec = [ln.split() for ln in lines if " L 1:1024:1024 " in ln]
+    assert len(rec) == 1 and int(rec[0][3]) == v and 0 <= v < 3
+    w = (v + 1) % 3
+    path.write_text("%s L 1:1024:1024 %d\n" % (rec[0][0], w))
+    assert run() == w
