@@ -56,8 +56,10 @@ __device__ __forceinline__ void step_task(const T *__restrict__ src, T *__restri
 }
 
 // MINB: minimum resident 256-thread blocks per SM asked of the compiler,
-// i.e. a register cap (1: none, 2: 128, 3: 80 registers).  The launch
-// variants of the tuner are MINB = 1, 2, 3.
+// i.e. a register cap (1: none, 2: 128, 3: 80 registers) and so the warps
+// an SM holds (8, 16, 24); the kernels are launched with smaller blocks
+// (64 threads) that fill the same warp slots.  The launch variants of the
+// tuner are MINB = 1, 2, 3.
 template <typename T, int MINB>
 __global__ void __launch_bounds__(256, MINB)
 k_step_dev(const T *__restrict__ src, T *__restrict__ dst, Geom g, DevParams P,
@@ -158,9 +160,10 @@ cudaError_t launch_step_batch_t(const BatchList &bl, int parity, cudaStream_t st
                                 int variant, const int *limits, int k) {
   if (bl.nblocks < 1 || bl.ntasks < 1) return cudaSuccess;
   if (variant >= kStepVariants) {
-    // persistent: MINB resident blocks per SM striding over the records
+    // persistent: the resident blocks (MINB x 256 threads per SM) striding
+    // over the records
     const int minb = variant - kStepVariants + 1;
-    long long pgrid = (long long)sm_count() * minb;
+    long long pgrid = (long long)sm_count() * minb * (256 / block);
     if (pgrid > bl.nblocks) pgrid = bl.nblocks;
     switch (minb) {
       case 1:
