@@ -235,6 +235,39 @@ def test_vn_unstable_band_claim():
                 assert np.max(np.abs(lam)) < 1.0 + 1e-9
 
 
+def test_vn_small_bulk_viscosity_claims():
+    """Section 4.2 on Table 3 (sigma_e, sigma_nu ~ 1e-3 .. 1e-6): the
+    original free rates (Lallemand-Luo s_eps, s_q) grow for almost every
+    wave direction, and grow faster as the bulk viscosity shrinks (group B
+    against group A); the optimized rates are stable without a mean flow.
+    (With the mean flow U = V = 0.1 of the paper's figures the optimized
+    sets keep a weakly growing mode at k ~ 2 near the axes, max |lambda|
+    1.008 for group A, far below the original rates' 1.04.)"""
+    ks = np.linspace(0.05, math.pi, 48)
+    ths = np.linspace(0.0, 2 * math.pi, 36, endpoint=False)
+    K, T = np.meshgrid(ks, ths)
+
+    def rates(t, original):
+        d = {k_: 1.0 / (t["sigma_" + k_[2:]] + 0.5) for k_ in ("s_e", "s_eps", "s_q", "s_nu")}
+        if original:
+            d.update(s_eps=inp.LL["s_eps"], s_q=inp.LL["s_q"])
+        return inp.s_paper(d)
+
+    def growth(t, original, U, V):
+        lam = vn.eigs(K * np.cos(T), K * np.sin(T), U, V, rates(t, original))
+        return np.max(np.abs(lam), axis=-1)  # (direction, k)
+
+    for U, V in ((0.0, 0.0), (0.1, 0.0), (0.1, 0.1)):
+        gA = growth(inp.TABLE3["A"], True, U, V)
+        gB = growth(inp.TABLE3["B"], True, U, V)
+        assert np.mean(gA.max(axis=1) > 1.0 + 1e-9) > 0.85  # all but the axes
+        assert gB.max() > gA.max() > 1.009
+        oA = growth(inp.TABLE3["A"], False, U, V)
+        assert oA.max() < 1.0 + 0.25 * (gA.max() - 1.0)
+    for g in ("A", "B"):
+        assert growth(inp.TABLE3[g], False, 0.0, 0.0).max() < 1.0 + 1e-12
+
+
 @pytest.mark.parametrize("U,name", [(0.0, "LL"), (0.1, "OPT"), (0.0, "OPT-Z")])
 def test_step_matches_linear_propagation(U, name):
     """At amplitude 1e-7 the nonlinear oracle equals the exact linear
