@@ -164,3 +164,20 @@ def test_oracle_minimizer_reproduces_table3_group_a():
     assert r["sigma_eps"] == pytest.approx(t["sigma_eps"], rel=1e-5)
     assert r["sigma_q"] == pytest.approx(t["sigma_q"], rel=1e-5)
     assert v == pytest.approx(14.453655614637361, rel=2e-9)
+
+
+def test_dispersion_along_the_axes_is_independent_of_the_free_rates():
+    """Section 4.2: along the axes the optimized and the original schemes
+    have the same dispersion.  In B_5 the dispersive coefficients (odd
+    powers of dt k: dt^0, dt^2, dt^4) do not depend on sigma_eps, sigma_q at
+    theta = 0, pi/2, pi, 3 pi/2, while off the axes dt^4 does (the cross
+    derivatives carry the difference)."""
+    opt = md.s_paper_from_sigmas(0.0025, 0.0, 105.468091254867, 0.0025)
+    orig = md.s_paper_from_sigmas(0.0025, 1 / 1.54 - 0.5, 1 / 1.9 - 0.5, 0.0025)
+    axes = np.array([0.0, np.pi / 2, np.pi, 3 * np.pi / 2])
+    a, b = md.bn_coeffs(axes, 0.0, 0.0, opt, 5), md.bn_coeffs(axes, 0.0, 0.0, orig, 5)
+    for l in (0, 2, 4):
+        assert np.max(np.abs(a[:, l] - b[:, l])) <= 1e-12
+    off = np.array([np.pi / 6, np.pi / 4, 2 * np.pi / 3])
+    a, b = md.bn_coeffs(off, 0.0, 0.0, opt, 5), md.bn_coeffs(off, 0.0, 0.0, orig, 5)
+    assert np.min(np.max(np.abs(a[:, 4] - b[:, 4]), axis=(1, 2))) > 1e-3
