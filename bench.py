@@ -174,6 +174,9 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
+
+
 def traffic_record(kernel):
     """DRAM bytes per lattice update from the committed ncu summary, or None
     when the kernel sources changed since it was captured."""
@@ -362,7 +365,13 @@ def bench_batched(args, L, torch, rank, ws):
                 "kernel": "k_step_batch<float> (launch variant %d)" % variant,
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": BYTES_PER_LU["f32"] * nodes,
-                "avg_launch_ms": round(launch_ms, 4)}
+                "avg_launch_ms": round(launch_ms, 4),
+                # against GB300's nominal 7.9 TB/s HBM3e, and the DRAM bytes
+                # ncu counted (traffic) over the same launch time
+                "nominal_peak": NOMINAL_HBM_GBS,
+                "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
+                "achieved_dram": (round(tr["dram_bytes_per_lu"] * nodes / (launch_ms * 1e-3) / 1e9, 1)
+                                  if tr else None)}
     line = {
         "metric": "MLUPS (lattice updates/s, millions), batched FP32-deviation D2Q9 MRT",
         "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
