@@ -8,16 +8,28 @@
 // every matrix of the two recursions (Eqs. R-A/R-B for the moment map
 // m = Phi W, Eqs. R-D/R-E for B) is a polynomial in dt stored as its
 // coefficients, and matrix powers of B are taken in that polynomial ring,
-// truncated at dt^(n-1).  The scheme's operators A_l = (1/l!) M
-// diag((-i v.k)^l) M^-1 Psi are applied as M (d_l o (G X)) with G = M^-1 Psi,
-// never formed.
+// truncated at dt^(n-1).
+//
+// Real arithmetic.  The scheme's operators are A_l = (1/l!) M
+// diag((-i v.k)^l) M^-1 Psi = (-i)^l H_l with the real
+// H_l = M diag(t_l) M^-1 Psi, t_l,j = (v_j.k)^l / l!.  Psi is real, so by
+// induction over both recursions the dt^t coefficient of Phi_m is (-i)^t
+// times a real matrix, that of B_m is (-i)^(t+1) times a real matrix and
+// that of a power B_s^p is (-i)^(t+p) times a real matrix; the phases
+// cancel from every recursion step, which therefore runs on the real
+// factors alone, and come back only in the final norm (cross terms of
+// coefficients l, m carry Re (-i)^(l-m): zero for odd l - m).
+//
+// H_l = K_l D^-1 Psi with K_l = M diag(t_l) M^T (M^-1 = M^T D^-1,
+// D = diag(9, 6, 6, 36, 36, 12, 12, 4, 4)); K_l depends on the wave
+// direction only and is tabulated on the host per direction.
 //
 // One warp per quadrature point (theta, flow direction, flow speed), its
-// polynomial matrices in shared memory and one lane per matrix entry.  The
-// wave-number integral over dt k in [0, pi] of ||M_eps||_F^2, M_eps =
-// sum_l (dt k)^(l+1) (b^l - b_exact^l), is taken in closed form per point;
-// the point sums are reduced in a fixed order per candidate, so results are
-// reproducible bit for bit.
+// polynomial matrices in shared memory; each lane owns some entries of
+// each matrix being formed.  The wave-number integral over dt k in [0, pi]
+// of ||M_eps||_F^2, M_eps = sum_l (dt k)^(l+1) (b^l - b_exact^l), is taken
+// in closed form per point; the point sums are reduced in a fixed order per
+// candidate, so results are reproducible bit for bit.
 #include <math.h>
 
 #include <algorithm>
@@ -33,27 +45,23 @@ constexpr int NMAX = 6;                       // largest truncation order
 constexpr int SLOTS = NMAX * (NMAX + 1) / 2;  // coefficients of orders 1..NMAX
 constexpr int WPB = 4;                        // warps (points) per block
 constexpr int MAX_SPEED = 32;
-
-struct cplx {
-  double re, im;
-};
-__device__ __forceinline__ cplx cx(double r, double i) { return cplx{r, i}; }
-__device__ __forceinline__ cplx operator+(cplx a, cplx b) { return cx(a.re + b.re, a.im + b.im); }
-__device__ __forceinline__ cplx operator-(cplx a, cplx b) { return cx(a.re - b.re, a.im - b.im); }
-__device__ __forceinline__ cplx operator*(cplx a, cplx b) {
-  return cx(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
-}
-__device__ __forceinline__ cplx operator*(double s, cplx a) { return cx(s * a.re, s * a.im); }
+constexpr int MAX_THETA = 4 * NMAX + 4;
+constexpr int MAX_DIR = 6 * NMAX;
+// the point table of one evaluation (device, read by every warp): wave
+// directions, flow directions, flow speeds and weights, pi^p / p
+constexpr int T_CTH = 0, T_STH = T_CTH + MAX_THETA, T_CPH = T_STH + MAX_THETA,
+              T_SPH = T_CPH + MAX_DIR, T_SU = T_SPH + MAX_DIR, T_WU = T_SU + MAX_SPEED,
+              T_KINT = T_WU + MAX_SPEED, T_SIZE = T_KINT + 2 * NMAX + 2;
 
 // D2Q9 velocities (the order of the step kernels) and the Lallemand-Luo
 // moment matrix in the paper's row order with its row norms
-__device__ __forceinline__ int vx(int j) {
+__host__ __device__ __forceinline__ int vx(int j) {
   return j == 1 || j == 5 || j == 8 ? 1 : (j == 3 || j == 6 || j == 7 ? -1 : 0);
 }
-__device__ __forceinline__ int vy(int j) {
+__host__ __device__ __forceinline__ int vy(int j) {
   return j == 2 || j == 5 || j == 6 ? 1 : (j == 4 || j == 7 || j == 8 ? -1 : 0);
 }
-__device__ __forceinline__ int mm(int k, int j) {
+__host__ __device__ __forceinline__ int mm(int k, int j) {
   const int c2 = vx(j) * vx(j) + vy(j) * vy(j);
   switch (k) {
     case 0: return 1;
@@ -67,41 +75,35 @@ __device__ __forceinline__ int mm(int k, int j) {
     default: return vx(j) * vy(j);
   }
 }
-__device__ __forceinline__ double dnorm(int k) {
-  return k == 0 ? 9.0 : (k <= 2 ? 6.0 : (k <= 4 ? 36.0 : (k <= 6 ? 12.0 : 4.0)));
-}
-
-struct Rates {
-  double s[9];  // paper order; s[0..2] unused
-};
-
-// the printed Psi of section 2.3 about rho = 1, j = (U, V)
-__device__ double psi(int r, int c, double U, double V, const Rates &R) {
-  const double se = R.s[3], seps = R.s[4], sq = R.s[5], snu = R.s[7];
-  const double u2 = U * U + V * V;
-  if (r == c) return r < 3 ? 1.0 : 1.0 - R.s[r];
-  switch (r) {
-    case 3: return c == 0 ? (-2 * se - 3 * u2 * se) : c == 1 ? 6 * U * se : c == 2 ? 6 * V * se : 0.0;
-    case 4: return c == 0 ? (seps + 3 * u2 * seps) : c == 1 ? -6 * U * seps : c == 2 ? -6 * V * seps : 0.0;
-    case 5: return c == 1 ? -sq : 0.0;
-    case 6: return c == 2 ? -sq : 0.0;
-    case 7: return c == 0 ? -(U * U - V * V) * snu : c == 1 ? 2 * U * snu : c == 2 ? -2 * V * snu : 0.0;
-    case 8: return c == 0 ? -U * V * snu : c == 1 ? V * snu : c == 2 ? U * snu : 0.0;
-    default: return 0.0;
-  }
+// 1 / D_kk
+__host__ __device__ __forceinline__ double rnorm(int k) {
+  return k == 0 ? 1.0 / 9.0
+                : (k <= 2 ? 1.0 / 6.0 : (k <= 4 ? 1.0 / 36.0 : (k <= 6 ? 1.0 / 12.0 : 1.0 / 4.0)));
 }
 
 __device__ __forceinline__ int slot(int m, int d) { return m * (m - 1) / 2 + d; }
 
+// B_s^p for p >= 2 (degrees 0..s-1) is kept for s = 1..NMAX-1 and
+// p = 2..NMAX-s+1: block index of its degree 0 (blocks of 3 x 3)
+constexpr int PW_BLOCKS = 35;  // sum over s of (NMAX - s) s
+__device__ __forceinline__ int pw_off(int s, int p) {
+  int o = 0;
+  for (int q = 1; q < s; ++q) o += (NMAX - q) * q;
+  return o + (p - 2) * s;
+}
+
+// 1 / l!, l = 0..NMAX+1
+__constant__ double c_rfact[NMAX + 2] = {1.0,        1.0,         1.0 / 2.0,   1.0 / 6.0,
+                                         1.0 / 24.0, 1.0 / 120.0, 1.0 / 720.0, 1.0 / 5040.0};
+
+// real factors of the polynomial matrices of one point
 struct WarpMem {
-  double G[81];          // M^-1 Psi
-  cplx d[NMAX + 1][9];   // d_l,j = (-i v_j.k)^l / l!
-  cplx phi[SLOTS][27];   // Phi_m, 9 x 3, coefficient d at slot(m, d)
-  cplx B[SLOTS][9];      // B_m, 3 x 3
-  cplx Y[27];            // G X
-  cplx P[NMAX][9];       // powers of B
-  cplx P2[NMAX][9];
-  cplx T[27];            // rows 0..2 of A_l Phi (scratch)
+  double H[NMAX][81];       // H_l, l = 1..n (row-major)
+  double psi0[18];          // Psi, rows 3..8, columns 0..2
+  double q[18];             // the same divided by D_kk
+  double phi[SLOTS][18];    // Phi_m, rows 3..8 (rows 0..2: the identity at degree 0, zero above)
+  double B[SLOTS][9];       // B_m, 3 x 3
+  double pw[PW_BLOCKS][9];  // powers of B_s
   double part[9];
 };
 
@@ -112,86 +114,83 @@ struct CostSpec {
   int reference;  // 0 convection + dissipation, 1 convection, 2 convection + shear
   int n_theta, n_dir, n_speed;
   double u0;
+  double w_theta, w_dir;  // quadrature weights of the wave and flow directions
+  // host copies of the point table
   double su[MAX_SPEED], wu[MAX_SPEED];  // speed nodes and weights
+  double kint[2 * NMAX + 2];            // pi^p / p: integral of K^(p-1) over [0, pi]
+  double cth[MAX_THETA], sth[MAX_THETA];  // wave directions
+  double cph[MAX_DIR], sph[MAX_DIR];      // flow directions
 };
 
-// out (rows lo..hi-1 of the 9 x 3 result, others untouched) += coef * A_l X
-__device__ void apply_A(WarpMem &w, int l, const cplx *X, cplx *out, int lo, int hi, double coef,
-                        int lane) {
-  if (lane < 27) {
-    const int r = lane / 3, c = lane % 3;
-    cplx y = cx(0, 0);
+// real factor of row r of H_l times column c of the degree-a coefficient of
+// a Phi (X: its rows 3..8)
+__device__ __forceinline__ double hx(const double *Hl, int r, const double *X, int a, int c) {
+  double z = a == 0 ? Hl[r * 9 + c] : 0.0;
 #pragma unroll
-    for (int j = 0; j < 9; ++j) y = y + w.G[r * 9 + j] * X[j * 3 + c];
-    w.Y[lane] = w.d[l][r] * y;
-  }
-  __syncwarp();
-  if (lane < 27) {
-    const int r = lane / 3, c = lane % 3;
-    if (r >= lo && r < hi) {
-      cplx z = cx(0, 0);
-#pragma unroll
-      for (int j = 0; j < 9; ++j) z = z + (double)mm(r, j) * w.Y[j * 3 + c];
-      out[lane] = out[lane] + coef * z;
-    }
-  }
-  __syncwarp();
+  for (int j = 3; j < 9; ++j) z += Hl[r * 9 + j] * X[(j - 3) * 3 + c];
+  return z;
 }
 
-// P (3 x 3 polynomial, degrees 0..maxdeg) = B_m^p truncated
-__device__ void bpow(WarpMem &w, int m, int p, int maxdeg, int lane) {
-  for (int d = 0; d <= maxdeg; ++d)
-    if (lane < 9) w.P[d][lane] = d < m ? w.B[slot(m, d)][lane] : cx(0, 0);
-  __syncwarp();
-  for (int q = 1; q < p; ++q) {
-    if (lane < 9) {
-      const int r = lane / 3, c = lane % 3;
-      for (int d = 0; d <= maxdeg; ++d) {
-        cplx acc = cx(0, 0);
-        for (int a = 0; a <= d; ++a) {
-          const int b = d - a;
-          if (b >= m) continue;
-#pragma unroll
-          for (int k = 0; k < 3; ++k) acc = acc + w.P[a][r * 3 + k] * w.B[slot(m, b)][k * 3 + c];
-        }
-        w.P2[d][lane] = acc;
-      }
-    }
-    __syncwarp();
-    for (int d = 0; d <= maxdeg; ++d)
-      if (lane < 9) w.P[d][lane] = w.P2[d][lane];
-    __syncwarp();
-  }
+// B_s^p, coefficient of degree d
+__device__ __forceinline__ const double *bpow(const WarpMem &w, int s, int p, int d) {
+  return p == 1 ? w.B[slot(s, d)] : w.pw[pw_off(s, p) + d];
 }
 
-// exact coefficients (convection b_ex^0, dissipation b_ex^1) at |k| = 1
-__device__ cplx exact_entry(int l, int e, double kx, double ky, double U, double V,
-                            const CostSpec &cs, double sig_e, double sig_nu) {
+// 1 / s_r = sigma_r + 1/2 of a non-conserved row r (sigma_e, sigma_eps,
+// sigma_q, sigma_nu)
+__device__ __forceinline__ double inv_rate(int r, const double *sg) {
+  return (r == 3 ? sg[0] : r == 4 ? sg[1] : r <= 6 ? sg[2] : sg[3]) + 0.5;
+}
+__device__ __forceinline__ double rate(int r, const double *s) {
+  return r == 3 ? s[0] : (r == 4 ? s[1] : (r <= 6 ? s[2] : s[3]));
+}
+
+// real factors (b_ex^l = (-i)^(l+1) e_l) of the exact coefficients at
+// |k| = 1: convection (l = 0) and dissipation (l = 1)
+__device__ __forceinline__ double exact_real(int l, int e, double kx, double ky, double U,
+                                             double V, const CostSpec &cs, double sig_e,
+                                             double sig_nu) {
   const int r = e / 3, c = e % 3;
-  if (l == 0) {
+  if (l == 0) {  // b_ex^0 = i v, so e_0 = -v
     double v = 0.0;
     if (r == 0) v = c == 1 ? -kx : (c == 2 ? -ky : 0.0);
     if (r == 1) v = c == 0 ? (-kx / 3 + kx * U * U + ky * U * V) : (c == 1 ? (-2 * kx * U - ky * V) : -ky * U);
     if (r == 2) v = c == 0 ? (-ky / 3 + ky * V * V + kx * U * V) : (c == 1 ? -kx * V : (-2 * ky * V - kx * U));
-    return cx(0.0, v);
+    return -v;
   }
-  if (l != 1 || cs.reference == 1) return cx(0, 0);
+  if (l != 1 || cs.reference == 1) return 0.0;
+  // b_ex^1 = x real, so e_1 = -x
   const double se = cs.reference == 2 ? 0.0 : sig_e;
-  double v = 0.0;
-  if (r == 1 && c == 1) v = -(kx * kx * se + (kx * kx + ky * ky) * sig_nu) / 3;
-  if ((r == 1 && c == 2) || (r == 2 && c == 1)) v = -kx * ky * se / 3;
-  if (r == 2 && c == 2) v = -(ky * ky * se + (kx * kx + ky * ky) * sig_nu) / 3;
-  return cx(v, 0.0);
+  double x = 0.0;
+  if (r == 1 && c == 1) x = -(kx * kx * se + (kx * kx + ky * ky) * sig_nu) / 3;
+  if ((r == 1 && c == 2) || (r == 2 && c == 1)) x = -kx * ky * se / 3;
+  if (r == 2 && c == 2) x = -(ky * ky * se + (kx * kx + ky * ky) * sig_nu) / 3;
+  return -x;
 }
 
+// The recursions on the real factors, written per output entry.  With
+// s = m - l and d = t - l, the dt^t factor of Phi_m (t >= 1, non-conserved
+// rows r) is
+//   (1/s_r) sum_{l=1..t} [ -(1/l!) (Phi_s B_s^l)_d + H_l Phi_s,d ]_rc
+// (degree 0: Psi_rc / s_r), and that of B_m is
+//   - sum_{l=1..min(t, m-1)} (1/(l+1)!) (B_s^(l+1))_d
+//   + sum_{l=1..min(m, t+1)} rows 0..2 of H_l Phi_{m+1-l, t-l+1}
+// -- Eqs. R-A/R-B and R-D/R-E with every product truncated at dt^(m-1).
+// No two lanes write one entry, and the powers B_m^p needed later are
+// formed once, right after B_m.  Work items run heaviest first (highest
+// degree t), so that each round of 32 lanes holds items of similar cost.
+//
+// tab: the point table (T_* offsets) followed by, per candidate, sigma_e,
+// sigma_eps, sigma_q, sigma_nu and the rates s = 1 / (sigma + 1/2) in that
+// order; ktab: K_l per wave direction, [n_theta][NMAX][81].
 __global__ void __launch_bounds__(WPB * 32)
-k_opt_points(CostSpec cs, const double *__restrict__ sigmas, long long npoints,
-             double *__restrict__ partial) {
+k_opt_points(CostSpec cs, const double *__restrict__ tab, const double *__restrict__ ktab,
+             long long npoints, double *__restrict__ partial) {
   extern __shared__ unsigned char smem_raw[];
   WarpMem &w = reinterpret_cast<WarpMem *>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const long long p = (long long)blockIdx.x * WPB + (threadIdx.x >> 5);
-  const int cand = blockIdx.y;
+  const int ci = blockIdx.y;
   if (p >= npoints) return;  // warp-uniform
   const int n = cs.order;
 
@@ -200,132 +199,115 @@ k_opt_points(CostSpec cs, const double *__restrict__ sigmas, long long npoints,
   const long long q = p / cs.n_theta;
   const int id = (int)(q % cs.n_dir);
   const int iu = (int)(q / cs.n_dir);
-  const double th = 2.0 * M_PI * it / cs.n_theta;
-  const double kx = cos(th), ky = sin(th);
-  double U = 0.0, V = 0.0, weight = 2.0 * M_PI / cs.n_theta;
+  const double kx = tab[T_CTH + it], ky = tab[T_STH + it];
+  double U = 0.0, V = 0.0, weight = cs.w_theta;
   if (cs.kind == 1) {
-    const double ph = 2.0 * M_PI * id / cs.n_dir;
-    U = cs.su[iu] * cos(ph);
-    V = cs.su[iu] * sin(ph);
-    weight *= 2.0 * M_PI / cs.n_dir * cs.wu[iu];
+    U = tab[T_SU + iu] * tab[T_CPH + id];
+    V = tab[T_SU + iu] * tab[T_SPH + id];
+    weight *= cs.w_dir * tab[T_WU + iu];
   }
-  const double *sg = sigmas + 4 * (long long)cand;  // sigma_e, sigma_eps, sigma_q, sigma_nu
-  Rates R;
-  R.s[0] = R.s[1] = R.s[2] = 0.0;
-  R.s[3] = 1.0 / (sg[0] + 0.5);
-  R.s[4] = 1.0 / (sg[1] + 0.5);
-  R.s[5] = R.s[6] = 1.0 / (sg[2] + 0.5);
-  R.s[7] = R.s[8] = 1.0 / (sg[3] + 0.5);
+  const double *sg = tab + T_SIZE + 8 * (long long)ci;  // sigmas
+  const double *rs = sg + 4;                    // rates
 
-  for (int e = lane; e < 81; e += 32) {
-    const int r = e / 9, c = e % 9;
-    double g = 0.0;
-    for (int k = 0; k < 9; ++k) g += (double)mm(k, r) / dnorm(k) * psi(k, c, U, V, R);
-    w.G[e] = g;
-  }
-  if (lane < 9) {
-    const double vk = vx(lane) * kx + vy(lane) * ky;
-    cplx pw = cx(1.0, 0.0);
-    double fact = 1.0;
-    w.d[0][lane] = pw;
-    for (int l = 1; l <= n; ++l) {
-      pw = pw * cx(0.0, -vk);
-      fact *= l;
-      w.d[l][lane] = (1.0 / fact) * pw;
+  // Psi (section 2.3, about rho = 1, j = (U, V)), rows 3..8 and columns
+  // 0..2: s_r times the derivative of m^eq_r by (rho, jx, jy)
+  if (lane < 18) {
+    const int r = 3 + lane / 3, c = lane % 3;
+    const double u2 = U * U + V * V;
+    double j;
+    switch (r) {
+      case 3: j = c == 0 ? -2.0 - 3.0 * u2 : (c == 1 ? 6.0 * U : 6.0 * V); break;
+      case 4: j = c == 0 ? 1.0 + 3.0 * u2 : (c == 1 ? -6.0 * U : -6.0 * V); break;
+      case 5: j = c == 1 ? -1.0 : 0.0; break;
+      case 6: j = c == 2 ? -1.0 : 0.0; break;
+      case 7: j = c == 0 ? -(U * U - V * V) : (c == 1 ? 2.0 * U : -2.0 * V); break;
+      default: j = c == 0 ? -U * V : (c == 1 ? V : U); break;
     }
+    const double ps = rate(r, rs) * j;
+    w.psi0[lane] = ps;
+    w.q[lane] = ps * rnorm(r);
   }
-  // Phi_1: identity on the conserved rows, Psi_ic / s_i below
-  if (lane < 27) {
-    const int r = lane / 3, c = lane % 3;
-    w.phi[slot(1, 0)][lane] = r < 3 ? cx(r == c ? 1.0 : 0.0, 0.0) : cx(psi(r, c, U, V, R) / R.s[r], 0.0);
-  }
-  if (lane < 27) w.T[lane] = cx(0, 0);
   __syncwarp();
-  // B_1 = rows 0..2 of A_1 Phi_1 (entries 0..8 of the 9 x 3 product)
-  apply_A(w, 1, w.phi[slot(1, 0)], w.T, 0, 3, 1.0, lane);
-  if (lane < 9) w.B[slot(1, 0)][lane] = w.T[lane];
-  __syncwarp();
-
-  for (int m = 2; m <= n; ++m) {
-    const int deg = m - 1;
-    // Phi_m accumulated in its slots: degree 0 = Psi (columns 0..2)
-    for (int d = 0; d < m; ++d)
-      if (lane < 27) {
-        const int r = lane / 3, c = lane % 3;
-        w.phi[slot(m, d)][lane] = d == 0 ? cx(psi(r, c, U, V, R), 0.0) : cx(0, 0);
-      }
-    __syncwarp();
-    double fact = 1.0;
-    for (int l = 1; l < m; ++l) {
-      fact *= l;
-      const int md = deg - l;  // degrees kept in the shifted terms
-      bpow(w, m - l, l, md, lane);
-      // T = Phi_{m-l} B_{m-l}^l, degrees 0..md
-      if (lane < 27) {
-        const int r = lane / 3, c = lane % 3;
-        for (int d = 0; d <= md; ++d) {
-          cplx acc = cx(0, 0);
-          for (int a = 0; a <= d && a < m - l; ++a)
+  // H_l = K_l D^-1 Psi: columns 0..2 (identity + Psi's first columns),
+  // then columns 3..8 ((1 - s_c) / D_cc times column c of K_l)
+  const double *K = ktab + (long long)it * NMAX * 81;
+  for (int e = lane; e < 27 * n; e += 32) {
+    const int l = e / 27, r = (e % 27) / 3, c = e % 3;
+    const double *Kr = K + l * 81 + r * 9;
+    double h = Kr[c] * rnorm(c);
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-              acc = acc + w.phi[slot(m - l, a)][r * 3 + k] * w.P[d - a][k * 3 + c];
-          w.phi[slot(m, d + l)][lane] = w.phi[slot(m, d + l)][lane] - (1.0 / fact) * acc;
+    for (int k = 3; k < 9; ++k) h += Kr[k] * w.q[(k - 3) * 3 + c];
+    w.H[l][r * 9 + c] = h;
+  }
+  for (int e = lane; e < 54 * n; e += 32) {
+    const int l = e / 54, r = (e % 54) / 6, c = 3 + e % 6;
+    w.H[l][r * 9 + c] = K[l * 81 + r * 9 + c] * ((1.0 - rate(c, rs)) * rnorm(c));
+  }
+  __syncwarp();
+
+  for (int m = 1; m <= n; ++m) {
+    // Phi_m, rows 3..8
+    for (int e = lane; e < 18 * m; e += 32) {
+      const int t = m - 1 - e / 18, rc = e % 18, r = 3 + rc / 3, c = rc % 3;
+      double v = t == 0 ? w.psi0[rc] : 0.0;
+      for (int l = 1; l <= t; ++l) {
+        const int s = m - l, d = t - l;
+        double acc = 0.0;
+        for (int a = 0; a <= d; ++a) {
+          const double *X = w.phi[slot(s, a)];
+          const double *Pp = bpow(w, s, l, d - a);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) acc += X[rc - c + k] * Pp[k * 3 + c];
         }
+        v -= c_rfact[l] * acc;
+        v += hx(w.H[l - 1], r, w.phi[slot(s, d)], d, c);
       }
-      __syncwarp();
-      for (int a = 0; a < m - l && a + l <= deg; ++a)
-        apply_A(w, l, w.phi[slot(m - l, a)], w.phi[slot(m, a + l)], 3, 9, 1.0, lane);
+      w.phi[slot(m, t)][rc] = inv_rate(r, sg) * v;
     }
-    // rows 3..8 divided by s_i; rows 0..2 the identity
-    for (int d = 0; d < m; ++d)
-      if (lane < 27) {
-        const int r = lane / 3, c = lane % 3;
-        cplx v = w.phi[slot(m, d)][lane];
-        if (r < 3) v = cx(d == 0 && r == c ? 1.0 : 0.0, 0.0);
-        else v = (1.0 / R.s[r]) * v;
-        w.phi[slot(m, d)][lane] = v;
-      }
     __syncwarp();
     // B_m
-    for (int d = 0; d < m; ++d)
-      if (lane < 9) w.B[slot(m, d)][lane] = cx(0, 0);
-    __syncwarp();
-    fact = 1.0;
-    for (int l = 1; l < m; ++l) {
-      fact *= (l + 1);
-      const int md = deg - l;
-      bpow(w, m - l, l + 1, md, lane);
-      if (lane < 9)
-        for (int d = 0; d <= md; ++d)
-          w.B[slot(m, d + l)][lane] = w.B[slot(m, d + l)][lane] - (1.0 / fact) * w.P[d][lane];
-      __syncwarp();
+    for (int e = lane; e < 9 * m; e += 32) {
+      const int t = m - 1 - e / 9, rc = e % 9, r = rc / 3, c = rc % 3;
+      double v = 0.0;
+      for (int l = 1; l <= t && l < m; ++l) v -= c_rfact[l + 1] * bpow(w, m - l, l + 1, t - l)[rc];
+      for (int l = 1; l <= m && l <= t + 1; ++l)
+        v += hx(w.H[l - 1], r, w.phi[slot(m + 1 - l, t - l + 1)], t - l + 1, c);
+      w.B[slot(m, t)][rc] = v;
     }
-    for (int l = 1; l <= m; ++l) {
-      const int src = m + 1 - l;
-      for (int a = 0; a < src && a + l - 1 <= deg; ++a) {
-        if (lane < 27) w.T[lane] = cx(0, 0);
-        __syncwarp();
-        apply_A(w, l, w.phi[slot(src, a)], w.T, 0, 3, 1.0, lane);
-        if (lane < 9) w.B[slot(m, a + l - 1)][lane] = w.B[slot(m, a + l - 1)][lane] + w.T[lane];
-        __syncwarp();
+    __syncwarp();
+    // B_m^p, p = 2..n-m+1, truncated at degree m-1
+    for (int pp = 2; pp <= n - m + 1; ++pp) {
+      for (int e = lane; e < 9 * m; e += 32) {
+        const int d = m - 1 - e / 9, rc = e % 9, r = rc / 3, c = rc % 3;
+        double acc = 0.0;
+        for (int a = 0; a <= d; ++a) {
+          const double *X = bpow(w, m, pp - 1, a);
+          const double *Bb = w.B[slot(m, d - a)];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) acc += X[r * 3 + k] * Bb[k * 3 + c];
+        }
+        w.pw[pw_off(m, pp) + d][rc] = acc;
       }
+      __syncwarp();
     }
   }
 
-  // closed-form K integral of ||sum_l K^(l+1) E^l||^2 over [0, pi]
+  // closed-form K integral of ||sum_l K^(l+1) E^l||^2 over [0, pi]:
+  // E^l = (-i)^(l+1) (b_l - e_l) on the real factors, so the (l, m) term is
+  // Re (-i)^(l-m) (b_l - e_l).(b_m - e_m) pi^(l+m+3) / (l+m+3); the factors
+  // E_l are kept where the powers were
+  double(*E)[9] = w.pw;
+  if (lane < 9)
+    for (int l = 0; l < n; ++l)
+      E[l][lane] = w.B[slot(n, l)][lane] - exact_real(l, lane, kx, ky, U, V, cs, sg[0], sg[3]);
   if (lane < 9) {
     double acc = 0.0;
     for (int l = 0; l < n; ++l) {
       const bool odd_l = ((l + 1) & 1) != 0;
       if ((cs.part == 1 && !odd_l) || (cs.part == 2 && odd_l)) continue;
-      const cplx El = w.B[slot(n, l)][lane] - exact_entry(l, lane, kx, ky, U, V, cs, sg[0], sg[3]);
-      for (int mq = 0; mq < n; ++mq) {
-        const bool odd_m = ((mq + 1) & 1) != 0;
-        if ((cs.part == 1 && !odd_m) || (cs.part == 2 && odd_m)) continue;
-        const cplx Em =
-            w.B[slot(n, mq)][lane] - exact_entry(mq, lane, kx, ky, U, V, cs, sg[0], sg[3]);
-        const int pw = l + mq + 3;
-        acc += (El.re * Em.re + El.im * Em.im) * pow(M_PI, pw) / pw;
+      for (int mq = l & 1; mq < n; mq += 2) {  // odd l - mq: Re (-i)^(l-mq) = 0
+        const double sgn = ((l - mq) & 3) == 0 ? 1.0 : -1.0;
+        acc += sgn * (E[l][lane] * E[mq][lane]) * tab[T_KINT + l + mq + 3];
       }
     }
     w.part[lane] = acc;
@@ -334,7 +316,7 @@ k_opt_points(CostSpec cs, const double *__restrict__ sigmas, long long npoints,
   if (lane == 0) {
     double v = 0.0;
     for (int e = 0; e < 9; ++e) v += w.part[e];
-    partial[(long long)cand * npoints + p] = v * weight;
+    partial[(long long)ci * npoints + p] = v * weight;
   }
 }
 
@@ -400,15 +382,31 @@ int make_spec(const lbm_cost_spec *in, CostSpec *cs) {
   // exact for the integrands of orders <= NMAX (trigonometric / polynomial
   // degrees grow with the order)
   cs->n_theta = 4 * cs->order + 4;
+  for (int p = 0; p < 2 * NMAX + 2; ++p) cs->kint[p] = p ? pow(M_PI, p) / p : 0.0;
+  for (int i = 0; i < cs->n_theta; ++i) {
+    const double th = 2.0 * M_PI * i / cs->n_theta;
+    cs->cth[i] = cos(th);
+    cs->sth[i] = sin(th);
+  }
+  cs->w_theta = 2.0 * M_PI / cs->n_theta;
   if (cs->kind == LBM_COST_F) {
     cs->n_dir = 1;
     cs->n_speed = 1;
+    cs->cph[0] = 1.0;
+    cs->sph[0] = 0.0;
+    cs->w_dir = 1.0;
     cs->su[0] = 0.0;
     cs->wu[0] = 1.0;
   } else {
     if (!(cs->u0 >= 0.0) || !std::isfinite(cs->u0)) return LBM_EINVAL;
     cs->n_dir = 6 * cs->order;
     cs->n_speed = 2 * cs->order + 2;
+    for (int i = 0; i < cs->n_dir; ++i) {
+      const double ph = 2.0 * M_PI * i / cs->n_dir;
+      cs->cph[i] = cos(ph);
+      cs->sph[i] = sin(ph);
+    }
+    cs->w_dir = 2.0 * M_PI / cs->n_dir;
     if (in->fixed_speed) {
       cs->n_speed = 1;
       cs->su[0] = cs->u0;
@@ -425,23 +423,51 @@ int make_spec(const lbm_cost_spec *in, CostSpec *cs) {
   return LBM_OK;
 }
 
+// K_l = M diag(t_l) M^T, t_l,j = (v_j.k)^l / l!, for every wave direction
+// of the quadrature and l = 1..order: [n_theta][NMAX][81]
+std::vector<double> k_tables(const CostSpec &cs) {
+  std::vector<double> out((size_t)cs.n_theta * NMAX * 81, 0.0);
+  for (int it = 0; it < cs.n_theta; ++it) {
+    double vk[9], t[9];
+    for (int j = 0; j < 9; ++j) {
+      vk[j] = vx(j) * cs.cth[it] + vy(j) * cs.sth[it];
+      t[j] = 1.0;
+    }
+    double fact = 1.0;
+    for (int l = 1; l <= cs.order; ++l) {
+      fact *= l;
+      for (int j = 0; j < 9; ++j) t[j] *= vk[j];
+      double *K = out.data() + ((size_t)it * NMAX + (l - 1)) * 81;
+      for (int r = 0; r < 9; ++r)
+        for (int c = 0; c < 9; ++c) {
+          double s = 0.0;
+          for (int j = 0; j < 9; ++j) s += (double)(mm(r, j) * mm(c, j)) * t[j];
+          K[r * 9 + c] = s / fact;
+        }
+    }
+  }
+  return out;
+}
+
 // device buffers of the cost evaluations, grown on demand and reused by the
 // many small evaluations of a minimization
 struct Workspace {
-  double *sig = nullptr, *part = nullptr, *out = nullptr;
+  double *tab = nullptr, *part = nullptr, *out = nullptr, *ktab = nullptr;
   size_t cap_n = 0, cap_part = 0;
+  int k_order = -1, k_theta = -1;  // what ktab holds
   ~Workspace() {
-    lbm::dev_free(sig);
+    lbm::dev_free(tab);
     lbm::dev_free(part);
     lbm::dev_free(out);
+    lbm::dev_free(ktab);
   }
   bool ensure(size_t n, size_t npart) {
     if (n > cap_n) {
-      lbm::dev_free(sig);
+      lbm::dev_free(tab);
       lbm::dev_free(out);
-      sig = (double *)lbm::dev_alloc(sizeof(double) * 4 * n);
+      tab = (double *)lbm::dev_alloc(sizeof(double) * (T_SIZE + 8 * n));
       out = (double *)lbm::dev_alloc(sizeof(double) * n);
-      cap_n = (sig && out) ? n : 0;
+      cap_n = (tab && out) ? n : 0;
       if (!cap_n) return false;
     }
     if (npart > cap_part) {
@@ -449,6 +475,10 @@ struct Workspace {
       part = (double *)lbm::dev_alloc(sizeof(double) * npart);
       cap_part = part ? npart : 0;
       if (!cap_part) return false;
+    }
+    if (!ktab) {
+      ktab = (double *)lbm::dev_alloc(sizeof(double) * MAX_THETA * NMAX * 81);
+      if (!ktab) return false;
     }
     return true;
   }
@@ -461,13 +491,36 @@ int eval_costs(Workspace &ws, const CostSpec &cs, int n, const double *sig_host,
     lbm::set_error("out of device memory for the cost evaluation");
     return LBM_ENOMEM;
   }
-  cudaError_t e = cudaMemcpy(ws.sig, sig_host, sizeof(double) * 4 * n, cudaMemcpyHostToDevice);
+  cudaError_t e = cudaSuccess;
+  if (ws.k_order != cs.order || ws.k_theta != cs.n_theta) {
+    const std::vector<double> kt = k_tables(cs);
+    e = cudaMemcpy(ws.ktab, kt.data(), sizeof(double) * kt.size(), cudaMemcpyHostToDevice);
+    ws.k_order = e == cudaSuccess ? cs.order : -1;
+    ws.k_theta = cs.n_theta;
+  }
+  // the point table, then per candidate the sigmas and the rates
+  // s = 1 / (sigma + 1/2)
+  std::vector<double> cd(T_SIZE + 8 * (size_t)n, 0.0);
+  std::copy(cs.cth, cs.cth + MAX_THETA, cd.begin() + T_CTH);
+  std::copy(cs.sth, cs.sth + MAX_THETA, cd.begin() + T_STH);
+  std::copy(cs.cph, cs.cph + MAX_DIR, cd.begin() + T_CPH);
+  std::copy(cs.sph, cs.sph + MAX_DIR, cd.begin() + T_SPH);
+  std::copy(cs.su, cs.su + MAX_SPEED, cd.begin() + T_SU);
+  std::copy(cs.wu, cs.wu + MAX_SPEED, cd.begin() + T_WU);
+  std::copy(cs.kint, cs.kint + 2 * NMAX + 2, cd.begin() + T_KINT);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < 4; ++k) {
+      cd[T_SIZE + 8 * (size_t)i + k] = sig_host[4 * (size_t)i + k];
+      cd[T_SIZE + 8 * (size_t)i + 4 + k] = 1.0 / (sig_host[4 * (size_t)i + k] + 0.5);
+    }
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ws.tab, cd.data(), sizeof(double) * cd.size(), cudaMemcpyHostToDevice);
   const size_t shm = sizeof(WarpMem) * WPB;
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_opt_points, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   if (e == cudaSuccess) {
     dim3 grid((unsigned)((npoints + WPB - 1) / WPB), (unsigned)n);
-    k_opt_points<<<grid, WPB * 32, shm>>>(cs, ws.sig, npoints, ws.part);
+    k_opt_points<<<grid, WPB * 32, shm>>>(cs, ws.tab, ws.ktab, npoints, ws.part);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
