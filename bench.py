@@ -65,6 +65,8 @@ def parse():
     p.add_argument("--max-nodes", type=int, default=0, help="server resident-node cap")
     p.add_argument("--size", type=int, default=8192, help="side of the large lattice")
     p.add_argument("--dtypes", default="f32,f16,bf16,f64", help="storage types (large)")
+    p.add_argument("--batch-dtype", default="f32", choices=["f32", "f16", "bf16"],
+                   help="storage type of the batched workload")
     p.add_argument("--batch-variant", type=int, default=-1,
                    help="pin the batched launch variant (default: tuned)")
     return p.parse_args()
@@ -275,7 +277,8 @@ def bench_batched(args, L, torch, rank, ws):
     dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream()
     specs = rank_specs(args, rank)
-    hs, fields = setup_batch(L, torch, specs, "f32", stream)
+    bdt = args.batch_dtype
+    hs, fields = setup_batch(L, torch, specs, bdt, stream)
     nodes = sum(s["nx"] * s["ny"] for s in specs)
     b = L.lbm_batch_create(hs)
     if args.batch_variant >= 0:
@@ -355,16 +358,18 @@ def bench_batched(args, L, torch, rank, ws):
         L.lbm_destroy(h)
 
     peak, peak_kind = peaks()
-    achieved = BYTES_PER_LU["f32"] * nodes / (launch_ms * 1e-3) / 1e9
-    tr = traffic_record("k_step_batch<float>")
+    kname = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16"}[bdt]
+    sname = {"f32": "FP32", "f16": "FP16", "bf16": "BF16"}[bdt]
+    achieved = BYTES_PER_LU[bdt] * nodes / (launch_ms * 1e-3) / 1e9
+    tr = traffic_record("k_step_batch<%s>" % kname)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
                 # ncu DRAM bytes per lattice update of a smaller capture of the
                 # same kernel, scaled to this launch's lattice updates
                 "traffic": (round(tr["dram_bytes_per_lu"] * nodes) if tr else None),
-                "kernel": "k_step_batch<float> (launch variant %d)" % variant,
+                "kernel": "k_step_batch<%s> (launch variant %d)" % (kname, variant),
                 "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": BYTES_PER_LU["f32"] * nodes,
+                "algorithmic_bytes_per_launch": BYTES_PER_LU[bdt] * nodes,
                 "avg_launch_ms": round(launch_ms, 4),
                 # against GB300's nominal 7.9 TB/s HBM3e, and the DRAM bytes
                 # ncu counted (traffic) over the same launch time
@@ -373,16 +378,18 @@ def bench_batched(args, L, torch, rank, ws):
                 "achieved_dram": (round(tr["dram_bytes_per_lu"] * nodes / (launch_ms * 1e-3) / 1e9, 1)
                                   if tr else None)}
     line = {
-        "metric": "MLUPS (lattice updates/s, millions), batched FP32-deviation D2Q9 MRT",
+        "metric": "MLUPS (lattice updates/s, millions), batched %s-deviation D2Q9 MRT" % sname,
         "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": bdt,
         "data": "synthetic (seeded Gaussian pulses, per-lattice relaxation rates)",
-        "config": {"workload": "batched-512-lattices-fp32dev-500-steps",
+        "config": {"workload": "batched-%d-lattices-%sdev-%d-steps" % (
+                       args.lattices, {"f32": "fp32", "f16": "fp16", "bf16": "bf16"}[bdt],
+                       lbm_steps),
                    "lattices_per_gpu": len(specs), "nodes_per_gpu": nodes,
-                   "lbm_steps_per_step": lbm_steps, "storage": "fp32 deviation",
+                   "lbm_steps_per_step": lbm_steps, "storage": "%s deviation" % sname.lower(),
                    "l2": "working set %.1f GB per time step > L2 (129 MB)" % (
-                       2 * 72 / 2 * nodes / 1e9),
+                       BYTES_PER_LU[bdt] * nodes / 1e9),
                    "parallelism": "independent lattices per GPU (weak scaling)"},
         "e2e": {"value": round(e2e_value, 1), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
