@@ -376,7 +376,9 @@ def bench_batched(args, L, torch, rank, ws):
                 "nominal_peak": NOMINAL_HBM_GBS,
                 "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                 "achieved_dram": (round(tr["dram_bytes_per_lu"] * nodes / (launch_ms * 1e-3) / 1e9, 1)
-                                  if tr else None)}
+                                  if tr else None),
+                "dram_frac_of_nominal": (round(tr["dram_bytes_per_lu"] * nodes / (launch_ms * 1e-3)
+                                               / 1e9 / NOMINAL_HBM_GBS, 4) if tr else None)}
     line = {
         "metric": "MLUPS (lattice updates/s, millions), batched %s-deviation D2Q9 MRT" % sname,
         "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
