@@ -27,7 +27,11 @@ static int failures = 0;
 template <int V>
 static void check_lattice(int nx, int ny, int esize) {
   const Geom g = make_geom(nx, ny, V, esize);
-  CHECK(g.pitch >= nx && (g.pitch * esize) % 128 == 0, "pitch %d nx %d", g.pitch, nx);
+  // rows start on 128-byte lines (4-byte elements) or 64-byte halves of
+  // lines (2-byte elements)
+  const int line = esize == 2 ? 64 : 128;
+  CHECK(g.pitch >= nx && (g.pitch * esize) % line == 0 && g.pitch - nx < line / esize + V,
+        "pitch %d nx %d", g.pitch, nx);
   CHECK(g.cpr * V == g.pitch && g.nchunks * V >= nx && (g.nchunks - 1) * V < nx,
         "chunks nx %d V %d", nx, V);
   CHECK(g.plane == g.pitch && g.rstride == 9LL * g.pitch, "layout");
@@ -43,8 +47,8 @@ static void check_lattice(int nx, int ny, int esize) {
       CHECK(p.y == y && p.x0 == xc * V, "position nx %d ny %d V %d c %lld", nx, ny, V, c);
       CHECK(p.first == (lane == 0 || xc == 0), "first nx %d V %d c %lld", nx, V, c);
       CHECK(p.last == (lane == 31 || xc + 1 == g.nchunks), "last nx %d V %d c %lld", nx, V, c);
-      // every task starts on a 128-byte line of its row
-      if (lane == 0) CHECK((xc * V * esize) % 128 == 0, "task alignment nx %d V %d", nx, V);
+      // every task starts on such a line of its row
+      if (lane == 0) CHECK((xc * V * esize) % line == 0, "task alignment nx %d V %d", nx, V);
       seen[(size_t)y * g.nchunks + xc]++;
     }
   for (size_t k = 0; k < seen.size(); ++k) CHECK(seen[k] == 1, "chunk %zu seen %d times", k, seen[k]);
