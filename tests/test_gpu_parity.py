@@ -174,9 +174,11 @@ def test_dev_plane_wave_config2(L, dtype, U, name):
 # ----------------------------------------------------- whole-path checks
 @pytest.mark.parametrize("dtype", ["f64", "f32", "f16"])
 def test_checkpoint_restore_is_exact(L, dtype):
-    """100 steps straight equal 50 steps, get, set, 50 steps (bit for bit;
-    for FP16 the restore keeps the storage scale because the largest
-    deviation is unchanged)."""
+    """100 steps straight equal 50 steps, get, set, 50 steps: bit for bit
+    for FP64 and FP32; FP16 re-chooses its storage scale from the snapshot's
+    largest deviation on restore, so there the two runs agree to the FP16
+    bar (2e-3 of the amplitude) and a snapshot restored and read back moves
+    by at most one FP16 rounding."""
     nx, ny = 40, 24
     r = inp.rates("OPT")
     fields = inp.gaussian_pulse(nx, ny, 1e-3, 4.0)
@@ -189,15 +191,22 @@ def test_checkpoint_restore_is_exact(L, dtype):
         L.lbm_init_field(g, *fields)
         L.lbm_step(g, 50)
         mid = L.lbm_get_populations(g)
-        if dtype == "f16":
-            pytest.skip("FP16 restore re-chooses the scale from the snapshot")
         L.lbm_set_populations(g, mid)
+        back = L.lbm_get_populations(g)
         L.lbm_step(g, 50)
         b = L.lbm_get_populations(g)
     finally:
         L.lbm_destroy(h)
         L.lbm_destroy(g)
-    assert np.array_equal(a, b)
+    if dtype == "f16":
+        err = np.max(np.abs(a - b)) / 1e-3
+        print("\nf16 restore: max|df| / A = %.2e, read-back exact: %s"
+              % (err, np.array_equal(back, mid)))
+        assert err <= 2e-3
+        assert np.max(np.abs(back - mid)) <= 1e-3 * 2.0 ** -11
+    else:
+        assert np.array_equal(back, mid)
+        assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
