@@ -519,7 +519,7 @@ def bench_vn(args, L, torch):
     return {"metric": "von Neumann eigenproblems (9x9 complex) per second",
             "value": round(gpu, 1), "unit": "problems/s", "higher_is_better": True,
             "config": {"workload": "vn-sweep-%d-cases" % n},
-            "note": "host arrays in and out, device allocation per call included",
+            "note": "host (pageable) arrays in and out per call, best of the timed calls",
             "cpu_baseline": {"value": round(cpu, 1), "unit": "problems/s", "cores": 1,
                              "kind": "oracle", "sample": "%d cases, numpy eigvals" % kx.size}}
 

@@ -245,7 +245,11 @@ const char *lbm_last_error(void);
  * lambda = exp(-i omega): damping per step -ln|lambda|, phase speed
  * -arg(lambda)/|k|.  *unconverged (may be NULL) counts eigenvalues whose QR
  * iteration reached its limit of 60 sweeps (returns LBM_ETIMEOUT then).
- * Synchronizes; allocates device memory for the call. */
+ * Synchronizes.  The cases go in up to 8 chunks on their own streams, so
+ * the host's packing and unpacking overlap the copies and the kernels;
+ * page-locked host and device staging sized for the largest call so far
+ * is kept for the life of the process, and concurrent calls are
+ * serialized. */
 int lbm_vn_eigs(int n, const double *kx, const double *ky, const double *U,
                 const double *V, const double *S, double *eig,
                 int *unconverged);

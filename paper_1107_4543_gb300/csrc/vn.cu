@@ -13,6 +13,10 @@
 // entries) with a bounded number of sweeps per eigenvalue.
 #include <math.h>
 
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -245,6 +249,87 @@ __global__ void k_vn_eigs(const VnCase *__restrict__ cases, int n, double *__res
 
 }  // namespace
 
+namespace {
+
+// Staging of lbm_vn_eigs, kept for the life of the process and grown to
+// the largest call: page-locked host copies of the cases and results,
+// their device copies, and one stream per chunk.  A call cuts its cases
+// into up to kVnChunks chunks; the host fills chunk j while chunk j-1 is
+// uploaded and solved, every chunk's kernel runs on its own stream (all of
+// them together fill the GPU: one thread's QR iteration is a long
+// dependent chain, so the kernel wants every case in flight at once), and
+// the host drains each chunk's eigenvalues as soon as they are back.
+constexpr int kVnChunks = 8;
+constexpr int kVnMinChunk = 4096;
+
+struct VnStage {
+  int device = -1;
+  long long cap = 0;
+  VnCase *h_in = nullptr, *d_in = nullptr;
+  double *h_out = nullptr, *d_out = nullptr;
+  int *d_fail = nullptr;
+  cudaStream_t st[kVnChunks] = {};
+  cudaEvent_t ev[kVnChunks] = {};
+};
+
+std::mutex g_vn_mu;
+VnStage g_vn;  // its CUDA objects are never released (none may be at process exit)
+
+void vn_release(VnStage &v) {
+  cudaFreeHost(v.h_in);
+  cudaFreeHost(v.h_out);
+  cudaFree(v.d_in);
+  cudaFree(v.d_out);
+  v.h_in = v.d_in = nullptr;
+  v.h_out = v.d_out = nullptr;
+  v.cap = 0;
+  cudaGetLastError();
+}
+
+cudaError_t vn_ready(VnStage &v, long long n) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (v.device != dev) {
+    if (v.device >= 0) {
+      // staging of another device: let it go (on that device)
+      cudaSetDevice(v.device);
+      vn_release(v);
+      cudaFree(v.d_fail);
+      v.d_fail = nullptr;
+      for (int k = 0; k < kVnChunks; ++k) {
+        cudaStreamDestroy(v.st[k]);
+        cudaEventDestroy(v.ev[k]);
+        v.st[k] = nullptr;
+        v.ev[k] = nullptr;
+      }
+      cudaSetDevice(dev);
+      cudaGetLastError();
+    }
+    v.device = -1;
+    for (int k = 0; k < kVnChunks; ++k) {
+      if ((e = cudaStreamCreateWithFlags(&v.st[k], cudaStreamNonBlocking)) != cudaSuccess) return e;
+      if ((e = cudaEventCreateWithFlags(&v.ev[k], cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+    if ((e = cudaMalloc(&v.d_fail, sizeof(int))) != cudaSuccess) return e;
+    v.device = dev;
+  }
+  if (n > v.cap) {
+    vn_release(v);
+    if ((e = cudaHostAlloc(&v.h_in, sizeof(VnCase) * n, cudaHostAllocDefault)) != cudaSuccess ||
+        (e = cudaHostAlloc(&v.h_out, sizeof(double) * 18 * n, cudaHostAllocDefault)) != cudaSuccess ||
+        (e = cudaMalloc(&v.d_in, sizeof(VnCase) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&v.d_out, sizeof(double) * 18 * n)) != cudaSuccess) {
+      vn_release(v);
+      return e;
+    }
+    v.cap = n;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
 extern "C" int lbm_vn_eigs(int n, const double *kx, const double *ky, const double *U,
                            const double *V, const double *S, double *eig, int *unconverged) {
   using namespace lbm;
@@ -255,32 +340,48 @@ extern "C" int lbm_vn_eigs(int n, const double *kx, const double *ky, const doub
   if (unconverged) *unconverged = 0;
   if (n == 0) return LBM_OK;
   const int ll_of_paper[9] = {0, 3, 5, 1, 2, 4, 6, 7, 8};
-  VnCase *h = new (std::nothrow) VnCase[n];
-  if (!h) return LBM_ENOMEM;
-  for (int c = 0; c < n; ++c) {
-    h[c].kx = kx[c];
-    h[c].ky = ky[c];
-    h[c].U = U[c];
-    h[c].V = V[c];
-    for (int k = 0; k < 9; ++k) h[c].s[k] = S[9 * c + ll_of_paper[k]];
+  std::lock_guard<std::mutex> lk(g_vn_mu);
+  VnStage &v = g_vn;
+  cudaError_t e = vn_ready(v, n);
+  const int nch = std::max(1, std::min(kVnChunks, n / kVnMinChunk));
+  auto lo = [&](int j) { return (int)((long long)n * j / nch); };
+  // zero the failure count before any chunk stream runs (the legacy
+  // stream of a plain memset does not order the non-blocking streams)
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.d_fail, 0, sizeof(int), v.st[0]);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(v.st[0]);
+  int launched = 0;
+  for (int j = 0; j < nch && e == cudaSuccess; ++j) {
+    const int c0 = lo(j), c1 = lo(j + 1), cnt = c1 - c0;
+    for (int c = c0; c < c1; ++c) {
+      VnCase &k = v.h_in[c];
+      k.kx = kx[c];
+      k.ky = ky[c];
+      k.U = U[c];
+      k.V = V[c];
+      for (int q = 0; q < 9; ++q) k.s[q] = S[9LL * c + ll_of_paper[q]];
+    }
+    e = cudaMemcpyAsync(v.d_in + c0, v.h_in + c0, sizeof(VnCase) * cnt, cudaMemcpyHostToDevice,
+                        v.st[j]);
+    if (e == cudaSuccess) {
+      k_vn_eigs<<<(cnt + 127) / 128, 128, 0, v.st[j]>>>(v.d_in + c0, cnt, v.d_out + 18LL * c0,
+                                                        v.d_fail);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(v.h_out + 18LL * c0, v.d_out + 18LL * c0, sizeof(double) * 18 * cnt,
+                          cudaMemcpyDeviceToHost, v.st[j]);
+    if (e == cudaSuccess) e = cudaEventRecord(v.ev[j], v.st[j]);
+    if (e == cudaSuccess) ++launched;
   }
-  VnCase *d_cases = (VnCase *)dev_alloc(sizeof(VnCase) * n);
-  double *d_out = (double *)dev_alloc(sizeof(double) * 18 * n);
-  int *d_fail = (int *)dev_alloc(sizeof(int));
-  cudaError_t e = (!d_cases || !d_out || !d_fail) ? cudaErrorMemoryAllocation : cudaSuccess;
-  if (e == cudaSuccess) e = cudaMemcpy(d_cases, h, sizeof(VnCase) * n, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(d_fail, 0, sizeof(int));
-  if (e == cudaSuccess) {
-    k_vn_eigs<<<(n + 127) / 128, 128>>>(d_cases, n, d_out, d_fail);
-    e = cudaGetLastError();
+  // drain each chunk as it lands (after an error: wait for what was queued)
+  for (int j = 0; j < launched; ++j) {
+    const cudaError_t w = cudaEventSynchronize(v.ev[j]);
+    if (e == cudaSuccess) e = w;
+    if (e == cudaSuccess)
+      memcpy(eig + 18LL * lo(j), v.h_out + 18LL * lo(j), sizeof(double) * 18 * (lo(j + 1) - lo(j)));
   }
   int fails = 0;
-  if (e == cudaSuccess) e = cudaMemcpy(eig, d_out, sizeof(double) * 18 * n, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemcpy(&fails, d_fail, sizeof(int), cudaMemcpyDeviceToHost);
-  dev_free(d_cases);
-  dev_free(d_out);
-  dev_free(d_fail);
-  delete[] h;
+  if (e == cudaSuccess) e = cudaMemcpy(&fails, v.d_fail, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) {
     set_error(std::string("lbm_vn_eigs: ") + cudaGetErrorString(e));
     cudaGetLastError();

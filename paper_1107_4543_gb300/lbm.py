@@ -348,7 +348,7 @@ def lbm_vn_eigs(kx, ky, U, V, S):
     bad = ctypes.c_int()
     _ck(load().lbm_vn_eigs(n, _ptr(kx), _ptr(ky), _ptr(U), _ptr(V), _ptr(S), _ptr(out),
                            ctypes.byref(bad)), "lbm_vn_eigs")
-    return out[:, 0::2] + 1j * out[:, 1::2]
+    return out.view(np.complex128)  # (re, im) pairs: (n, 9) complex, no copy
 
 
 def lbm_batch_create(handles):
