@@ -479,7 +479,10 @@ int lbm_create(int nx, int ny, const double S[9], double rho0, const double u0[2
   int dev = 0;
   CK(cudaGetDevice(&dev));
   lbm_ctx *h = new (std::nothrow) lbm_ctx();
-  if (!h) return LBM_ENOMEM;
+  if (!h) {
+    set_error("out of host memory");
+    return LBM_ENOMEM;
+  }
   h->device = dev;
   h->L.g = make_geom(nx, ny, V, esize);
   h->L.dtype = storage_dtype;
@@ -1221,7 +1224,10 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
   }
   DevGuard g(dev);
   lbm_batch_ctx *b = new (std::nothrow) lbm_batch_ctx();
-  if (!b) return LBM_ENOMEM;
+  if (!b) {
+    set_error("out of host memory");
+    return LBM_ENOMEM;
+  }
   b->device = dev;
   b->stream = members[0]->stream;
   for (int k = 0; k < n; ++k) b->members.push_back(members[k]);
