@@ -204,3 +204,26 @@ def test_gpu_vn_sweep_unstable_band(L, theta):
             assert np.max(growth[band]) > 1.005
         else:
             assert np.max(growth[band]) < 1.0 + 1e-12
+
+
+def test_gpu_vn_mean_flow_stability_claim(L):
+    """Section 4.2 on Fig. 4-4 through the GPU sweep: with U = V = 0.1 the
+    original free rates grow near k = 1.5 for k along and across the flow,
+    the optimized Table 2 group A rates do not, and along the axes
+    (theta = 0, pi/2, pi) neither grows."""
+    t = inp.TABLE2["A"]
+    opt = {k_: 1.0 / (t["sigma_" + k_[2:]] + 0.5) for k_ in ("s_e", "s_eps", "s_q", "s_nu")}
+    orig = dict(opt, s_eps=inp.LL["s_eps"], s_q=inp.LL["s_q"])
+    k = np.linspace(0.02, math.pi, 160)
+    for theta, off_axis in ((math.pi / 4, True), (3 * math.pi / 4, True), (0.0, False),
+                            (math.pi / 2, False), (math.pi, False)):
+        g = {}
+        for name, rates in (("opt", opt), ("orig", orig)):
+            lam = L.lbm_vn_eigs(k * math.cos(theta), k * math.sin(theta), 0.1, 0.1,
+                                inp.s_ll(rates))
+            g[name] = np.max(np.abs(lam))
+        assert g["opt"] < 1.0 + 1e-12, theta
+        if off_axis:
+            assert g["orig"] > 1.005, theta
+        else:
+            assert g["orig"] < 1.0 + 1e-12, theta

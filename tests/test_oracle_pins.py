@@ -235,6 +235,47 @@ def test_vn_unstable_band_claim():
                 assert np.max(np.abs(lam)) < 1.0 + 1e-9
 
 
+def test_vn_mean_flow_claims():
+    """Section 4.2 on Fig. 4-4 (U = V = 0.1, Table 2 group A against the
+    original free rates, the same s_e and s_nu): the optimized scheme is the
+    more stable one -- off the axes the original rates have a growing mode
+    near k = 1.5 (k along the flow and across it) and the optimized rates
+    none -- while along the axes (theta = 0, pi/2, pi) the two schemes'
+    hydrodynamic modes (the three least damped) nearly coincide."""
+    t = inp.TABLE2["A"]
+    opt = {k_: 1.0 / (t["sigma_" + k_[2:]] + 0.5) for k_ in ("s_e", "s_eps", "s_q", "s_nu")}
+    orig = dict(opt, s_eps=inp.LL["s_eps"], s_q=inp.LL["s_q"])
+    U = V = 0.1
+    ks = np.linspace(0.02, math.pi, 160)
+
+    def growth(r, th):
+        return max(np.max(np.abs(vn.eigs(k * math.cos(th), k * math.sin(th), U, V,
+                                          inp.s_paper(r)))) for k in ks)
+
+    for th in (math.pi / 4, 3 * math.pi / 4):
+        assert growth(orig, th) > 1.005
+        assert growth(opt, th) < 1.0 + 1e-12
+    for th in (0.0, math.pi / 2, math.pi):
+        assert growth(orig, th) < 1.0 + 1e-12 and growth(opt, th) < 1.0 + 1e-12
+
+    def hydro(r, th, k):
+        lam = vn.eigs(k * math.cos(th), k * math.sin(th), U, V, inp.s_paper(r))
+        top = lam[np.argsort(-np.abs(lam))[:3]]
+        return np.sort(np.abs(top)), np.sort(np.angle(top))
+
+    for th, near in ((0.0, True), (math.pi / 2, True), (math.pi, True), (math.pi / 4, False),
+                     (3 * math.pi / 4, False)):
+        dmag = dphase = 0.0
+        for k in np.linspace(0.1, 1.0, 10):
+            (ma, pa), (mb, pb) = hydro(opt, th, k), hydro(orig, th, k)
+            dmag = max(dmag, np.max(np.abs(ma - mb)))
+            dphase = max(dphase, np.max(np.abs(pa - pb)))
+        if near:
+            assert dmag < 1e-4 and dphase < 1e-5, (th, dmag, dphase)
+        else:
+            assert dmag > 1e-3, (th, dmag)
+
+
 def test_vn_small_bulk_viscosity_claims():
     """Section 4.2 on Table 3 (sigma_e, sigma_nu ~ 1e-3 .. 1e-6): the
     original free rates (Lallemand-Luo s_eps, s_q) grow for almost every
