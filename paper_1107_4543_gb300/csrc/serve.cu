@@ -57,12 +57,12 @@ struct Req {
   std::vector<double> rho, ux, uy;
 };
 
+// device bytes of a request's lattice: two population buffers laid out as
+// lbm_create lays them out, plus the per-lattice scratch
 size_t estimate_bytes(const lbm_request &r) {
-  int esize = r.dtype == LBM_F32DEV ? 4 : 2;
-  int V = vec_nodes(r.dtype);
-  int align = std::max(V, 128 / esize);
-  size_t pitch = (size_t)((r.nx + align - 1) / align * align);
-  return 2 * pitch * (size_t)r.ny * 9 * esize + 64 * 1024;
+  const int esize = r.dtype == LBM_F32DEV ? 4 : 2;
+  const Geom g = make_geom(r.nx, r.ny, vec_nodes(r.dtype), esize);
+  return 2 * (size_t)g.pitch * (size_t)r.ny * 9 * esize + 64 * 1024;
 }
 
 }  // namespace
