@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="batched",
-                   choices=["batched", "large", "serving", "vn", "opt", "oracle"])
+                   choices=["batched", "large", "serving", "vn", "opt", "source", "oracle"])
     p.add_argument("--lattices", type=int, default=512)
     p.add_argument("--lbm-steps", type=int, default=500)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -569,6 +569,57 @@ def bench_opt(args, L, torch):
                              "kind": "oracle", "sample": "%d candidates, numpy" % nc}}
 
 
+def bench_source(args, L, torch):
+    """The point-source experiment of section 5.1: a 101 x 101 periodic
+    lattice with the node at its centre forced to rho0 + rho_s sin(2 pi t/T)
+    (rho_s = 0.01, T = 20), for the three schemes compared there -- BGK, the
+    original MRT and the optimized one (Table 4 group A) -- in FP64 and
+    FP32 deviation storage.  A lattice this small is bound by launch
+    latency: the forced steps run as graphs of 64 (forced node, step)
+    pairs."""
+    import oracle as orc
+
+    stream = torch.cuda.current_stream()
+    n, rs, period, steps = 101, 0.01, 20.0, 64 * 64
+    t4 = inp.TABLE4["A"]
+    schemes = {"BGK": dict(s_e=t4["s_nu"], s_eps=t4["s_nu"], s_q=t4["s_nu"], s_nu=t4["s_nu"]),
+               "original": dict(s_e=t4["s_e"], s_eps=inp.LL["s_eps"], s_q=inp.LL["s_q"],
+                                s_nu=t4["s_nu"]),
+               "optimized": inp.rates("OPT-Z")}
+    per = {}
+    for dtype in ("f64", "f32"):
+        for name, r in schemes.items():
+            h = L.lbm_create(n, n, inp.s_ll(r), 1.0, (0.0, 0.0), L.DTYPES[dtype])
+            try:
+                L.lbm_set_stream(h, stream)
+                L.lbm_set_source(h, n // 2, n // 2, rs, period)
+                L.lbm_step(h, 64 * max(args.warmup, 1))
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                L.lbm_step(h, steps)
+                e1.record()
+                torch.cuda.synchronize()
+                per["%s-%s" % (name, dtype)] = round(n * n * steps / (e0.elapsed_time(e1) * 1e3), 1)
+            finally:
+                L.lbm_destroy(h)
+    # CPU baseline: the oracle's forced run of the optimized scheme
+    f0 = orc.init_eq(np.ones((n, n)), np.zeros((n, n)), np.zeros((n, n)))
+    cpu_steps = 2000
+    t0 = time.perf_counter()
+    orc.run_source(f0, inp.s_paper(schemes["optimized"]), cpu_steps, (n // 2, n // 2, rs, period))
+    cpu = n * n * cpu_steps / (time.perf_counter() - t0) / 1e6
+    return {"metric": "MLUPS, section 5.1 point source, 101x101, forced steps",
+            "value": per["optimized-f32"], "unit": "MLUPS", "higher_is_better": True,
+            "config": {"workload": "point-source-101x101-%d-steps" % steps, "period": period,
+                       "rho_s": rs},
+            "per_scheme": per,
+            "note": "launch-latency bound: 10,201 nodes per step",
+            "cpu_baseline": {"value": round(cpu, 1), "unit": "MLUPS", "cores": orc.threads(),
+                             "kind": "oracle", "sample": "optimized scheme, %d steps" % cpu_steps}}
+
+
 def oracle_timing(args):
     """The FP64 CPU oracle as it stands on the host cores: config 1 in full
     with one thread and with all cores, and config 3 (8192^2) timed over 20
@@ -669,6 +720,10 @@ def main():
     if args.workload == "opt":
         if rank == 0:
             print(json.dumps(bench_opt(args, L, torch)))
+        return
+    if args.workload == "source":
+        if rank == 0:
+            print(json.dumps(bench_source(args, L, torch)))
         return
     line, specs = bench_batched(args, L, torch, rank, ws)
     if rank == 0:

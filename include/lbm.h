@@ -118,9 +118,14 @@ int lbm_step(lbm_handle h, long n);
  * collision of every later lbm_step, node (x, y) is set to the equilibrium
  * at rest with density rho0 + amplitude * sin(2 pi t / period), t the
  * lattice time at the start of that step (0 after init).  amplitude = 0
- * removes the source.  Steps of a lattice with a source are launched one by
- * one (the forcing changes every step), not from a CUDA graph.  Errors:
- * LBM_EINVAL (node outside the lattice, period <= 0, batch member). */
+ * removes the source.  Runs of 64 steps from an even step replay a captured
+ * graph of (forced node, step) pairs after the host uploads that run's 64
+ * forcing values; other steps are launched one by one (same results).  FP16
+ * storage: a source set before lbm_init_field / lbm_set_populations enters
+ * the choice of the storage scale (its node deviates by up to 4/9 of the
+ * amplitude).  Errors: LBM_EINVAL (node outside the lattice, period <= 0,
+ * batch member, or an FP16 state whose scale leaves no room for the
+ * amplitude). */
 int lbm_set_source(lbm_handle h, int x, int y, double amplitude, double period);
 
 /* lbm_tune -- time the launch variants of the step kernel on this lattice

@@ -152,6 +152,23 @@ cudaError_t launch_force_node(const AuxView &a, int x, int y, const double fs[9]
   return cudaGetLastError();
 }
 
+// the same, with the nine populations read from device memory (a table the
+// host fills before a captured sequence of forced steps)
+__global__ void k_force_node_tab(AuxView a, int x, int y, const double *fs) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.ny);
+    store_value(a, (long long)i * a.g.plane + (long long)ys * a.g.rstride + xs, i, fs[i]);
+  }
+}
+
+cudaError_t launch_force_node_tab(const AuxView &a, int x, int y, const double *fs_dev,
+                                  cudaStream_t st) {
+  k_force_node_tab<<<1, 32, 0, st>>>(a, x, y, fs_dev);
+  return cudaGetLastError();
+}
+
 __global__ void k_maxdev_eq(AuxView a, const double *rho, const double *ux, const double *uy,
                             int kind, AnalyticParams ap, unsigned int *max_bits) {
   const long long N = (long long)a.g.nx * a.g.ny;

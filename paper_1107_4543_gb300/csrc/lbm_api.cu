@@ -111,6 +111,10 @@ struct lbm_ctx {
   bool src_on = false;
   int sx = 0, sy = 0;
   double s_amp = 0, s_period = 1;
+  // forced steps in graphs: kSrcGraph x (forced node from src_tab[k], step)
+  cudaGraphExec_t src_graph = nullptr;
+  double *src_tab = nullptr;  // 9 populations per captured step
+  int src_gx = -1, src_gy = -1;  // source node the graph was captured for
 };
 
 #define CK(call)                                                            \
@@ -144,6 +148,17 @@ static AuxView aux_view(const lbm_ctx *h) {
   return a;
 }
 
+static int free_graph(lbm_ctx *h);
+
+// the largest |f'| the point source writes: at its node f^eq(rho0 +
+// amplitude sin(...), 0) - f^eq(rho0, 0) peaks at the rest weight 4/9
+static double source_maxdev(const lbm_ctx *h) {
+  return h->src_on ? 4.0 / 9.0 * fabs(h->s_amp) : 0.0;
+}
+
+// The captured step graphs hold the storage scale (the step kernel's
+// DevParams, the forced-node kernel's AuxView) by value: a new scale drops
+// them, so the next run recaptures.
 static void set_qscale(lbm_ctx *h, double maxabs) {
   // stored |f'| * qscale stays near 2^14: 11-bit FP16 mantissas with 4x
   // headroom below the largest finite FP16 (65504), and no subnormals for
@@ -154,6 +169,7 @@ static void set_qscale(lbm_ctx *h, double maxabs) {
     k = std::max(-100, std::min(100, k));
     s = ldexp(1.0, k);
   }
+  if (s != h->qscale) free_graph(h);
   h->qscale = s;
   h->L.dp.scale = (float)s;
   h->L.dp.inv_scale = (float)(1.0 / s);
@@ -165,14 +181,15 @@ static int free_graph(lbm_ctx *h) {
     h->graph = nullptr;
     h->graph_steps = 0;
   }
+  if (h->src_graph) {
+    cudaGraphExecDestroy(h->src_graph);
+    h->src_graph = nullptr;
+  }
   return LBM_OK;
 }
 
-// Launch variant used before (or without) tuning, from GB300 measurements:
-// the 80-register cap (3 blocks per SM) is fastest for FP32 and FP16,
-// 128 registers for BF16.
-// launch variant before (or without) tuning: 3 blocks of 256 per SM, the
-// fastest for every deviation type on GB300
+// launch variant before (or without) tuning: the 80-register cap (3 blocks
+// of 256 per SM), the fastest for every deviation type on GB300
 static int default_variant(int) { return 2; }
 
 static bool autotune_enabled() {
@@ -313,6 +330,52 @@ static int capture_graph(lbm_ctx *h, int steps) {
   return LBM_OK;
 }
 
+// steps per captured graph of forced steps (even)
+constexpr int kSrcGraph = 64;
+
+// capture kSrcGraph forced steps starting from buffer 0: before step k the
+// source node's populations are set from src_tab + 9 k (filled by the host
+// for each replay), then the step runs
+static int capture_src_graph(lbm_ctx *h) {
+  if (h->src_graph) {
+    cudaGraphExecDestroy(h->src_graph);
+    h->src_graph = nullptr;
+  }
+  if (!h->src_tab) {
+    h->src_tab = (double *)dev_alloc(sizeof(double) * 9 * kSrcGraph);
+    if (!h->src_tab) {
+      set_error("out of device memory for the source table");
+      return LBM_ENOMEM;
+    }
+  }
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < kSrcGraph && e == cudaSuccess; ++k) {
+      AuxView a = aux_view(h);
+      a.buf = h->L.buf[k & 1];
+      e = launch_force_node_tab(a, h->sx, h->sy, h->src_tab + 9 * k, cs);
+      if (e == cudaSuccess) e = launch_one(h, k & 1, cs);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->src_graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    h->src_graph = nullptr;
+    set_error(std::string("source graph capture: ") + cudaGetErrorString(e));
+    cudaGetLastError();
+    return LBM_ECUDA;
+  }
+  h->src_gx = h->sx;
+  h->src_gy = h->sy;
+  return LBM_OK;
+}
+
 static int ensure_stage(lbm_ctx *h) {
   if (h->stage) return LBM_OK;
   const size_t n = (size_t)h->L.g.nx * h->L.g.ny;
@@ -420,7 +483,7 @@ static int do_init(lbm_ctx *h, const double *rho, const double *ux, const double
     CK(cudaStreamSynchronize(h->stream));
     float m;
     memcpy(&m, &bits, sizeof(m));
-    set_qscale(h, (double)m);
+    set_qscale(h, std::max((double)m, source_maxdev(h)));
     a = aux_view(h);
   }
   CK(launch_init_eq(a, rho, ux, uy, kind, params, h->stream, bad));
@@ -583,6 +646,7 @@ int lbm_destroy(lbm_handle h) {
   DevGuard g(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   free_graph(h);
+  dev_free(h->src_tab);
   dev_free(h->L.buf[0]);
   dev_free(h->L.buf[1]);
   dev_free(h->partials);
@@ -659,16 +723,37 @@ int lbm_step(lbm_handle h, long n) {
     if (rc != LBM_OK) return rc;
   }
   if (h->src_on) {
-    // the forcing changes every step: direct launches, no graph
+    // The forcing changes every step.  Runs of kSrcGraph steps from buffer 0
+    // replay a captured graph after the host uploads that run's forcing
+    // (the same host arithmetic as a single forced step, so both paths give
+    // identical populations); other steps are launched one by one.
     const double PI = 3.14159265358979323846;
-    for (; n > 0; --n) {
-      double fs[9];
-      const double rho_t = h->rho0 + h->s_amp * sin(2.0 * PI * (double)h->t / h->s_period);
+    auto forcing = [&](long long t, double *fs) {
+      const double rho_t = h->rho0 + h->s_amp * sin(2.0 * PI * (double)t / h->s_period);
       host_feq_j(rho_t, 0.0, 0.0, fs);
-      CK(launch_force_node(aux_view(h), h->sx, h->sy, fs, h->stream));
-      CK(launch_one(h, h->L.cur, h->stream));
-      h->L.cur ^= 1;
-      h->t += 1;
+    };
+    while (n > 0) {
+      if (h->L.cur == 0 && n >= kSrcGraph) {
+        if (!h->src_graph || h->src_gx != h->sx || h->src_gy != h->sy) {
+          int rc = capture_src_graph(h);
+          if (rc != LBM_OK) return rc;
+        }
+        double tab[9 * kSrcGraph];
+        for (int k = 0; k < kSrcGraph; ++k) forcing(h->t + k, tab + 9 * k);
+        // pageable source: the copy is staged before the call returns
+        CK(cudaMemcpyAsync(h->src_tab, tab, sizeof(tab), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaGraphLaunch(h->src_graph, h->stream));
+        n -= kSrcGraph;
+        h->t += kSrcGraph;
+      } else {
+        double fs[9];
+        forcing(h->t, fs);
+        CK(launch_force_node(aux_view(h), h->sx, h->sy, fs, h->stream));
+        CK(launch_one(h, h->L.cur, h->stream));
+        h->L.cur ^= 1;
+        n -= 1;
+        h->t += 1;
+      }
     }
     return LBM_OK;
   }
@@ -697,6 +782,11 @@ int lbm_set_source(lbm_handle h, int x, int y, double amplitude, double period) 
   REQUIRE(x >= 0 && x < h->L.g.nx && y >= 0 && y < h->L.g.ny, "source outside the lattice");
   REQUIRE(isfinite(amplitude) && isfinite(period) && period > 0, "bad source amplitude or period");
   REQUIRE(h->batch == nullptr, "lattice is a batch member");
+  // FP16: the stored state's scale must leave room for the source (the
+  // scale maps the largest deviation near 2^14, FP16's largest is 65504)
+  REQUIRE(h->L.dtype != LBM_F16DEV || 4.0 / 9.0 * fabs(amplitude) * h->qscale < 32768.0,
+          "source amplitude exceeds the FP16 storage scale of the current state; set the "
+          "source before lbm_init_field or lbm_set_populations");
   h->src_on = amplitude != 0.0;
   h->sx = x;
   h->sy = y;
@@ -789,7 +879,7 @@ int lbm_set_populations(lbm_handle h, const double *f) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     float m;
     memcpy(&m, &bits, sizeof(m));
-    if (e == cudaSuccess) set_qscale(h, (double)m);
+    if (e == cudaSuccess) set_qscale(h, std::max((double)m, source_maxdev(h)));
   }
   if (e == cudaSuccess) e = launch_set_pop(aux_view(h), tmp, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -144,6 +144,8 @@ cudaError_t launch_moments_dev(const AuxView &a, double *rho, double *ux, double
                                cudaStream_t st);
 cudaError_t launch_force_node(const AuxView &a, int x, int y, const double fs[9],
                               cudaStream_t st);
+cudaError_t launch_force_node_tab(const AuxView &a, int x, int y, const double *fs_dev,
+                                  cudaStream_t st);
 cudaError_t launch_get_pop(const AuxView &a, double *f, cudaStream_t st);
 cudaError_t launch_set_pop(const AuxView &a, const double *f, cudaStream_t st);
 cudaError_t launch_maxdev_pop(const AuxView &a, const double *f, unsigned int *max_bits,

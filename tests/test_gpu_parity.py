@@ -209,6 +209,64 @@ def test_checkpoint_restore_is_exact(L, dtype):
         assert np.array_equal(a, b)
 
 
+def test_fp16_reinit_with_a_new_scale_after_graph_runs(L):
+    """An FP16 lattice re-initialised (or restored) with a field of another
+    amplitude picks a new storage scale; runs long enough to replay the
+    captured step graph (and the forced-step graph with a point source)
+    must use it: the result equals that of a fresh lattice."""
+    n, steps = 48, 130
+    r = inp.rates("OPT")
+    small = inp.gaussian_pulse(n, n, 1e-5, 4.0)
+    large = inp.gaussian_pulse(n, n, 1e-2, 4.0)
+
+    def fresh(fields, source):
+        h = L.lbm_create(n, n, inp.s_ll(r), 1.0, (0.0, 0.0), L.LBM_F16DEV)
+        try:
+            if source:
+                L.lbm_set_source(h, 20, 21, 1e-3, 20.0)
+            L.lbm_init_field(h, *fields)
+            L.lbm_step(h, steps)
+            return L.lbm_get_populations(h)
+        finally:
+            L.lbm_destroy(h)
+
+    for source in (False, True):
+        h = L.lbm_create(n, n, inp.s_ll(r), 1.0, (0.0, 0.0), L.LBM_F16DEV)
+        try:
+            if source:
+                L.lbm_set_source(h, 20, 21, 1e-3, 20.0)
+            L.lbm_init_field(h, *small)
+            L.lbm_step(h, steps)  # captures the graph at the small field's scale
+            L.lbm_init_field(h, *large)
+            L.lbm_step(h, steps)
+            got = L.lbm_get_populations(h)
+            snap = fresh(small, source)
+            L.lbm_set_populations(h, snap)  # back to the small scale
+            L.lbm_step(h, steps)
+            got2 = L.lbm_get_populations(h)
+        finally:
+            L.lbm_destroy(h)
+        assert np.array_equal(got, fresh(large, source)), source
+        ref = L.lbm_create(n, n, inp.s_ll(r), 1.0, (0.0, 0.0), L.LBM_F16DEV)
+        try:
+            if source:
+                L.lbm_set_source(ref, 20, 21, 1e-3, 20.0)
+            L.lbm_set_populations(ref, snap)
+            L.lbm_step(ref, steps)
+            want2 = L.lbm_get_populations(ref)
+        finally:
+            L.lbm_destroy(ref)
+        assert np.array_equal(got2, want2), source
+    # a source far beyond the scale of an FP16 state already stored is refused
+    h = L.lbm_create(n, n, inp.s_ll(r), 1.0, (0.0, 0.0), L.LBM_F16DEV)
+    try:
+        L.lbm_init_field(h, *small)
+        with pytest.raises(L.LbmError):
+            L.lbm_set_source(h, 20, 21, 1.0, 20.0)
+    finally:
+        L.lbm_destroy(h)
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_drift_is_small_and_deterministic(L, dtype):
     nx = ny = 64
