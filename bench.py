@@ -18,11 +18,13 @@ reduction).
   fp64_plain the plain FP64 path on one 8192^2 lattice, for comparison
   cpu_baseline  the FP64 CPU oracle on a bounded sample of the workload
 
+--batch-dtype f16 / bf16 runs the same batch in 16-bit deviation storage.
 Other workloads: --workload large (one 8192^2 lattice, per storage type),
 --workload serving (Poisson request stream through lbm_submit/poll),
 --workload vn (von Neumann eigenvalue sweep), --workload opt (the
-free-parameter cost functions and their minimization) and --workload oracle
-(the CPU oracle alone: one thread and all cores).
+free-parameter cost functions and their minimization), --workload source
+(the section 5.1 point source on 101 x 101, three schemes) and --workload
+oracle (the CPU oracle alone: one thread and all cores).
 --impl reference times the CPU oracle on the same metric.
 """
 import argparse
