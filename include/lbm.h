@@ -227,10 +227,13 @@ typedef struct {
 } lbm_info_t;
 int lbm_info(lbm_handle h, lbm_info_t *out);
 
-/* Device allocator used for all later allocations of the library
- * (e.g. a caching allocator).  alloc returns NULL on failure.  Passing
- * NULL functions restores cudaMalloc / cudaFree.  Not thread-safe with
- * respect to concurrent lbm_create calls. */
+/* Device allocator used for all later allocations of lattices, batches,
+ * servers and cost evaluations (e.g. a caching allocator).  alloc returns
+ * NULL on failure.  Passing NULL functions restores cudaMalloc / cudaFree.
+ * Not thread-safe with respect to concurrent lbm_create calls.  The
+ * staging that lbm_vn_eigs keeps for the life of the process uses
+ * cudaMalloc / cudaHostAlloc directly, so that it never outlives the
+ * allocator that made it. */
 typedef void *(*lbm_alloc_fn)(size_t bytes, void *ctx);
 typedef void (*lbm_free_fn)(void *ptr, void *ctx);
 int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void *ctx);
