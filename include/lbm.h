@@ -128,7 +128,8 @@ int lbm_step(lbm_handle h, long n);
  * amplitude). */
 int lbm_set_source(lbm_handle h, int x, int y, double amplitude, double period);
 
-/* lbm_tune -- time the launch variants of the step kernel on this lattice
+/* lbm_tune -- (runtime; no counterpart in the paper) time the launch
+ * variants of the step kernel on this lattice
  * (LBM_TUNE_VARIANTS register caps of the deviation-storage kernel) and keep
  * the fastest for later steps.  Trial launches read the current state and
  * write only the idle buffer, so the lattice's state does not change.
@@ -227,7 +228,8 @@ typedef struct {
 } lbm_info_t;
 int lbm_info(lbm_handle h, lbm_info_t *out);
 
-/* Device allocator used for all later allocations of lattices, batches,
+/* (runtime; no counterpart in the paper) Device allocator used for all
+ * later allocations of lattices, batches,
  * servers and cost evaluations (e.g. a caching allocator).  alloc returns
  * NULL on failure.  Passing NULL functions restores cudaMalloc / cudaFree.
  * Not thread-safe with respect to concurrent lbm_create calls.  The
@@ -313,7 +315,8 @@ int lbm_opt_minimize(const lbm_cost_spec *spec, const double sigmas_in[4],
                      double sigmas_out[4], double *cost_out, int *evals);
 
 /* ------------------------------------------------------------- batches */
-/* Many independent lattices advanced together: every time step is ONE
+/* Many independent lattices advanced together (runtime around the step of
+ * section 2.1, which the paper states for one lattice): every time step is ONE
  * kernel launch per storage type over a work list of all members (each
  * lattice starts on a block boundary; one record per block gives its
  * lattice, geometry and buffers), and chunks of 64 steps are replayed from a
@@ -398,7 +401,8 @@ typedef struct {
 
 typedef struct lbm_server_ctx *lbm_server;
 
-/* A continuous-batching server on the current device: a host scheduler
+/* A continuous-batching server on the current device (runtime around the
+ * step of section 2.1; no counterpart in the paper): a host scheduler
  * thread admits queued requests while their device bytes fit in
  * hbm_budget_bytes (see lbm_server_set_policy for order and caps), steps
  * all admitted lattices together in generations of at most chunk_steps
