@@ -222,3 +222,21 @@ def test_off_axis_dispersion_is_improved_by_the_optimized_rates():
         assert phase_speed_error(opt, th) == pytest.approx(phase_speed_error(orig, th), abs=1e-12)
     for th in off:
         assert phase_speed_error(opt, th) < phase_speed_error(orig, th) - 1e-3
+
+
+def test_coefficients_carry_fixed_phases():
+    """Section 2.2 with a real Psi: the dt^l coefficient of B_n is (-i)^(l+1)
+    times a real matrix, for every direction, mean flow and rate set (the
+    operators are A_l = (-i)^l times real matrices and the phases multiply
+    through both recursions).  The device cost kernel runs the recursion on
+    these real factors; here the complex oracle, which does not assume it,
+    shows it exactly (imaginary parts of the factors are zero)."""
+    rng = np.random.default_rng(5)
+    for n in (2, 4, 6):
+        th = rng.uniform(0, 2 * np.pi, 7)
+        U, V = rng.uniform(-0.2, 0.2, (2, 7))
+        sig = 10 ** rng.uniform(-4, 1, 4)
+        b = md.bn_coeffs(th, U, V, md.s_paper_from_sigmas(*sig), n)
+        for l in range(n):
+            z = b[:, l] / (-1j) ** (l + 1)
+            assert np.max(np.abs(z.imag)) <= 1e-15 * max(np.max(np.abs(z.real)), 1.0), (n, l)
