@@ -43,7 +43,8 @@ namespace {
 
 constexpr int NMAX = 6;                       // largest truncation order
 constexpr int SLOTS = NMAX * (NMAX + 1) / 2;  // coefficients of orders 1..NMAX
-constexpr int WPB = 4;                        // warps (points) per block
+constexpr int WPB = 2;                        // warps per block
+constexpr int PPW = 2;                        // quadrature points per warp
 constexpr int MAX_SPEED = 32;
 constexpr int MAX_THETA = 4 * NMAX + 4;
 constexpr int MAX_DIR = 6 * NMAX;
@@ -97,7 +98,7 @@ __constant__ double c_rfact[NMAX + 2] = {1.0,        1.0,         1.0 / 2.0,   1
                                          1.0 / 24.0, 1.0 / 120.0, 1.0 / 720.0, 1.0 / 5040.0};
 
 // real factors of the polynomial matrices of one point
-struct WarpMem {
+struct PointMem {
   double H[NMAX][81];       // H_l, l = 1..n (row-major)
   double psi0[18];          // Psi, rows 3..8, columns 0..2
   double q[18];             // the same divided by D_kk
@@ -105,6 +106,13 @@ struct WarpMem {
   double B[SLOTS][9];       // B_m, 3 x 3
   double pw[PW_BLOCKS][9];  // powers of B_s
   double part[9];
+  double kx, ky, U, V, weight;  // the point: wave direction, mean flow, weight
+  int it;                       // its wave-direction index
+};
+
+// the PPW points of one warp
+struct WarpMem {
+  PointMem pt[PPW];
 };
 
 struct CostSpec {
@@ -132,7 +140,7 @@ __device__ __forceinline__ double hx(const double *Hl, int r, const double *X, i
 }
 
 // B_s^p, coefficient of degree d
-__device__ __forceinline__ const double *bpow(const WarpMem &w, int s, int p, int d) {
+__device__ __forceinline__ const double *bpow(const PointMem &w, int s, int p, int d) {
   return p == 1 ? w.B[slot(s, d)] : w.pw[pw_off(s, p) + d];
 }
 
@@ -177,8 +185,10 @@ __device__ __forceinline__ double exact_real(int l, int e, double kx, double ky,
 //   + sum_{l=1..min(m, t+1)} rows 0..2 of H_l Phi_{m+1-l, t-l+1}
 // -- Eqs. R-A/R-B and R-D/R-E with every product truncated at dt^(m-1).
 // No two lanes write one entry, and the powers B_m^p needed later are
-// formed once, right after B_m.  Work items run heaviest first (highest
-// degree t), so that each round of 32 lanes holds items of similar cost.
+// formed once, right after B_m.  A warp carries PPW points (the matrices are
+// small: one point leaves most lanes idle), its lanes taking the entries of
+// all of them; work items run heaviest first (highest degree t, the points
+// interleaved), so that each round of 32 lanes holds items of similar cost.
 //
 // tab: the point table (T_* offsets) followed by, per candidate, sigma_e,
 // sigma_eps, sigma_q, sigma_nu and the rates s = 1 / (sigma + 1/2) in that
@@ -189,31 +199,44 @@ k_opt_points(CostSpec cs, const double *__restrict__ tab, const double *__restri
   extern __shared__ unsigned char smem_raw[];
   WarpMem &w = reinterpret_cast<WarpMem *>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
-  const long long p = (long long)blockIdx.x * WPB + (threadIdx.x >> 5);
+  const long long p0 = ((long long)blockIdx.x * WPB + (threadIdx.x >> 5)) * PPW;
   const int ci = blockIdx.y;
-  if (p >= npoints) return;  // warp-uniform
+  if (p0 >= npoints) return;  // warp-uniform
   const int n = cs.order;
-
-  // the point: theta (fastest), flow direction, flow speed
-  const int it = (int)(p % cs.n_theta);
-  const long long q = p / cs.n_theta;
-  const int id = (int)(q % cs.n_dir);
-  const int iu = (int)(q / cs.n_dir);
-  const double kx = tab[T_CTH + it], ky = tab[T_STH + it];
-  double U = 0.0, V = 0.0, weight = cs.w_theta;
-  if (cs.kind == 1) {
-    U = tab[T_SU + iu] * tab[T_CPH + id];
-    V = tab[T_SU + iu] * tab[T_SPH + id];
-    weight *= cs.w_dir * tab[T_WU + iu];
-  }
   const double *sg = tab + T_SIZE + 8 * (long long)ci;  // sigmas
-  const double *rs = sg + 4;                    // rates
+  const double *rs = sg + 4;                             // rates
+
+  // the points: theta (fastest), flow direction, flow speed; a slot past the
+  // last point repeats the last point and is not written
+  if (lane < PPW) {
+    long long p = p0 + lane;
+    if (p >= npoints) p = npoints - 1;
+    const int it = (int)(p % cs.n_theta);
+    const long long q = p / cs.n_theta;
+    const int id = (int)(q % cs.n_dir);
+    const int iu = (int)(q / cs.n_dir);
+    PointMem &P = w.pt[lane];
+    P.it = it;
+    P.kx = tab[T_CTH + it];
+    P.ky = tab[T_STH + it];
+    double U = 0.0, V = 0.0, weight = cs.w_theta;
+    if (cs.kind == 1) {
+      U = tab[T_SU + iu] * tab[T_CPH + id];
+      V = tab[T_SU + iu] * tab[T_SPH + id];
+      weight *= cs.w_dir * tab[T_WU + iu];
+    }
+    P.U = U;
+    P.V = V;
+    P.weight = weight;
+  }
+  __syncwarp();
 
   // Psi (section 2.3, about rho = 1, j = (U, V)), rows 3..8 and columns
   // 0..2: s_r times the derivative of m^eq_r by (rho, jx, jy)
-  if (lane < 18) {
-    const int r = 3 + lane / 3, c = lane % 3;
-    const double u2 = U * U + V * V;
+  for (int e = lane; e < 18 * PPW; e += 32) {
+    PointMem &P = w.pt[e / 18];
+    const int rc = e % 18, r = 3 + rc / 3, c = rc % 3;
+    const double U = P.U, V = P.V, u2 = U * U + V * V;
     double j;
     switch (r) {
       case 3: j = c == 0 ? -2.0 - 3.0 * u2 : (c == 1 ? 6.0 * U : 6.0 * V); break;
@@ -224,69 +247,74 @@ k_opt_points(CostSpec cs, const double *__restrict__ tab, const double *__restri
       default: j = c == 0 ? -U * V : (c == 1 ? V : U); break;
     }
     const double ps = rate(r, rs) * j;
-    w.psi0[lane] = ps;
-    w.q[lane] = ps * rnorm(r);
+    P.psi0[rc] = ps;
+    P.q[rc] = ps * rnorm(r);
   }
   __syncwarp();
   // H_l = K_l D^-1 Psi: columns 0..2 (identity + Psi's first columns),
   // then columns 3..8 ((1 - s_c) / D_cc times column c of K_l)
-  const double *K = ktab + (long long)it * NMAX * 81;
-  for (int e = lane; e < 27 * n; e += 32) {
-    const int l = e / 27, r = (e % 27) / 3, c = e % 3;
-    const double *Kr = K + l * 81 + r * 9;
+  for (int e = lane; e < 27 * n * PPW; e += 32) {
+    PointMem &P = w.pt[e % PPW];
+    const int f = e / PPW, l = f / 27, r = (f % 27) / 3, c = f % 3;
+    const double *Kr = ktab + ((long long)P.it * NMAX + l) * 81 + r * 9;
     double h = Kr[c] * rnorm(c);
 #pragma unroll
-    for (int k = 3; k < 9; ++k) h += Kr[k] * w.q[(k - 3) * 3 + c];
-    w.H[l][r * 9 + c] = h;
+    for (int k = 3; k < 9; ++k) h += Kr[k] * P.q[(k - 3) * 3 + c];
+    P.H[l][r * 9 + c] = h;
   }
-  for (int e = lane; e < 54 * n; e += 32) {
-    const int l = e / 54, r = (e % 54) / 6, c = 3 + e % 6;
-    w.H[l][r * 9 + c] = K[l * 81 + r * 9 + c] * ((1.0 - rate(c, rs)) * rnorm(c));
+  for (int e = lane; e < 54 * n * PPW; e += 32) {
+    PointMem &P = w.pt[e % PPW];
+    const int f = e / PPW, l = f / 54, r = (f % 54) / 6, c = 3 + f % 6;
+    P.H[l][r * 9 + c] = ktab[((long long)P.it * NMAX + l) * 81 + r * 9 + c] *
+                        ((1.0 - rate(c, rs)) * rnorm(c));
   }
   __syncwarp();
 
   for (int m = 1; m <= n; ++m) {
     // Phi_m, rows 3..8
-    for (int e = lane; e < 18 * m; e += 32) {
-      const int t = m - 1 - e / 18, rc = e % 18, r = 3 + rc / 3, c = rc % 3;
-      double v = t == 0 ? w.psi0[rc] : 0.0;
+    for (int e = lane; e < 18 * PPW * m; e += 32) {
+      const int t = m - 1 - e / (18 * PPW), rc = e % 18, r = 3 + rc / 3, c = rc % 3;
+      PointMem &P = w.pt[(e / 18) % PPW];
+      double v = t == 0 ? P.psi0[rc] : 0.0;
       for (int l = 1; l <= t; ++l) {
         const int s = m - l, d = t - l;
         double acc = 0.0;
         for (int a = 0; a <= d; ++a) {
-          const double *X = w.phi[slot(s, a)];
-          const double *Pp = bpow(w, s, l, d - a);
+          const double *X = P.phi[slot(s, a)];
+          const double *Pp = bpow(P, s, l, d - a);
 #pragma unroll
           for (int k = 0; k < 3; ++k) acc += X[rc - c + k] * Pp[k * 3 + c];
         }
         v -= c_rfact[l] * acc;
-        v += hx(w.H[l - 1], r, w.phi[slot(s, d)], d, c);
+        v += hx(P.H[l - 1], r, P.phi[slot(s, d)], d, c);
       }
-      w.phi[slot(m, t)][rc] = inv_rate(r, sg) * v;
+      P.phi[slot(m, t)][rc] = inv_rate(r, sg) * v;
     }
     __syncwarp();
     // B_m
-    for (int e = lane; e < 9 * m; e += 32) {
-      const int t = m - 1 - e / 9, rc = e % 9, r = rc / 3, c = rc % 3;
+    for (int e = lane; e < 9 * PPW * m; e += 32) {
+      const int t = m - 1 - e / (9 * PPW), rc = e % 9, r = rc / 3, c = rc % 3;
+      PointMem &P = w.pt[(e / 9) % PPW];
       double v = 0.0;
-      for (int l = 1; l <= t && l < m; ++l) v -= c_rfact[l + 1] * bpow(w, m - l, l + 1, t - l)[rc];
+      for (int l = 1; l <= t && l < m; ++l) v -= c_rfact[l + 1] * bpow(P, m - l, l + 1, t - l)[rc];
       for (int l = 1; l <= m && l <= t + 1; ++l)
-        v += hx(w.H[l - 1], r, w.phi[slot(m + 1 - l, t - l + 1)], t - l + 1, c);
-      w.B[slot(m, t)][rc] = v;
+        v += hx(P.H[l - 1], r, P.phi[slot(m + 1 - l, t - l + 1)], t - l + 1, c);
+      P.B[slot(m, t)][rc] = v;
     }
     __syncwarp();
     // B_m^p, p = 2..n-m+1, truncated at degree m-1
     for (int pp = 2; pp <= n - m + 1; ++pp) {
-      for (int e = lane; e < 9 * m; e += 32) {
-        const int d = m - 1 - e / 9, rc = e % 9, r = rc / 3, c = rc % 3;
+      for (int e = lane; e < 9 * PPW * m; e += 32) {
+        const int d = m - 1 - e / (9 * PPW), rc = e % 9, r = rc / 3, c = rc % 3;
+        PointMem &P = w.pt[(e / 9) % PPW];
         double acc = 0.0;
         for (int a = 0; a <= d; ++a) {
-          const double *X = bpow(w, m, pp - 1, a);
-          const double *Bb = w.B[slot(m, d - a)];
+          const double *X = bpow(P, m, pp - 1, a);
+          const double *Bb = P.B[slot(m, d - a)];
 #pragma unroll
           for (int k = 0; k < 3; ++k) acc += X[r * 3 + k] * Bb[k * 3 + c];
         }
-        w.pw[pw_off(m, pp) + d][rc] = acc;
+        P.pw[pw_off(m, pp) + d][rc] = acc;
       }
       __syncwarp();
     }
@@ -296,27 +324,29 @@ k_opt_points(CostSpec cs, const double *__restrict__ tab, const double *__restri
   // E^l = (-i)^(l+1) (b_l - e_l) on the real factors, so the (l, m) term is
   // Re (-i)^(l-m) (b_l - e_l).(b_m - e_m) pi^(l+m+3) / (l+m+3); the factors
   // E_l are kept where the powers were
-  double(*E)[9] = w.pw;
-  if (lane < 9)
+  if (lane < 9 * PPW) {
+    PointMem &P = w.pt[lane / 9];
+    const int e = lane % 9;
+    double(*E)[9] = P.pw;
     for (int l = 0; l < n; ++l)
-      E[l][lane] = w.B[slot(n, l)][lane] - exact_real(l, lane, kx, ky, U, V, cs, sg[0], sg[3]);
-  if (lane < 9) {
+      E[l][e] = P.B[slot(n, l)][e] - exact_real(l, e, P.kx, P.ky, P.U, P.V, cs, sg[0], sg[3]);
     double acc = 0.0;
     for (int l = 0; l < n; ++l) {
       const bool odd_l = ((l + 1) & 1) != 0;
       if ((cs.part == 1 && !odd_l) || (cs.part == 2 && odd_l)) continue;
       for (int mq = l & 1; mq < n; mq += 2) {  // odd l - mq: Re (-i)^(l-mq) = 0
         const double sgn = ((l - mq) & 3) == 0 ? 1.0 : -1.0;
-        acc += sgn * (E[l][lane] * E[mq][lane]) * tab[T_KINT + l + mq + 3];
+        acc += sgn * (E[l][e] * E[mq][e]) * tab[T_KINT + l + mq + 3];
       }
     }
-    w.part[lane] = acc;
+    P.part[e] = acc;
   }
   __syncwarp();
-  if (lane == 0) {
+  if (lane < PPW && p0 + lane < npoints) {
+    const PointMem &P = w.pt[lane];
     double v = 0.0;
-    for (int e = 0; e < 9; ++e) v += w.part[e];
-    partial[(long long)ci * npoints + p] = v * weight;
+    for (int e = 0; e < 9; ++e) v += P.part[e];
+    partial[(long long)ci * npoints + p0 + lane] = v * P.weight;
   }
 }
 
@@ -519,7 +549,7 @@ int eval_costs(Workspace &ws, const CostSpec &cs, int n, const double *sig_host,
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_opt_points, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   if (e == cudaSuccess) {
-    dim3 grid((unsigned)((npoints + WPB - 1) / WPB), (unsigned)n);
+    dim3 grid((unsigned)((npoints + WPB * PPW - 1) / (WPB * PPW)), (unsigned)n);
     k_opt_points<<<grid, WPB * 32, shm>>>(cs, ws.tab, ws.ktab, npoints, ws.part);
     e = cudaGetLastError();
   }
