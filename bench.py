@@ -50,7 +50,7 @@ KERNEL_SOURCES = ["csrc/step_impl.cuh", "csrc/d2q9_pull.cuh", "csrc/collide.cuh"
                   "csrc/step_f32.cu", "csrc/step_f16.cu", "csrc/step_bf16.cu", "csrc/step_f64.cu"]
 
 
-def parse():
+def parser():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=5)
@@ -71,7 +71,11 @@ def parse():
                    help="storage type of the batched workload")
     p.add_argument("--batch-variant", type=int, default=-1,
                    help="pin the batched launch variant (default: tuned)")
-    return p.parse_args()
+    return p
+
+
+def parse(argv=None):
+    return parser().parse_args(argv)
 
 
 # ------------------------------------------------------------ environment
