@@ -302,6 +302,36 @@ def test_vn_shear_mode_claim_at_very_small_bulk_viscosity():
         assert shear_error(orig, th) > 0.5, th
 
 
+@pytest.mark.parametrize("group", ["A", "B"])
+def test_vn_acoustic_damping_claim_at_small_viscosities(group):
+    """Section 4.2 on Fig. 4-7 and the conclusion: at very small shear and
+    bulk viscosities (Table 3, U = 0.1, V = 0) the optimized acoustic modes
+    damp at the exact rate k^2 (sigma_e + sigma_nu) / 6 within 10% for
+    k <= 0.6 in every direction, while off the axes the original free rates'
+    acoustic modes miss it by more than 100% (modes taken as the eigenvalues
+    nearest the exact exp(-i k (U cos(theta) +- c_s) - Gamma))."""
+    t = inp.TABLE3[group]
+    opt = {k_: 1.0 / (t["sigma_" + k_[2:]] + 0.5) for k_ in ("s_e", "s_eps", "s_q", "s_nu")}
+    orig = dict(opt, s_eps=inp.LL["s_eps"], s_q=inp.LL["s_q"])
+    U, V = 0.1, 0.0
+
+    def acoustic_error(r, th):
+        worst = 0.0
+        for k in np.linspace(0.1, 0.6, 6):
+            gamma = k * k * (t["sigma_e"] + t["sigma_nu"]) / 6
+            lam = vn.eigs(k * math.cos(th), k * math.sin(th), U, V, inp.s_paper(r))
+            for sgn in (1.0, -1.0):
+                exact = np.exp(-1j * k * (U * math.cos(th) + V * math.sin(th) + sgn * vn.CS) - gamma)
+                got = lam[np.argmin(np.abs(lam - exact))]
+                worst = max(worst, abs(-math.log(abs(got)) - gamma) / gamma)
+        return worst
+
+    for th in (0.0, math.pi / 4, math.pi / 3, math.pi / 2):
+        assert acoustic_error(opt, th) < 0.1, th
+    for th in (math.pi / 4, math.pi / 3):
+        assert acoustic_error(orig, th) > 1.0, th
+
+
 def test_vn_small_bulk_viscosity_claims():
     """Section 4.2 on Table 3 (sigma_e, sigma_nu ~ 1e-3 .. 1e-6): the
     original free rates (Lallemand-Luo s_eps, s_q) grow for almost every
