@@ -47,8 +47,9 @@ def test_zero_flow_low_orders_match_printed_matrices():
 
 
 def test_uniform_flow_matches_printed_convection_and_appendix_c():
-    """dt^0 coefficient with a mean flow (section 2.3.2) and entries of the
-    dt^1 coefficient of B_2 printed in Appendix C (1-based indices there)."""
+    """dt^0 coefficient with a mean flow (section 2.3.2) and the nine entries
+    of the dt^1 coefficient of B_2 printed in Appendix C (1-based indices
+    there)."""
     rng = np.random.default_rng(4)
     se, sn = 0.021, 0.0073
     s = md.s_paper_from_sigmas(se, 0.4, 0.9, sn)
@@ -68,9 +69,22 @@ def test_uniform_flow_matches_printed_convection_and_appendix_c():
     c33 = (-kx ** 2 * sn / 3 + 3 * kx * ky * U * V * sn - ky ** 2 * sn / 3 + kx ** 2 * U ** 2 * sn
            - ky ** 2 * U ** 2 * sn / 2 + 1.5 * ky ** 2 * V ** 2 * sn - ky ** 2 * se / 3
            + kx * ky * U * V * se + 1.5 * ky ** 2 * V ** 2 * se + ky ** 2 * U ** 2 * se / 2)
-    assert np.max(np.abs(b[:, 1, 1, 1] - c22)) <= 1e-15
-    assert np.max(np.abs(b[:, 1, 1, 2] - c23)) <= 1e-15
-    assert np.max(np.abs(b[:, 1, 2, 2] - c33)) <= 1e-15
+    c21 = (-2 * ky ** 2 * U * V ** 2 * sn + ky ** 2 * U * sn / 3 - 3 * kx * ky * U ** 2 * V * sn
+           + kx ** 2 * U * V ** 2 * sn + kx * ky * V ** 3 * sn + kx ** 2 * U * sn / 3
+           - kx ** 2 * U ** 3 * sn - kx ** 2 * U * V ** 2 * se + kx ** 2 * U * se / 3
+           - kx ** 2 * U ** 3 * se - kx * ky * U ** 2 * V * se + kx * ky * V * se / 3
+           - kx * ky * V ** 3 * se)
+    c31 = (-3 * ky * kx * U * V ** 2 * sn - ky ** 2 * V ** 3 * sn + kx ** 2 * V * sn / 3
+           + ky ** 2 * U ** 2 * V * sn + ky * kx * U ** 3 * sn + ky ** 2 * V * sn / 3
+           - 2 * kx ** 2 * V * U ** 2 * sn - ky ** 2 * V ** 3 * se - ky * kx * U * V ** 2 * se
+           + ky ** 2 * V * se / 3 - ky * kx * U ** 3 * se + ky * kx * U * se / 3
+           - ky ** 2 * U ** 2 * V * se)
+    c32 = (-ky ** 2 * U * V * sn - 1.5 * kx * ky * U ** 2 * sn + 1.5 * kx * ky * V ** 2 * sn
+           + 2 * kx ** 2 * U * V * sn - kx * ky * se / 3 + 1.5 * kx * ky * U ** 2 * se
+           + 0.5 * kx * ky * V ** 2 * se + ky ** 2 * U * V * se)
+    for (i, j), c in (((1, 0), c21), ((1, 1), c22), ((1, 2), c23), ((2, 0), c31), ((2, 1), c32),
+                      ((2, 2), c33)):
+        assert np.max(np.abs(b[:, 1, i, j] - c)) <= 1e-15, (i, j)
     assert np.max(np.abs(b[:, 1, 0, :])) <= 1e-15  # Coeff(B_2[1, j], dt) = 0
 
 
