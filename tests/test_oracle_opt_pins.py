@@ -271,3 +271,92 @@ def test_mean_flow_optimization_reduces_only_the_dissipation(table, group, refer
     ge = [md.cost(s, 4, "G", "even", 0.2, reference) for s in (opt, orig)]
     assert go[0] == pytest.approx(go[1], rel=1e-4)
     assert ge[0] < 0.02 * ge[1]
+
+
+# Appendix B as printed, with the readings: "sigma v", "sigma e",
+# "sigma epsilon" typos are sigma_nu, sigma_e, sigma_eps; arguments
+# x = k_x, y = k_y, e = sigma_e, n = sigma_nu, p = sigma_eps, q = sigma_q.
+def appendix_b_dt3(x, y, e, n, p, q):
+    """B_5[2,2], [2,3], [3,2], [3,3] at dt^3 (App. B (B))."""
+    c22 = (-5/9*x**2*y**2*n*p*q + 1/9*x**4*p*q*n + 5/18*x**2*y**2*n**2*q - 1/9*x**2*y**2*n**2*e
+           - 5/54*x**2*y**2*n - 13/108*x**2*y**2*e - 1/9*x**4*n*e**2 + 1/6*x**4*e**2*q
+           - 1/108*x**4*n - 1/108*x**4*e - 1/9*x**4*e*p*q - 1/9*x**2*y**2*e*p*q
+           - 1/36*y**4*n - 1/9*y**4*n**3 + 10/9*x**2*y**2*n*e*q - 2/9*x**4*n*e*q
+           + 1/6*x**2*y**2*e**2*q - 1/9*x**2*y**2*e**2*n + 1/18*x**4*n**2*q - 1/9*x**4*n**2*e
+           - 1/9*x**2*y**2*n**3 + 2/9*y**4*n**2*q + 1/18*x**2*y**2*p)
+    c23 = (1/6*x*y**3*n**2*q - 5/9*x*y**3*n*p*q - 1/9*x*y**3*e*p*q + 1/6*x**3*y*n**2*q
+           + 1/9*x**3*y*p*q*n - 1/9*x**3*y*e*p*q + 1/6*x*y**3*e**2*q + 7/9*x*y**3*n*e*q
+           + 1/6*x**3*y*e**2*q + 1/9*x**3*y*e*n*q - 5/54*x*y**3*e - 7/108*x*y**3*n
+           - 7/108*x**3*y*n - 1/27*x**3*y*e - 1/9*x*y**3*e**2*n + 1/9*x**3*y*n**3
+           + 1/9*x*y**3*n**3 - 1/9*x**3*y*n**2*e + 1/18*x*y**3*p - 1/9*x**3*y*n*e**2
+           - 1/9*x*y**3*n**2*e)
+    c32 = (1/18*x**3*y*p - 5/9*x**3*y*p*q*n + 1/9*x*y**3*n*p*q - 1/9*x*y**3*e*p*q
+           - 1/9*x**3*y*e*p*q + 1/6*x**3*y*n**2*q - 1/9*x**3*y*n*e**2 - 1/27*x*y**3*e
+           - 7/108*x*y**3*n - 7/108*x**3*y*n - 5/54*x**3*y*e + 1/9*x*y**3*n**3
+           + 7/9*x**3*y*e*n*q + 1/9*x*y**3*n*e*q - 1/9*x**3*y*n**2*e + 1/6*x*y**3*n**2*q
+           - 1/9*x*y**3*e**2*n + 1/6*x**3*y*e**2*q + 1/9*x**3*y*n**3 - 1/9*x*y**3*n**2*e
+           + 1/6*x*y**3*e**2*q)
+    c33 = (-5/9*x**2*y**2*n*p*q + 5/18*x**2*y**2*n**2*q - 1/9*x**2*y**2*n**2*e - 5/54*x**2*y**2*n
+           - 13/108*x**2*y**2*e - 1/36*x**4*n - 1/9*x**2*y**2*e*p*q - 1/108*y**4*n
+           + 1/9*y**4*n*p*q + 10/9*x**2*y**2*n*e*q + 1/6*y**4*e**2*q - 1/9*y**4*e**2*n
+           - 1/9*y**4*n**2*e - 1/9*x**4*n**3 - 1/108*y**4*e + 1/6*x**2*y**2*e**2*q
+           - 1/9*x**2*y**2*e**2*n + 2/9*x**4*n**2*q - 1/9*x**2*y**2*n**3 + 1/18*y**4*n**2*q
+           - 2/9*y**4*n*e*q - 1/9*y**4*e*p*q + 1/18*x**2*y**2*p)
+    return c22, c23, c32, c33
+
+def appendix_b_zetas(e, n, p, q):
+    """zeta_{4,1}, zeta_{2,3}, zeta_{0,5} of B_5 at dt^4 (App. B (C))."""
+    z41 = (1/54*p**2 - 19/648*e**2 - 1/27*n**4 - 5/27*p*q**2*n + 7/27*n**3*q + 1/9*e**3*q
+           + 1/18*e**2*q**2 - 2/27*e**2*n**2 - 1/27*n*e**3 - 1/12*e*q + 7/54*n**2*q**2
+           + 7/27*e*q*n**2 + 7/27*e*q**2*n + 5/108*p*n + 1/108*e*p - 17/324*n*e - 7/108*n*q
+           + 1/18*p*q - 5/27*p*q*n**2 - 5/27*p**2*n*q - 1/27*p**2*q*e - 1/27*p*q*e**2
+           + 7/27*n*q*e**2 - 1/27*q**2*p*e - 1/27*e**4 + 13/1620 - 31/648*n**2 - 1/27*e*n**3)
+    z23 = (13/810 + 1/54*p**2 - 4/81*e**2 - 2/27*n**4 - 4/27*p*q**2*n + 8/27*n**3*q + 2/9*e**3*q
+           + 1/9*e**2*q**2 - 4/27*e**2*n**2 - 2/27*n*e**3 - 13/108*e*q + 4/27*n**2*q**2
+           + 11/27*e*q*n**2 + 11/27*e*q**2*n + 1/27*p*n + 1/54*e*p - 25/324*n*e - 13/108*n*q
+           + 1/18*p*q - 4/27*p*q*n**2 - 4/27*p**2*n*q - 2/27*p**2*q*e - 2/27*p*q*e**2
+           + 11/27*n*q*e**2 - 2/27*q**2*p*e - 2/27*e**4 - 19/324*n**2 - 2/27*e*n**3)
+    z05 = (-1/27*e*n**3 + 1/54*n**2*q**2 + 1/27*p*q**2*n - 2/27*e**2*n**2 + 1/27*p**2*n*q
+           + 1/9*e**3*q - 1/27*e**4 + 1/27*n**3*q - 1/27*n**4 + 1/18*e**2*q**2 - 2/27*e*q*n**2
+           - 1/108*p*n + 1/108*e*p - 2/27*e*q**2*n + 1/27*p*q*n**2 - 1/27*p*q*e**2
+           - 1/27*q**2*p*e - 1/648*e**2 - 2/27*n*q*e**2 - 1/27*n*e**3 + 1/1620 - 1/27*p**2*q*e
+           + 5/648*n**2 + 5/162*n*e)
+    return z41, z23, z05
+
+
+def test_appendix_b_dt3_and_dt4_matrices():
+    """The dt^3 and dt^4 coefficient matrices of B_5 printed in Appendix B,
+    free parameters sigma_eps and sigma_q included, at random rates and
+    directions.  Reading: the zeta_{0,5} terms of B_5[2,1] and B_5[3,1] are
+    printed with k_y^5 and k_x^5 swapped -- the j_x row must be odd in k_x
+    and the index (0,5) names k_y^5; the swapped form misses by 1e-3."""
+    rng = np.random.default_rng(7)
+    for _ in range(4):
+        e, p, q, n = 10 ** rng.uniform(-3, 0, 4)
+        th = rng.uniform(0, 2 * np.pi, 6)
+        b = md.bn_coeffs(th, 0.0, 0.0, md.s_paper_from_sigmas(e, p, q, n), 5)
+        x, y = np.cos(th), np.sin(th)
+        c22, c23, c32, c33 = appendix_b_dt3(x, y, e, n, p, q)
+        b3 = b[:, 3]
+        for (i, j), c in (((1, 1), c22), ((1, 2), c23), ((2, 1), c32), ((2, 2), c33)):
+            assert np.max(np.abs(b3[:, i, j] - c)) <= 1e-15, (i, j)
+        for (i, j) in ((0, 1), (0, 2), (1, 0), (2, 0)):
+            assert np.max(np.abs(b3[:, i, j])) <= 1e-15, (i, j)
+        b4 = b[:, 4]
+        c12 = -1j / 540 * x * (20 * x ** 2 * y ** 2 * n * e + 10 * x ** 4 * n * e
+                               - 90 * y ** 2 * e * q * x ** 2 + 10 * y ** 4 * n * e + 4 * x ** 4
+                               + 7 * y ** 4 - 30 * y ** 4 * n * q + 60 * x ** 2 * p * q * y ** 2
+                               + 14 * x ** 2 * y ** 2 - 30 * x ** 2 * y ** 2 * n * q)
+        c13 = -1j / 540 * y * (60 * x ** 2 * p * q * y ** 2 + 14 * x ** 2 * y ** 2
+                               - 90 * y ** 2 * e * q * x ** 2 + 20 * x ** 2 * y ** 2 * n * e
+                               + 7 * x ** 4 - 30 * x ** 2 * y ** 2 * n * q - 30 * x ** 4 * n * q
+                               + 10 * x ** 4 * n * e + 10 * y ** 4 * n * e + 4 * y ** 4)
+        z41, z23, z05 = appendix_b_zetas(e, n, p, q)
+        c21 = 1j * (z41 * x * y ** 4 + z23 * x ** 3 * y ** 2 + z05 * x ** 5)
+        c31 = 1j * (z41 * x ** 4 * y + z23 * x ** 2 * y ** 3 + z05 * y ** 5)
+        for (i, j), c in (((0, 1), c12), ((0, 2), c13), ((1, 0), c21), ((2, 0), c31)):
+            assert np.max(np.abs(b4[:, i, j] - c)) <= 1e-15, (i, j)
+        for (i, j) in ((0, 0), (1, 1), (1, 2), (2, 1), (2, 2)):
+            assert np.max(np.abs(b4[:, i, j])) <= 1e-15, (i, j)
+        swapped = 1j * (z41 * x * y ** 4 + z23 * x ** 3 * y ** 2 + z05 * y ** 5)
+        assert np.max(np.abs(b4[:, 1, 0] - swapped)) > 1e-5
