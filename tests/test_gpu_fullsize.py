@@ -14,13 +14,13 @@ import lbm_inputs as inp
 import oracle as orc
 
 pytestmark = pytest.mark.gpu
-# max |rho'_gpu - rho'_oracle| / A.  FP32 1e-6 and FP16 2e-3 are the stated
-# bars.  BF16 keeps an 8-bit significand: every stored population is
-# rounded by up to 2^-9 = 1.95e-3 of itself, so a single rounding already
-# reaches the 2e-3 bar near the pulse peak; it is gated at 2^-8, half a
-# BF16 ulp at the amplitude's scale (measured: 1.6e-3 on the 8192^2 pulse,
-# 2.03e-3 on the smallest lattice of the batch).
-TOL = {"f32": 1e-6, "f16": 2e-3, "bf16": 2.0 ** -8}
+# max |rho'_gpu - rho'_oracle| / A against the stated bars: FP32 1e-6,
+# FP16 and BF16 2e-3.  BF16 keeps an 8-bit significand, so every stored
+# population is rounded by up to 2^-9 = 1.95e-3 of itself each step; the
+# cases below that miss the 2e-3 bar are marked as expected failures at that
+# bar (strict: they fail the run if they start passing) and listed as
+# misses in the design notes, not gated at a wider tolerance.
+TOL = {"f32": 1e-6, "f16": 2e-3, "bf16": 2e-3}
 
 
 @pytest.fixture(scope="module")
@@ -73,13 +73,14 @@ def test_large_lattice_sampled(L, large_fields, dtype, T):
     assert max(errs) <= TOL[dtype]
 
 
-@pytest.mark.parametrize("dtype,T", [("f32", 500), ("f16", 200), ("bf16", 200)])
-def test_batched_workload_sampled(L, dtype, T):
-    """The 512-lattice batch in the batched launch (FP32 deviation: the
-    benchmark's 500 steps; the 16-bit types, measured with --batch-dtype,
-    200 steps as for the large lattice); three lattices (small, medium,
-    large) checked against the oracle: whole lattices when small, sampled
-    windows otherwise."""
+_BATCH = {}
+
+
+def batch_results(L, dtype, T):
+    """Run the 512-lattice batch once per storage type (cached): the three
+    checked lattices' density fields after T batched steps."""
+    if dtype in _BATCH:
+        return _BATCH[dtype]
     specs = inp.batch_specs(512, seed=1107 + 4, steps=500)
     hs = []
     try:
@@ -93,23 +94,43 @@ def test_batched_workload_sampled(L, dtype, T):
         L.lbm_batch_destroy(b)
         areas = np.array([s["nx"] * s["ny"] for s in specs])
         order = np.argsort(areas)
-        picks = [int(order[5]), int(order[256]), int(order[-1])]
-        results = {k: L.lbm_moments(hs[k])[0] for k in picks}
+        picks = {"small": int(order[5]), "medium": int(order[256]), "large": int(order[-1])}
+        results = {name: (specs[k], L.lbm_moments(hs[k])[0]) for name, k in picks.items()}
     finally:
         for h in hs:
             L.lbm_destroy(h)
-    for k in picks:
-        spec = specs[k]
-        fields = inp.batch_fields(spec)
-        s = inp.s_paper(spec["rates"])
-        got = results[k]
-        if spec["nx"] * spec["ny"] <= 400 * 400:
-            want = orc.moments(orc.run(orc.init_eq(*fields), s, T))[0]
-            err = np.max(np.abs(got - want)) / spec["amp"]
-        else:
-            pts = [(int(spec["xc"]), int(spec["yc"])), (0, 0), (spec["nx"] // 3, spec["ny"] - 1)]
-            err = max(abs(got[y, x] - orc.window_run(*fields, s, T, x, y).sum()) / spec["amp"]
-                      for (x, y) in pts)
-        print("\nbatch %s lattice %d (%dx%d), T=%d: max|drho'|/A = %.2e"
-              % (dtype, k, spec["nx"], spec["ny"], T, err))
-        assert err <= TOL[dtype]
+    _BATCH[dtype] = results
+    return results
+
+
+BF16_SMALL_MISS = pytest.mark.xfail(
+    strict=True,
+    reason="BF16 storage misses the stated 2e-3 bar on the smallest checked batch lattice "
+           "(31 x 35, A = 1.9e-5, 200 steps): measured 2.03e-3 of the amplitude, one BF16 "
+           "rounding being up to 1.95e-3 of a stored population")
+
+
+@pytest.mark.parametrize("dtype,T,which", [
+    ("f32", 500, "small"), ("f32", 500, "medium"), ("f32", 500, "large"),
+    ("f16", 200, "small"), ("f16", 200, "medium"), ("f16", 200, "large"),
+    pytest.param("bf16", 200, "small", marks=BF16_SMALL_MISS),
+    ("bf16", 200, "medium"), ("bf16", 200, "large")])
+def test_batched_workload_sampled(L, dtype, T, which):
+    """The 512-lattice batch in the batched launch (FP32 deviation: the
+    benchmark's 500 steps; the 16-bit types, measured with --batch-dtype,
+    200 steps as for the large lattice); three lattices (small, medium,
+    large) checked against the oracle: whole lattices when small, sampled
+    windows otherwise."""
+    spec, got = batch_results(L, dtype, T)[which]
+    fields = inp.batch_fields(spec)
+    s = inp.s_paper(spec["rates"])
+    if spec["nx"] * spec["ny"] <= 400 * 400:
+        want = orc.moments(orc.run(orc.init_eq(*fields), s, T))[0]
+        err = np.max(np.abs(got - want)) / spec["amp"]
+    else:
+        pts = [(int(spec["xc"]), int(spec["yc"])), (0, 0), (spec["nx"] // 3, spec["ny"] - 1)]
+        err = max(abs(got[y, x] - orc.window_run(*fields, s, T, x, y).sum()) / spec["amp"]
+                  for (x, y) in pts)
+    print("\nbatch %s %s lattice (%dx%d), T=%d: max|drho'|/A = %.2e"
+          % (dtype, which, spec["nx"], spec["ny"], T, err))
+    assert err <= TOL[dtype]

@@ -150,14 +150,26 @@ def test_dev_random_populations_ragged(L, dtype, nx, ny):
 # Over the 2000 steps of config 2 the FP32 storage rounding of every step
 # feeds the shear-stress moments, which the s_nu = 1.99996 of Table 5 (LL*
 # and OPT keep it) leaves almost undamped (|1 - s_nu| = 0.99996): the noise
-# then integrates instead of relaxing.  An FP32 emulation of the kernel puts
-# this storage-only floor at 4e-7 .. 1.2e-6 of the amplitude depending on
-# the free rates; 1e-6 holds for LL and OPT, LL* is gated at 2e-6.
-PLANE_TOL = {"LL": 1e-6, "OPT": 1e-6, "LL*": 2e-6}
+# then integrates instead of relaxing.  The stated bar is 1e-6 of the
+# amplitude for every set.  LL* with the mean flow U = 0.1 misses it: the
+# von Neumann matrix of section 4.1 for those rates (optimized s_e, s_nu
+# with the original s_eps = 1.54, s_q = 1.9) has a growing mode along the
+# flow, |lambda| = 1.00098 at k_x = 3 pi / 4, which amplifies the storage
+# rounding it is seeded with about sevenfold over 2000 steps (the FP64
+# oracle's own rounding is 2^29 times smaller and stays invisible); measured
+# 1.1e-6.  That case is an expected failure at the stated bar (strict), not
+# a wider gate; test_llstar_mean_flow_has_growing_mode pins the mode.
+PLANE_TOL = 1e-6
+LLSTAR_U01_MISS = pytest.mark.xfail(
+    strict=True,
+    reason="LL* at U = 0.1 misses the stated 1e-6 bar in FP32 (measured 1.1e-6): a growing "
+           "von Neumann mode (|lambda| = 1.00098 at k_x = 3 pi/4) amplifies storage rounding")
 
 
 @pytest.mark.parametrize("dtype", ["f32"])
-@pytest.mark.parametrize("U,name", [(0.0, "LL"), (0.1, "OPT"), (0.0, "OPT"), (0.1, "LL*")])
+@pytest.mark.parametrize("U,name", [(0.0, "LL"), (0.1, "LL"), (0.1, "OPT"), (0.0, "OPT"),
+                                    (0.0, "LL*"),
+                                    pytest.param(0.1, "LL*", marks=LLSTAR_U01_MISS)])
 def test_dev_plane_wave_config2(L, dtype, U, name):
     """512 x 16 plane wave (lambda = 8), amplitude 1e-4, 2000 steps, FP32
     deviation about f^eq(1, (U, 0))."""
@@ -168,7 +180,7 @@ def test_dev_plane_wave_config2(L, dtype, U, name):
     (rho_o, _, _), _ = run_orc(r, steps, fields=fields)
     err = max_rel(rho, rho_o, amp)
     print("\n%s plane wave U=%.1f %s: max|drho'|/A = %.3e" % (dtype, U, name, err))
-    assert err <= PLANE_TOL[name]
+    assert err <= PLANE_TOL
 
 
 # ----------------------------------------------------- whole-path checks
@@ -288,6 +300,65 @@ def test_drift_is_small_and_deterministic(L, dtype):
     assert abs(d1[1]) <= tol * mass and abs(d1[2]) <= tol * mass
     assert d1[3] == 0
     assert np.array_equal(d1, d2)
+
+
+# Drift (the a7 reduction) against the oracle, with a mean flow so that the
+# momentum sums are far from zero: a Gaussian pulse A = 1e-2 (b = 6) carried
+# by u0 = (0.1, -0.05) has sum rho' = A pi / alpha and sum j' = u0 sum rho'.
+# Collision and streaming conserve both (section 2.1, Eq. eq_conservative),
+# so the exact values at any time are those of the initial field.
+#   * FP64 storage: the GPU state is the oracle's bit for bit, so lbm_drift
+#     must equal the sums of the oracle's state to 1e-12 relative (only the
+#     order of the lattice-wide sum differs), and the initial field's exact
+#     sums within the rounding of the FP64 initial populations (FP64
+#     conservation);
+#   * FP32 deviation storage: every stored deviation is rounded once per step
+#     (relative error <= 2^-24), which does not conserve mass exactly; over
+#     T steps the sums can move by at most T 2^-24 sum|f'| (the storage
+#     rounding bound, sum|f'| taken at twice its initial value), against the
+#     exact initial sums and against the oracle's state.
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_drift_matches_oracle_with_mean_flow(L, dtype):
+    nx, ny, T, amp, b = 80, 64, 150, 1e-2, 6.0
+    u0 = (0.1, -0.05)
+    r = inp.rates("LL", nu=1e-3)
+    s = inp.s_paper(r)
+    fields = inp.gaussian_pulse(nx, ny, amp, b, u0=u0)
+    rho_in = fields[0]
+    exact = np.array([(rho_in - 1.0).sum(), u0[0] * (rho_in - 1.0).sum(),
+                      u0[1] * (rho_in - 1.0).sum()])
+    h = L.lbm_create(nx, ny, inp.s_ll(r), 1.0, u0, L.DTYPES[dtype])
+    try:
+        L.lbm_init_field(h, *fields)
+        d0 = L.lbm_drift(h)
+        L.lbm_step(h, T)
+        d1 = L.lbm_drift(h)
+    finally:
+        L.lbm_destroy(h)
+    f0 = orc.init_eq(*fields)
+    f_o = orc.run(f0, s, T)
+    cx, cy = orc.velocities()
+    base = orc.init_eq(np.ones((1, 1)), np.full((1, 1), u0[0]), np.full((1, 1), u0[1]))
+    dev = f_o - base
+    want = np.array([dev.sum(), (cx[:, None, None] * dev).sum(), (cy[:, None, None] * dev).sum()])
+    assert d0[3] == 0 and d1[3] == 0
+    print("\n%s drift: GPU %s oracle %s exact %s" % (dtype, d1[:3], want, exact))
+    if dtype == "f64":
+        assert np.all(np.abs(d1[:3] - want) <= 1e-12 * np.abs(want))
+        # conservation: each FP64 population of the initial equilibrium is
+        # rounded once (<= 2^-53 of it), and those roundings need not cancel
+        # in the sums
+        cons = 9 * nx * ny * 2.0 ** -53 * np.max(np.abs(f0))
+        assert np.all(np.abs(d1[:3] - exact) <= cons)
+        assert np.all(np.abs(d0[:3] - exact) <= cons)
+    else:
+        bound = (T + 1) * 2.0 ** -24 * 2.0 * np.abs(f0 - base).sum()
+        assert np.all(np.abs(d0[:3] - exact) <= 2.0 ** -24 * np.abs(f0 - base).sum())
+        assert np.all(np.abs(d1[:3] - exact) <= bound)
+        assert np.all(np.abs(d1[:3] - want) <= bound)
+    # the sums are those of a moving pulse: momentum = u0 x mass, no sign or
+    # component swapped
+    assert d1[1] > 0 > d1[2]
 
 
 def test_nonfinite_state_is_reported(L):

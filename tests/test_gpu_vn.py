@@ -92,11 +92,54 @@ def fit_rates(series, t, k, lam):
     return d_vn + dd, c_vn - dphi / k
 
 
+def linear_series(k, U, s, fh0, ts):
+    """The von Neumann prediction of the density mode: the sum over the 9
+    components of G(k)^t fh0 (section 4.1), fh0 the initial field's Fourier
+    coefficient at k.  Unlike the acoustic eigenvalue alone it carries every
+    mode the travelling-wave equilibrium init excites (the backward wave, the
+    kinetic transient), which at lambda = 4, 6 still shows in the fit."""
+    G = vn.amplification(k, 0.0, U, 0.0, s)
+    out = np.zeros(len(ts), dtype=complex)
+    Gt = np.eye(9, dtype=complex)
+    t = 0
+    for j, tt in enumerate(ts):
+        Gt = np.linalg.matrix_power(G, int(tt - t)) @ Gt
+        t = tt
+        out[j] = (Gt @ fh0).sum()
+    return out
+
+
+def fit_window(ts, lin, amp):
+    """Samples used for the fit: t >= 200 while the predicted mode is above
+    1e-2 of the amplitude (well above the storage rounding); the strongly
+    damped Lallemand-Luo waves at lambda = 4, 6 fall below that before
+    t = 200 (damping 0.045, 0.020 per step) and are fitted from t = 20."""
+    sel = (ts >= 200) & (np.abs(lin) >= 0.5e-2 * amp)
+    if sel.sum() < 10:
+        sel = (ts >= 20) & (np.abs(lin) >= 0.5e-2 * amp)
+    return sel
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_plane_wave_damping_and_speed(L, dtype):
     """Config 2: lambda in {4, 6, 8, 12, 16, 32, 64}, U in {0, 0.1}, Lallemand-
-    Luo, LL* and optimized rates; 2000 steps; moments sampled every 100
-    steps from t = 200.  Reports the table; gates the match with VN."""
+    Luo, LL* and optimized rates; 2000 steps; moments sampled every 10 steps.
+
+    Gates, for every wavelength:
+      (i) the measured density mode equals the von Neumann prediction
+          G(k)^t (all nine modes) within 5e-5 of the amplitude -- the
+          nonlinear O(A) part of the scheme, which the linearization drops
+          (the FP64 oracle's own run departs from it by up to 2.7e-5 of
+          A = 1e-4, at lambda = 32 after 2000 steps);
+      (ii) the damping rate and phase speed fitted from the run match those
+          of the acoustic eigenvalue within the kinetic-transient bias
+          (the same fit applied to the prediction (i), whose departure from
+          the eigenvalue is the contribution of the other modes) plus 1e-2
+          of the damping (1e-2 * |d| + 2e-8 per step) and 1e-5 of the speed
+          (the FP64 oracle's fit departs from the prediction's fit by at
+          most 4e-8 in speed);
+      (iii) for lambda >= 8 the plain fit stays within 1e-4 (speed) and 5%
+          (damping) of the eigenvalue, as before."""
     cases = []
     for U in (0.0, 0.1):
         for name in ("LL", "LL*", "OPT") + (("OPT-Z",) if U == 0.0 else ()):
@@ -104,24 +147,31 @@ def test_plane_wave_damping_and_speed(L, dtype):
                 cases.append((U, name, lam_len))
     amp = 1e-4
     hs = []
+    fh0s = []
+    x = np.arange(NX)
     for U, name, lam_len in cases:
         r = inp.rates(name, nu=1e-3)
         m = int(round(NX / lam_len))
+        k = 2 * math.pi * m / NX
+        fields = inp.plane_wave(NX, NY, amp, m, U=U)
         h = L.lbm_create(NX, NY, inp.s_ll(r), 1.0, (U, 0.0), L.DTYPES[dtype])
-        L.lbm_init_field(h, *inp.plane_wave(NX, NY, amp, m, U=U))
+        L.lbm_init_field(h, *fields)
         hs.append(h)
-    ts = np.arange(200, 2001, 100)
+        base = orc.init_eq(np.ones((1, NX)), np.full((1, NX), U), np.zeros((1, NX)))
+        f0 = orc.init_eq(fields[0][:1], fields[1][:1], fields[2][:1])
+        fh0s.append(((f0 - base)[:, 0, :] * np.exp(-1j * k * x)[None, :]).sum(axis=1) / NX)
+    ts = np.arange(0, 2001, 10)
     series = np.zeros((len(cases), len(ts)), dtype=complex)
-    x = np.arange(NX)
     try:
         b = L.lbm_batch_create(hs) if dtype != "f64" else None
         t = 0
         for j, tt in enumerate(ts):
-            if b is not None:
-                L.lbm_batch_step(b, tt - t)
-            else:
-                for h in hs:
-                    L.lbm_step(h, tt - t)
+            if tt > t:
+                if b is not None:
+                    L.lbm_batch_step(b, tt - t)
+                else:
+                    for h in hs:
+                        L.lbm_step(h, tt - t)
             t = tt
             for i, (U, name, lam_len) in enumerate(cases):
                 k = 2 * math.pi * round(NX / lam_len) / NX
@@ -134,21 +184,33 @@ def test_plane_wave_damping_and_speed(L, dtype):
             L.lbm_destroy(h)
     rows = []
     worst_c = worst_d = 0.0
+    fails = []
     for i, (U, name, lam_len) in enumerate(cases):
         r = inp.rates(name, nu=1e-3)
+        s = inp.s_paper(r)
         m = int(round(NX / lam_len))
         k = 2 * math.pi * m / NX
-        lam, _ = forward_mode(k, U, inp.s_paper(r))
+        lam, _ = forward_mode(k, U, s)
         d_vn, c_vn = vn.mode_rates(lam, k)
-        d, c = fit_rates(series[i], ts, k, lam)
-        rows.append((U, name, lam_len, d, d_vn, c, c_vn))
+        lin = linear_series(k, U, s, fh0s[i], ts)
+        sel = fit_window(ts, lin, amp)
+        dev = np.max(np.abs(series[i, sel] - lin[sel])) / amp
+        d, c = fit_rates(series[i, sel], ts[sel], k, lam)
+        dl, cl = fit_rates(lin[sel], ts[sel], k, lam)
+        tol_d = abs(dl - d_vn) + 1e-2 * abs(d_vn) + 2e-8
+        tol_c = abs(cl - c_vn) + 1e-5 * abs(c_vn)
+        rows.append((U, name, lam_len, ts[sel][0], ts[sel][-1], d, dl, d_vn, c, cl, c_vn, dev))
+        if dev > 5e-5 or abs(d - d_vn) > tol_d or abs(c - c_vn) > tol_c:
+            fails.append((U, name, lam_len, dev, abs(d - d_vn), tol_d, abs(c - c_vn), tol_c))
         if lam_len >= 8:
             worst_c = max(worst_c, abs(c - c_vn) / abs(c_vn))
             # relative, with an absolute floor for the nearly undamped sets
             worst_d = max(worst_d, abs(d - d_vn) / (abs(d_vn) + 4e-6))
-    print("\n%s plane waves: U  set  lambda  damping(GPU)  damping(VN)  c(GPU)  c(VN)" % dtype)
+    print("\n%s plane waves: U set lambda [t0,t1] damping(GPU, VN series, VN eig) "
+          "c(GPU, VN series, VN eig) max|GPU - VN series|/A" % dtype)
     for row in rows:
-        print("  %.1f %-5s %3d  %.4e  %.4e  %.6f  %.6f" % row)
+        print("  %.1f %-5s %3d [%4d,%4d] %.4e %.4e %.4e  %.7f %.7f %.7f  %.1e" % row)
+    assert not fails, fails
     assert worst_c < 1e-4
     assert worst_d < 0.05
 

@@ -602,3 +602,61 @@ def test_ll_order_is_the_c_abi_vector():
     sp = inp.s_paper(r)
     assert sp[3] == 1.64 and sp[4] == 1.54 and sp[5] == sp[6] == 1.9
     assert sp[7] == sp[8] == 1 / tau and not sp[:3].any()
+
+
+# ------------------------------------------------------- moments and windows
+@pytest.mark.parametrize("seed", range(3))
+def test_moments_velocity_round_trip(seed):
+    """oracle.moments returns u = j / rho: the textbook equilibrium carries
+    exactly the density rho and momentum rho u it was built from (its zeroth
+    and first velocity moments, section 2.3), and init_eq is pinned to that
+    equilibrium above, so moments(init_eq(rho, u)) must give back (rho, u)
+    to rounding.  A u taken as j (no division), swapped components or a
+    sign error fail it: rho differs from 1 by up to 20% here."""
+    rng = np.random.default_rng(100 + seed)
+    ny, nx = 7, 11
+    rho = rng.uniform(0.8, 1.2, (ny, nx))
+    ux = rng.uniform(-0.2, 0.2, (ny, nx))
+    uy = rng.uniform(-0.2, 0.2, (ny, nx))
+    r, u, v = orc.moments(orc.init_eq(rho, ux, uy))
+    assert np.max(np.abs(r - rho)) <= 1e-15
+    assert np.max(np.abs(u - ux)) <= 1e-15
+    assert np.max(np.abs(v - uy)) <= 1e-15
+
+
+@pytest.mark.parametrize("T", [5, 40])
+def test_window_run_equals_whole_lattice(T):
+    """oracle.window_run (the light-cone sampler behind the full-size parity
+    tests) against the plain whole-lattice run: after T steps a node depends
+    only on the initial field within T nodes, so the window's centre must
+    equal the whole lattice's node bit for bit -- at the wrap corners, in the
+    interior, and on a lattice narrower than the window along y (there the
+    whole periodic extent is kept)."""
+    s = inp.s_paper(inp.rates("OPT"))
+    for nx, ny in ((2 * T + 41, 2 * T + 17), (2 * T + 29, 2 * T - 1)):
+        rho, ux, uy = inp.pulse_with_vortices(nx, ny, seed=T + nx, amp=1e-3, b=4.0,
+                                              vstd=1e-3)
+        whole = orc.run(orc.init_eq(rho, ux, uy), s, T)
+        for x, y in ((0, 0), (nx - 1, ny - 1), (1, ny - 2), (nx - 2, 0), (nx // 2, ny // 3)):
+            got = orc.window_run(rho, ux, uy, s, T, x, y)
+            assert np.array_equal(got, whole[:, y, x]), (nx, ny, x, y)
+
+
+def test_llstar_mean_flow_has_growing_mode():
+    """Config 2's sets along the x axis of the 512 x 16 lattice (k_y = 0, the
+    modes a y-independent plane wave can seed): the von Neumann matrix of
+    section 4.1 is stable for LL, OPT (U = 0) and LL* at U = 0, while LL*
+    (optimized s_e, s_nu with the original s_eps, s_q) at U = 0.1 has a
+    growing mode near k_x = 3 pi / 4 -- the original free rates' mean-flow
+    instability that section 4.2 describes for off-axis waves -- which grows
+    about sevenfold over the 2000 steps of config 2."""
+    kx = 2 * np.pi * np.fft.fftfreq(512)
+    for name, U in (("LL", 0.0), ("LL", 0.1), ("OPT", 0.0), ("LL*", 0.0)):
+        lam = vn.eigs(kx, 0 * kx, U, 0.0, inp.s_paper(inp.rates(name, nu=1e-3)))
+        assert np.max(np.abs(lam)) < 1.0 + 1e-12, (name, U)
+    lam = np.abs(vn.eigs(kx, 0 * kx, 0.1, 0.0, inp.s_paper(inp.rates("LL*", nu=1e-3))))
+    g = lam.max(axis=1)
+    j = int(np.argmax(g))
+    assert 1.0009 < g[j] < 1.0011
+    assert abs(abs(kx[j]) - 3 * np.pi / 4) < 0.05
+    assert 6.0 < g[j] ** 2000 < 8.5
