@@ -62,6 +62,8 @@ def parser():
     p.add_argument("--lbm-steps", type=int, default=500)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="batched workload alone (no FP16 batch, config 3, serving keys)")
     p.add_argument("--requests", type=int, default=10000)
     p.add_argument("--policy", default="fifo", choices=["fifo", "shortest"])
     p.add_argument("--max-nodes", type=int, default=0, help="server resident-node cap")
@@ -86,11 +88,21 @@ def dist():
     return ws, rank, local
 
 
-def rank_specs(args, rank):
-    """The lattices of one rank: the whole 512-lattice workload, seeded per
-    rank (weak scaling: each GPU steps its own independent batch, and no
-    data crosses ranks)."""
-    return inp.batch_specs(args.lattices, seed=1107 + 4 + 1000 * rank, steps=args.lbm_steps)
+def rank_specs(args, rank, world=None):
+    """The lattices of one rank.  The workload is `lattices` lattices per GPU
+    (weak scaling: N GPUs step N x 512 independent lattices), drawn as one
+    seeded set and placed on the ranks by bytes (multi_gpu.partition_by_bytes:
+    largest first onto the least-loaded rank); no data crosses ranks while
+    they step.  With one rank this is the 512-lattice workload itself."""
+    from paper_1107_4543_gb300 import multi_gpu
+
+    if world is None:
+        world = dist()[0]
+    specs = inp.batch_specs(args.lattices * world, seed=1107 + 4, steps=args.lbm_steps)
+    if world == 1:
+        return specs
+    sizes = [multi_gpu.lattice_bytes(sp["nx"], sp["ny"], 1) for sp in specs]
+    return [specs[i] for i in multi_gpu.partition_by_bytes(sizes, world)[rank]]
 
 
 def reduce_max(x, device="cuda"):
@@ -324,36 +336,51 @@ def bench_batched(args, L, torch, rank, ws):
     launch_ms = float(np.mean(step_ms)) / lbm_steps  # one batched kernel per time step
     launches = args.steps * (lbm_steps + 2)  # batched steps + one drift launch pair
 
-    # e2e: host fields in, moments out, through the public API: the packed
-    # batch I/O calls (page-locked host arrays of all members' fields, moved
-    # in a few large copies overlapped with the init / moments kernels)
+    # e2e: host fields in, moments out, through the public API: one
+    # lbm_batch_solve_packed call per benchmark step (upload of the fields
+    # from page-locked host arrays, equilibrium init, the 500 steps, the
+    # drift sums, moments, download), queued back to back so that one
+    # solve's copies overlap its neighbours' stepping; lbm_batch_wait ends
+    # the timed region and reports the last solve's device time per phase
     def pinned_flat():
         return torch.empty(nodes, dtype=torch.float64, pin_memory=True).numpy()
 
-    fin = [pinned_flat() for _ in range(3)]
+    fin = tuple(pinned_flat() for _ in range(3))
     for c in range(3):
         np.concatenate([f[c].ravel() for f in fields], out=fin[c])
     fout = tuple(pinned_flat() for _ in range(3))
+    dout = np.zeros((len(hs), 4))
 
-    def e2e_step():
-        L.lbm_batch_init_packed(b, *fin)
-        L.lbm_batch_step(b, lbm_steps)
-        L.lbm_batch_drift(b, len(hs))
-        L.lbm_batch_moments_packed(b, fout)
+    pipelined = bdt != "f16"  # FP16 members take their storage scale on the host
 
-    e2e_step()
+    def e2e_solve():
+        if pipelined:
+            L.lbm_batch_solve_packed(b, lbm_steps, fin, fout, dout)
+        else:
+            L.lbm_batch_init_packed(b, *fin)
+            L.lbm_batch_step(b, lbm_steps)
+            dout[...] = L.lbm_batch_drift(b, len(hs))
+            L.lbm_batch_moments_packed(b, fout)
+
+    def e2e_wait():
+        return L.lbm_batch_wait(b) if pipelined else None
+
+    for _ in range(2):
+        e2e_solve()
+    e2e_wait()
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        e2e_step()
+        e2e_solve()
+    phases = e2e_wait()
     torch.cuda.synchronize()
     e2e_s = reduce_max(time.perf_counter() - t0)
     e2e_value = job_mlups(lu_job, e2e_s)
     L.lbm_batch_destroy(b)
     h2d = 3 * 8 * nodes
-    d2h = 3 * 8 * nodes
+    d2h = 3 * 8 * nodes + 4 * 8 * len(hs)
 
     fp64 = None
     if not args.no_fp64:
@@ -398,9 +425,24 @@ def bench_batched(args, L, torch, rank, ws):
                    "lbm_steps_per_step": lbm_steps, "storage": "%s deviation" % sname.lower(),
                    "l2": "working set %.1f GB per time step > L2 (129 MB)" % (
                        BYTES_PER_LU[bdt] * nodes / 1e9),
-                   "parallelism": "independent lattices per GPU (weak scaling)"},
+                   "parallelism": "independent lattices placed on the GPUs by bytes "
+                                  "(weak scaling: 512 lattices per GPU)"},
         "e2e": {"value": round(e2e_value, 1), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h,
+                "ms_per_step": round(e2e_s * 1e3 / args.steps, 3),
+                "api": ("lbm_batch_solve_packed per step (pinned host fields in, moments and "
+                        "drift out), successive solves overlapped, lbm_batch_wait at the end"
+                        if pipelined else "lbm_batch_init_packed, lbm_batch_step, "
+                        "lbm_batch_drift, lbm_batch_moments_packed per step (synchronous)"),
+                # device time of each phase of the last solve (events on the
+                # streams that ran them; the copies overlap the neighbouring
+                # solves' steps)
+                "phases_ms": ({k: round(phases[k], 3) for k in L.BATCH_PHASES} if phases
+                              else None),
+                "h2d_gbs": (round(h2d / max(phases["h2d_ms"], 1e-9) / 1e6, 1) if phases
+                            else None),
+                "d2h_gbs": (round(d2h / max(phases["d2h_ms"], 1e-9) / 1e6, 1) if phases
+                            else None)},
         "roofline": roofline,
         "fp64_plain": fp64,
         "gpu_launches": launches,
@@ -409,34 +451,44 @@ def bench_batched(args, L, torch, rank, ws):
     return line, specs
 
 
-def bench_large(args, L, torch, rank, ws):
-    """One 8192^2 lattice per storage type; prints one line per type."""
-    stream = torch.cuda.current_stream()
-    n = args.size
+def large_one(L, torch, stream, n, dtype, lbm_steps, reps, warmup):
+    """One n x n lattice (optimized rates, device-side Gaussian pulse A = 1e-3,
+    b = 20) in one storage type: `reps` timed runs of lbm_steps steps after
+    `warmup` untimed ones (CUDA events on the launching stream).  Returns
+    (MLUPS, ms per time step)."""
     r = inp.rates("OPT")
-    lines = []
-    peak, peak_kind = peaks()
-    for dtype in args.dtypes.split(","):
-        h = L.lbm_create(n, n, inp.s_ll(r), 1.0, (0.0, 0.0), L.DTYPES[dtype])
+    h = L.lbm_create(n, n, inp.s_ll(r), 1.0, (0.0, 0.0), L.DTYPES[dtype])
+    try:
         L.lbm_set_stream(h, stream)
         L.lbm_init_analytic(h, L.LBM_INIT_GAUSSIAN, (1e-3, 20.0, n / 2, n / 2))
-        lbm_steps = 50 if dtype != "f64" else 10
-        for _ in range(args.warmup):
-            L.lbm_step(h, lbm_steps)
+        for _ in range(warmup):
+            L.lbm_step(h, min(lbm_steps, 50))
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(reps):
             L.lbm_step(h, lbm_steps)
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
+    finally:
         L.lbm_destroy(h)
-        lu = n * n * lbm_steps * args.steps
-        launch_ms = ms / (lbm_steps * args.steps)
+    return n * n * lbm_steps * reps / (ms * 1e-3) / 1e6, ms / (lbm_steps * reps)
+
+
+def bench_large(args, L, torch, rank, ws):
+    """One 8192^2 lattice per storage type; prints one line per type."""
+    stream = torch.cuda.current_stream()
+    n = args.size
+    lines = []
+    peak, peak_kind = peaks()
+    for dtype in args.dtypes.split(","):
+        lbm_steps = 50 if dtype != "f64" else 10
+        mlups, launch_ms = large_one(L, torch, stream, n, dtype, lbm_steps, args.steps,
+                                     args.warmup)
         achieved = BYTES_PER_LU[dtype] * n * n / (launch_ms * 1e-3) / 1e9
-        lines.append({"metric": "MLUPS, single %dx%d lattice" % (n, n), "value": round(lu / ms / 1e3, 1),
+        lines.append({"metric": "MLUPS, single %dx%d lattice" % (n, n), "value": round(mlups, 1),
                       "unit": "MLUPS", "dtype": dtype, "n_gpus": ws, "steps": args.steps,
                       "warmup": args.warmup, "higher_is_better": True,
                       "config": {"workload": "single-%dx%d-%s" % (n, n, dtype)},
@@ -444,6 +496,30 @@ def bench_large(args, L, torch, rank, ws):
                                    "unit": "GB/s", "frac": round(achieved / peak, 4),
                                    "peak_source": peak_kind}})
     return lines
+
+
+def config3_record(L, torch):
+    """Config 3 at its stated size: one 8192^2 lattice, 1000 time steps, per
+    storage type (FP32, FP16, BF16 deviation and plain FP64), each with the
+    roofline of its step kernel (algorithmic bytes per lattice update over
+    the average step time against the measured HBM copy rate; FP64 is bound
+    by GB300's FP64 pipe, its fraction is of the same HBM peak)."""
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = peaks()
+    n, steps = 8192, 1000
+    out = {"workload": "single-8192x8192-1000-steps", "note": "one timed run of 1000 steps "
+           "after 2 x 50 warm-up steps; 2.4-9.7 GB of populations per type (> L2)"}
+    kern = {"f32": "k_step_dev<float>", "f16": "k_step_dev<__half>",
+            "bf16": "k_step_dev<__nv_bfloat16>", "f64": "k_step_f64"}
+    for dtype in ("f32", "f16", "bf16", "f64"):
+        mlups, ms = large_one(L, torch, stream, n, dtype, steps, 1, 2)
+        achieved = BYTES_PER_LU[dtype] * n * n / (ms * 1e-3) / 1e9
+        out[dtype] = {"mlups": round(mlups, 1), "ms_per_lbm_step": round(ms, 4),
+                      "roofline": {"bound": "hbm" if dtype != "f64" else "fp64-alu",
+                                   "kernel": kern[dtype], "achieved": round(achieved, 1),
+                                   "peak": peak, "unit": "GB/s",
+                                   "frac": round(achieved / peak, 4), "peak_source": peak_kind}}
+    return out
 
 
 def bench_serving(args, L, torch):
@@ -457,6 +533,7 @@ def bench_serving(args, L, torch):
     k = 0
     pending = {}
     lat = []
+    failed = 0
     while k < len(reqs) or pending:
         now = time.perf_counter() - t0
         while k < len(reqs) and reqs[k]["arrival"] <= now:
@@ -470,13 +547,12 @@ def bench_serving(args, L, torch):
                                     dtype=q["dtype"], init_kind=kind, init_params=params)
             pending[L.lbm_submit(srv, req)] = q
             k += 1
-        done = []
-        for rid, q in pending.items():
-            rc, _, _, _, latency = L.lbm_poll(srv, rid)
-            if rc == L.LBM_OK:
+        for rid in L.lbm_server_done(srv):
+            try:
+                _, _, _, _, latency = L.lbm_poll(srv, rid)
                 lat.append(latency)
-                done.append(rid)
-        for rid in done:
+            except L.LbmError:
+                failed += 1
             del pending[rid]
         time.sleep(0.002)
     wall = time.perf_counter() - t0
@@ -488,7 +564,12 @@ def bench_serving(args, L, torch):
             "config": {"workload": "serving-poisson-%d-requests" % len(reqs),
                        "policy": args.policy, "max_resident_nodes": args.max_nodes,
                        "hbm_budget_gb": 150, "chunk_steps": 100},
-            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "latency_s": {"p50": round(float(np.percentile(lat, 50)), 3),
+                          "p99": round(float(np.percentile(lat, 99)), 3),
+                          "definition": "submit to moments on the host"},
+            "requests": {"completed": len(lat), "failed": failed},
+            "peak_resident_lattices": st["peak_resident"],
+            "wall_s": round(wall, 2),
             "server": st}
 
 
@@ -732,6 +813,20 @@ def main():
             print(json.dumps(bench_source(args, L, torch)))
         return
     line, specs = bench_batched(args, L, torch, rank, ws)
+    if rank == 0 and ws == 1 and not args.no_extras:
+        # the other workloads at their stated sizes, as extra keys of the one
+        # line: the batch in FP16 deviation storage, config 3 per storage
+        # type, config 5 serving
+        sub = parse(["--batch-dtype", "f16", "--steps", str(max(3, min(args.steps, 5))),
+                     "--warmup", "3", "--no-fp64"])
+        f16, _ = bench_batched(sub, L, torch, rank, ws)
+        line["batch_fp16"] = {k: f16[k] for k in ("value", "unit", "ms_per_step", "roofline",
+                                                  "e2e", "clocks")}
+        line["batch_fp16"]["workload"] = f16["config"]["workload"]
+        line["config3_large"] = config3_record(L, torch)
+        srv = parse(["--workload", "serving", "--policy", "shortest",
+                     "--max-nodes", str(1 << 27), "--requests", str(args.requests)])
+        line["config5_serving"] = bench_serving(srv, L, torch)
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
             mlups, cores, sample = cpu_oracle_mlups(specs)

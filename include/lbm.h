@@ -184,7 +184,10 @@ int lbm_sync(lbm_handle h);
 /* Global sums over the lattice in FP64, by a deterministic two-stage
  * reduction on the device: out[0] = sum rho', out[1] = sum jx',
  * out[2] = sum jy' (deviations from rho0, rho0 u0), out[3] = number of
- * non-finite stored populations.  The collision conserves mass and
+ * non-finite stored populations.  Each node's sums are taken over the
+ * populations' deviations from the base f^eq(rho0, j0) (stored as such by
+ * the deviation types; formed exactly from FP64 populations near the base),
+ * so they round at the size of the perturbation.  The collision conserves mass and
  * momentum exactly in exact arithmetic (section 2.1,
  * Eq. eq_conservative), so out[0..2] measure rounding drift.
  * Synchronizes; returns LBM_EUNSTABLE when out[3] > 0. */
@@ -199,7 +202,9 @@ int lbm_drift(lbm_handle h, double out[4]);
  * acceptable.
  *   f_dev   device array of 9 x ny x nx doubles (index (i*ny + y)*nx + x),
  *           owned by the caller, unchanged
- *   rho0, jx0, jy0  reference state subtracted at every node
+ *   rho0, jx0, jy0  reference state: its equilibrium populations
+ *           f^eq(rho0, j0) are subtracted from every node's populations
+ *           before the sums, as lbm_drift does
  *   out     host array of 4 doubles, owned by the caller: sum rho',
  *           sum jx', sum jy', number of non-finite populations
  *   stream  cudaStream_t to run on (NULL: the legacy default stream);
@@ -362,6 +367,44 @@ int lbm_batch_init_packed(lbm_batch b, const double *rho, const double *ux,
                           const double *uy);
 int lbm_batch_moments_packed(lbm_batch b, double *rho, double *ux, double *uy);
 
+/* (runtime; no counterpart in the paper) One whole solve of every member,
+ * queued without waiting: upload the packed fields (layout of
+ * lbm_batch_init_packed), set every member to f^eq(rho, u) (section 2.3),
+ * advance n time steps (section 2.1, Eq. blbs), take every member's drift
+ * sums (as lbm_batch_drift) and download the packed moments (as
+ * lbm_batch_moments_packed).  Returns once the work is queued.  Successive
+ * solves of a batch overlap: solve k's upload and solve k-1's download run
+ * on two copy streams of the batch while solve k-1 and solve k step, through
+ * two device staging slots (4 x 3 x nodes doubles in all, allocated on the
+ * first call and kept until lbm_batch_destroy).  Results equal those of
+ * lbm_batch_init_packed + lbm_batch_step + lbm_batch_drift +
+ * lbm_batch_moments_packed bit for bit.
+ *   rho_in, ux_in, uy_in    host arrays of the batch's node count (packed
+ *                           member after member, each ny x nx row-major),
+ *                           read by the upload; page-locked for overlap
+ *   rho_out, ux_out, uy_out host arrays of the same size, written by the
+ *                           download; page-locked (a copy into pageable
+ *                           memory blocks the call until it lands, which
+ *                           leaves nothing to overlap)
+ *   drift_out               host array of 4 doubles per member, or NULL
+ *                           (any host memory: the sums pass through a
+ *                           page-locked array of the batch)
+ * The caller owns every host array and must neither free nor change the
+ * inputs, nor read the outputs, before lbm_batch_wait returns.  Invalid
+ * fields (non-finite, rho <= 0) and non-finite populations are reported by
+ * lbm_batch_wait.  FP16 members are refused (LBM_EINVAL): their storage
+ * scale is chosen on the host from the fields (use lbm_batch_init_packed). */
+int lbm_batch_solve_packed(lbm_batch b, long n, const double *rho_in, const double *ux_in,
+                           const double *uy_in, double *rho_out, double *ux_out,
+                           double *uy_out, double *drift_out);
+/* Wait for every solve queued by lbm_batch_solve_packed.  phase_ms (may be
+ * NULL) receives 6 device times of the last solve, in ms, measured by events
+ * on the streams that ran them: upload, init, steps, drift, moments,
+ * download.  Returns LBM_EINVAL if any solve since the last wait had invalid
+ * fields (message names the member), LBM_EUNSTABLE if a drift array passed
+ * since then reports non-finite populations, else 0. */
+int lbm_batch_wait(lbm_batch b, double *phase_ms);
+
 /* As lbm_tune for the batch's launches (one variant for all its storage
  * types; the first lbm_batch_step of a batch of >= 2^20 nodes tunes unless
  * LBM_AUTOTUNE=0).  Batches have LBM_BATCH_TUNE_VARIANTS variants: the
@@ -449,6 +492,70 @@ typedef struct {
   double busy_s;            /* wall time with work on the device          */
 } lbm_server_stats_t;
 int lbm_server_stats(lbm_server s, lbm_server_stats_t *out);
+
+/* ------------------------------------------------------------------
+ * One periodic lattice split into y-slabs (multi-device decomposition).
+ * The periodic lattice of section 2.1 (Eq. blbs and its lattice-closure
+ * condition) couples row y only to rows y - 1 and y + 1, so a lattice can be
+ * cut into slabs of whole rows, each stepped by its own device: per step
+ * and slab boundary only the three populations that cross it move (c_y = +1,
+ * i = 2, 5, 6 upwards; c_y = -1, i = 4, 7, 8 downwards), one row each.  Each
+ * slab stores one halo row below and above its rows.  Results equal those of
+ * the unsplit lattice bit for bit.  FP64, FP32 and BF16 storage (FP16 slabs
+ * would need one storage scale for the whole lattice: LBM_EINVAL).
+ *
+ * lbm_slabs_create -- nslabs >= 1 slabs of an nx x ny lattice (arguments of
+ * lbm_create); slab k owns rows [floor(k ny / nslabs), floor((k+1) ny /
+ * nslabs)), on device devices[k] (NULL: all on the current device).  The
+ * halo exchange after each step is a set of device-to-device (peer) copies
+ * on a copy stream per slab, overlapped with the slab's interior rows (its
+ * two boundary rows run first).  The group owns all device memory.
+ * init_field / moments take whole-lattice host arrays (ny x nx), get / set
+ * populations 9 x ny x nx ones, as the single-lattice calls; drift sums the
+ * slabs' drifts in slab order.  Not thread-safe. */
+typedef struct lbm_slabs_ctx *lbm_slabs;
+int lbm_slabs_create(int nx, int ny, const double S[9], double rho0, const double u0[2],
+                     int storage_dtype, int nslabs, const int *devices, lbm_slabs *out);
+int lbm_slabs_rows(lbm_slabs s, int k, int *y0, int *rows, int *device);
+int lbm_slabs_init_field(lbm_slabs s, const double *rho, const double *ux, const double *uy);
+int lbm_slabs_set_populations(lbm_slabs s, const double *f);
+int lbm_slabs_step(lbm_slabs s, long n);
+int lbm_slabs_moments(lbm_slabs s, double *rho, double *ux, double *uy);
+int lbm_slabs_get_populations(lbm_slabs s, double *f);
+int lbm_slabs_drift(lbm_slabs s, double out[4]);
+int lbm_slabs_destroy(lbm_slabs s);
+
+/* One slab per process (the caller moves the halo rows, e.g. by NCCL
+ * send / recv between ranks).  lbm_slab_create makes a handle for rows
+ * [y0, y0 + rows) of an nx x ny_total periodic lattice; lbm_init_field,
+ * lbm_set_populations, lbm_moments, lbm_get_populations and lbm_drift take
+ * that slab's rows (rows x nx host arrays), lbm_step takes at most one step
+ * per call, and analytic fields, point sources and batches are refused.
+ * Between steps, and once after every init / set_populations with
+ * reverse = 1, each rank calls
+ *   lbm_slab_pack(h, reverse, to_below, to_above)
+ * which copies its outgoing rows into two device buffers of
+ * lbm_slab_halo_bytes bytes each (one part for the lower neighbour, slab
+ * rows below y0 cyclically, one for the upper), sends to_below to the lower
+ * neighbour and to_above to the upper one, receives their parts and calls
+ *   lbm_slab_unpack(h, reverse, from_below, from_above)
+ * (from_below: what the lower neighbour sent upwards).  reverse = 0 after a
+ * step: halo rows take the neighbours' boundary rows; reverse = 1 after an
+ * initialisation: the boundary slots that the neighbours' nodes initialised
+ * come back.  Both calls are enqueued on the handle's stream
+ * (lbm_set_stream) and do not synchronize. */
+int lbm_slab_create(int nx, int ny_total, int y0, int rows, const double S[9], double rho0,
+                    const double u0[2], int storage_dtype, lbm_handle *out);
+int lbm_slab_halo_bytes(lbm_handle h, size_t *bytes);
+int lbm_slab_pack(lbm_handle h, int reverse, void *to_below, void *to_above);
+int lbm_slab_unpack(lbm_handle h, int reverse, const void *from_below, const void *from_above);
+
+/* (runtime; no counterpart in the paper) Ids of requests that finished
+ * (completed or failed) since the previous call, in finishing order: up to
+ * cap ids are written to ids and their number to *count; the rest are kept
+ * for the next call.  Lets a client poll only finished requests instead of
+ * every pending one.  Thread-safe. */
+int lbm_server_done(lbm_server s, long long *ids, int cap, int *count);
 
 /* Stop admitting, wait for admitted work, free everything. */
 int lbm_server_destroy(lbm_server s);

@@ -27,6 +27,7 @@ UNITS = {
     "io_dev.cu": [],
     "serve.cu": [],
     "drift_noalloc.cu": [],
+    "slabs.cu": [],
     "vn.cu": [],
     "optcost.cu": [],
 }

@@ -124,7 +124,7 @@ __global__ void k_init_eq(AuxView a, const double *rho, const double *ux, const 
     feq_canonical(r, u, v, f);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.ny);
+      const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.nyw);
       store_value(a, (long long)i * a.g.plane + (long long)ys * a.g.rstride + xs, i, f[i]);
     }
   }
@@ -139,7 +139,7 @@ __global__ void k_force_node(AuxView a, int x, int y, NodePops fs) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.ny);
+    const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.nyw);
     store_value(a, (long long)i * a.g.plane + (long long)ys * a.g.rstride + xs, i, fs.f[i]);
   }
 }
@@ -158,7 +158,7 @@ __global__ void k_force_node_tab(AuxView a, int x, int y, const double *fs) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.ny);
+    const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.nyw);
     store_value(a, (long long)i * a.g.plane + (long long)ys * a.g.rstride + xs, i, fs[i]);
   }
 }
@@ -189,7 +189,7 @@ __global__ void k_maxdev_eq(AuxView a, const double *rho, const double *ux, cons
 __device__ __forceinline__ void gather(const AuxView &a, int x, int y, double f[9]) {
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.ny);
+    const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.nyw);
     f[i] = load_stored(a, (long long)i * a.g.plane + (long long)ys * a.g.rstride + xs);
   }
 }
@@ -234,7 +234,7 @@ __global__ void k_set_pop(AuxView a, const double *f) {
     const int x = (int)(n % a.g.nx), y = (int)(n / a.g.nx);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.ny);
+      const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.nyw);
       store_value(a, (long long)i * a.g.plane + (long long)ys * a.g.rstride + xs, i, f[i * N + n]);
     }
   }
@@ -288,15 +288,19 @@ struct FF {
 __device__ __forceinline__ void node_sums(const AuxView &a, long long off, double &r, double &jx,
                                           double &jy, double &bad) {
   if (a.dtype == LBM_F64) {
-    double f[9];
+    // deviations from the base populations first: f_i - f0_i is exact while
+    // f_i stays within a factor two of f0_i (Sterbenz), so the node's sums
+    // round at the size of the perturbation, not at the size of f
+    double d[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      f[i] = static_cast<const double *>(a.buf)[(long long)i * a.g.plane + off];
-      if (!isfinite(f[i])) { bad += 1.0; f[i] = 0.0; }
+      const double v = static_cast<const double *>(a.buf)[(long long)i * a.g.plane + off];
+      if (!isfinite(v)) { bad += 1.0; d[i] = 0.0; }
+      else d[i] = v - a.f0[i];
     }
-    r = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8] - a.rho0;
-    jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8] - a.jx0;
-    jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8] - a.jy0;
+    r = d[0] + d[1] + d[2] + d[3] + d[4] + d[5] + d[6] + d[7] + d[8];
+    jx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
+    jy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
     return;
   }
   float f[9];
@@ -480,6 +484,19 @@ cudaError_t launch_drift(const AuxView &a, double *partials, double *out, cudaSt
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_drift2<<<1, DRIFT_BLOCKS, 0, st>>>(partials, out);
+  return cudaGetLastError();
+}
+
+// acc[i] += add[i] for i < n (the pipelined batch solves' invalid-field
+// totals)
+__global__ void k_add_u32(unsigned int *acc, const unsigned int *add, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) acc[i] += add[i];
+}
+
+cudaError_t launch_add_u32(unsigned int *acc, const unsigned int *add, int n, cudaStream_t st) {
+  if (n < 1) return cudaSuccess;
+  k_add_u32<<<(n + 255) / 256, 256, 0, st>>>(acc, add, n);
   return cudaGetLastError();
 }
 

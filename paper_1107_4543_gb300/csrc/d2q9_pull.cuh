@@ -184,6 +184,10 @@ struct Geom {
   int nx, ny, pitch;  // pitch: elements per row of one plane (a multiple of 128 bytes)
   int nchunks;      // real vectors per row: ceil(nx / V)
   int cpr;          // chunk slots per row: pitch / V (>= nchunks)
+  // y extent of the periodic wrap: ny for a whole periodic lattice; 0 for a
+  // slab of rows whose neighbouring rows y = -1 and y = ny are stored halo
+  // rows (the wrap is then the identity)
+  int nyw;
   long long plane;    // offset between planes i and i + 1 (elements)
   long long rstride;  // offset between rows y and y + 1 of one plane (elements)
   // element (i, y, x) lives at i * plane + y * rstride + x
@@ -208,6 +212,7 @@ inline Geom make_geom(int nx, int ny, int V, int esize) {
   const int abytes = esize == 2 ? 64 : 128;
   const int align = V > abytes / esize ? V : abytes / esize;
   g.pitch = (nx + align - 1) / align * align;
+  g.nyw = ny;
   g.nchunks = (nx + V - 1) / V;
   g.cpr = g.pitch / V;  // whole lines of chunks: tasks start on lines
   // row-interleaved planes: row y of planes 0..8 lie back to back, so the
@@ -290,7 +295,7 @@ __device__ __forceinline__ void pull9(const T *__restrict__ src, const Geom &g,
   for (int i = 0; i < 9; ++i) {
     const int cx = CXd(i), cy = CYd(i);
     int ys = p.y - cy;
-    ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
+    ys = ys < 0 ? ys + g.nyw : (ys >= g.nyw ? ys - g.nyw : ys);
     const T *row = src + (long long)i * g.plane + (long long)ys * g.rstride;
     raw[i] = p.active ? __ldg(reinterpret_cast<const RawT *>(row + p.x0)) : Elem<T>::R::zero();
     edge[i] = C(0);
@@ -384,7 +389,7 @@ __device__ __forceinline__ void pull9_packed(const T *__restrict__ src, const Ge
   for (int i = 0; i < 9; ++i) {
     const int cx = CXd(i), cy = CYd(i);
     int ys = p.y - cy;
-    ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
+    ys = ys < 0 ? ys + g.nyw : (ys >= g.nyw ? ys - g.nyw : ys);
     const T *row = src + (long long)i * g.plane + (long long)ys * g.rstride;
     raw[i] = p.active ? __ldg(reinterpret_cast<const RawT *>(row + p.x0)) : Elem<T>::R::zero();
     edge[i] = 0u;

@@ -49,10 +49,16 @@ cudaError_t noalloc_scratch(int dev, double **out) {
   return cudaSuccess;
 }
 
-// one block per row: the row's nodes in a fixed order, then a fixed tree
+// base populations f^eq(rho0, j0), subtracted population by population
+struct Base {
+  double f0[9];
+};
+
+// one block per row: the row's nodes in a fixed order, then a fixed tree.
+// Each node's sums are taken over the deviations f_i - f0_i (exact while
+// f_i stays within a factor two of f0_i), as lbm_drift takes them.
 __global__ void __launch_bounds__(LBM_NOALLOC_THREADS)
-k_drift_rows(const double *__restrict__ f, int nx, int ny, double rho0, double jx0, double jy0,
-             double *scratch) {
+k_drift_rows(const double *__restrict__ f, int nx, int ny, Base base, double *scratch) {
   __shared__ double sh[4][LBM_NOALLOC_THREADS];
   const int y = blockIdx.x;
   const long long plane = (long long)nx * ny;
@@ -62,15 +68,17 @@ k_drift_rows(const double *__restrict__ f, int nx, int ny, double rho0, double j
     double g[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      g[i] = f[i * plane + n];
-      if (!isfinite(g[i])) {
+      const double v = f[i * plane + n];
+      if (!isfinite(v)) {
         bad += 1.0;
         g[i] = 0.0;
+      } else {
+        g[i] = v - base.f0[i];
       }
     }
-    s0 += (g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8]) - rho0;
-    s1 += (g[1] - g[3] + g[5] - g[6] - g[7] + g[8]) - jx0;
-    s2 += (g[2] - g[4] + g[5] + g[6] - g[7] - g[8]) - jy0;
+    s0 += g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
+    s1 += g[1] - g[3] + g[5] - g[6] - g[7] + g[8];
+    s2 += g[2] - g[4] + g[5] + g[6] - g[7] - g[8];
   }
   sh[0][threadIdx.x] = s0;
   sh[1][threadIdx.x] = s1;
@@ -127,7 +135,9 @@ extern "C" int lbm_drift_pop_noalloc(const double *f_dev, int nx, int ny, double
   if (e == cudaSuccess) e = noalloc_scratch(dev, &scratch);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (e == cudaSuccess) {
-    k_drift_rows<<<ny, LBM_NOALLOC_THREADS, 0, st>>>(f_dev, nx, ny, rho0, jx0, jy0, scratch);
+    Base base;
+    lbm::host_feq_j(rho0, jx0, jy0, base.f0);
+    k_drift_rows<<<ny, LBM_NOALLOC_THREADS, 0, st>>>(f_dev, nx, ny, base, scratch);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {

@@ -99,26 +99,33 @@ __device__ __forceinline__ double decode<__nv_bfloat16>(__nv_bfloat16 s, double)
 // Population i of node x goes to slot x - c_i, where the next step's pull
 // (f_i(x) = P_i(x - c_i)) reads it.  bad counts nodes whose field is not
 // finite or has rho <= 0.
+// one node of the equilibrium init: the deviations of f^eq(r, (u, v)) into
+// the slots the next pull reads; returns whether the field is invalid
+template <typename T>
+__device__ __forceinline__ bool init_node(const AuxView &a, const RefState &R, int x, int y,
+                                          double r, double u, double v) {
+  T *buf = static_cast<T *>(a.buf);
+  double d[9];
+  feq_deviation(R, r, u, v, d);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int xs = wrap(x - CXd(i), a.g.nx), ys = wrap(y - CYd(i), a.g.nyw);
+    buf[(long long)i * a.g.plane + (long long)ys * a.g.rstride + xs] = encode<T>(d[i], a.scale);
+  }
+  return !(r > 0.0) || !isfinite(r) || !isfinite(u) || !isfinite(v);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_init_dev(AuxView a, RefState R, const double *rho,
                                                   const double *ux, const double *uy,
                                                   unsigned int *bad) {
   const int nx = a.g.nx, ny = a.g.ny;
   const long long N = (long long)nx * ny;
-  T *buf = static_cast<T *>(a.buf);
   unsigned int nbad = 0;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(n / nx), x = (int)(n - (long long)y * nx);
-    const double r = rho[n], u = ux[n], v = uy[n];
-    if (!(r > 0.0) || !isfinite(r) || !isfinite(u) || !isfinite(v)) ++nbad;
-    double d[9];
-    feq_deviation(R, r, u, v, d);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const int xs = wrap(x - CXd(i), nx), ys = wrap(y - CYd(i), ny);
-      buf[(long long)i * a.g.plane + (long long)ys * a.g.rstride + xs] = encode<T>(d[i], a.scale);
-    }
+    if (init_node<T>(a, R, x, y, rho[n], ux[n], uy[n])) ++nbad;
   }
   if (bad && nbad) atomicAdd(bad, nbad);
 }
@@ -140,29 +147,104 @@ __global__ void __launch_bounds__(256) k_maxdev_dev(AuxView a, RefState R, const
 
 // rho = rho0 + sum f', j = j0 + sum c f' of the pre-collision populations
 // f_i(x) = P_i(x - c_i); u = j / rho
+// rho, u of node (x, y) from its pre-collision populations
+template <typename T>
+__device__ __forceinline__ void moments_node(const AuxView &a, int x, int y, double inv_scale,
+                                             double &r, double &u, double &v) {
+  const T *buf = static_cast<const T *>(a.buf);
+  double f[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int xs = wrap(x - CXd(i), a.g.nx), ys = wrap(y - CYd(i), a.g.nyw);
+    f[i] = decode<T>(buf[(long long)i * a.g.plane + (long long)ys * a.g.rstride + xs], inv_scale);
+  }
+  r = a.rho0 + (f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8]);
+  const double jx = a.jx0 + (f[1] - f[3] + f[5] - f[6] - f[7] + f[8]);
+  const double jy = a.jy0 + (f[2] - f[4] + f[5] + f[6] - f[7] - f[8]);
+  const double inv = 1.0 / r;
+  u = jx * inv;
+  v = jy * inv;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_moments_dev(AuxView a, double *rho, double *ux,
                                                      double *uy) {
   const int nx = a.g.nx, ny = a.g.ny;
   const long long N = (long long)nx * ny;
-  const T *buf = static_cast<const T *>(a.buf);
   const double inv_scale = 1.0 / a.scale;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(n / nx), x = (int)(n - (long long)y * nx);
-    double f[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const int xs = wrap(x - CXd(i), nx), ys = wrap(y - CYd(i), ny);
-      f[i] = decode<T>(buf[(long long)i * a.g.plane + (long long)ys * a.g.rstride + xs], inv_scale);
-    }
-    const double r = a.rho0 + (f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8]);
-    const double jx = a.jx0 + (f[1] - f[3] + f[5] - f[6] - f[7] + f[8]);
-    const double jy = a.jy0 + (f[2] - f[4] + f[5] + f[6] - f[7] - f[8]);
-    const double inv = 1.0 / r;
-    rho[n] = r;
-    ux[n] = jx * inv;
-    uy[n] = jy * inv;
+    moments_node<T>(a, x, y, inv_scale, rho[n], ux[n], uy[n]);
+  }
+}
+
+// Batched forms: block b covers nodes [start, start + count) of member
+// blocks[b].member, whose fields sit at poff[member] of the packed arrays
+// (rho at `stage`, ux at stage + total, uy at stage + 2 total).  The
+// per-node arithmetic is that of the single-lattice kernels.
+__device__ __forceinline__ RefState ref_of(const AuxView &a) {
+  RefState r;
+  r.rho0 = a.rho0;
+  r.jx0 = a.jx0;
+  r.jy0 = a.jy0;
+  r.axx0 = a.jx0 * a.jx0 / a.rho0;
+  r.ayy0 = a.jy0 * a.jy0 / a.rho0;
+  r.axy0 = a.jx0 * a.jy0 / a.rho0;
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void batch_init_block(const AuxView &a, const IoBlock &B,
+                                                 const double *r_, const double *u_,
+                                                 const double *v_, unsigned int *bad) {
+  const RefState R = ref_of(a);
+  unsigned int nbad = 0;
+  for (int j = threadIdx.x; j < B.count; j += blockDim.x) {
+    const long long n = B.start + j;
+    const int y = (int)(n / a.g.nx), x = (int)(n - (long long)y * a.g.nx);
+    if (init_node<T>(a, R, x, y, r_[n], u_[n], v_[n])) ++nbad;
+  }
+  if (nbad) atomicAdd(bad + B.member, nbad);
+}
+
+__global__ void __launch_bounds__(256) k_batch_init_dev(const AuxView *__restrict__ views,
+                                                        const IoBlock *__restrict__ blocks,
+                                                        const long long *__restrict__ poff,
+                                                        long long total, const double *stage,
+                                                        unsigned int *bad) {
+  const IoBlock B = blocks[blockIdx.x];
+  const AuxView &a = views[B.member];
+  const double *r = stage + poff[B.member];
+  switch (a.dtype) {
+    case LBM_F32DEV: batch_init_block<float>(a, B, r, r + total, r + 2 * total, bad); break;
+    case LBM_F16DEV: batch_init_block<__half>(a, B, r, r + total, r + 2 * total, bad); break;
+    default: batch_init_block<__nv_bfloat16>(a, B, r, r + total, r + 2 * total, bad); break;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void batch_moments_block(const AuxView &a, const IoBlock &B,
+                                                    double *r_, double *u_, double *v_) {
+  const double inv_scale = 1.0 / a.scale;
+  for (int j = threadIdx.x; j < B.count; j += blockDim.x) {
+    const long long n = B.start + j;
+    const int y = (int)(n / a.g.nx), x = (int)(n - (long long)y * a.g.nx);
+    moments_node<T>(a, x, y, inv_scale, r_[n], u_[n], v_[n]);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_batch_moments_dev(const AuxView *__restrict__ views,
+                                                           const IoBlock *__restrict__ blocks,
+                                                           const long long *__restrict__ poff,
+                                                           long long total, double *stage) {
+  const IoBlock B = blocks[blockIdx.x];
+  const AuxView &a = views[B.member];
+  double *r = stage + poff[B.member];
+  switch (a.dtype) {
+    case LBM_F32DEV: batch_moments_block<float>(a, B, r, r + total, r + 2 * total); break;
+    case LBM_F16DEV: batch_moments_block<__half>(a, B, r, r + total, r + 2 * total); break;
+    default: batch_moments_block<__nv_bfloat16>(a, B, r, r + total, r + 2 * total); break;
   }
 }
 
@@ -200,6 +282,23 @@ cudaError_t launch_maxdev_dev(const AuxView &a, const double *rho, const double 
   cudaError_t e = cudaMemsetAsync(max_bits, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
   k_maxdev_dev<<<grid_for(N), 256, 0, st>>>(a, make_ref(a), rho, ux, uy, max_bits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_init_dev(const AuxView *views, const IoBlock *blocks, long long nblocks,
+                                  const long long *poff, long long total, const double *stage,
+                                  unsigned int *bad, int members, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned int) * members, st);
+  if (e != cudaSuccess || nblocks < 1) return e;
+  k_batch_init_dev<<<(unsigned)nblocks, 256, 0, st>>>(views, blocks, poff, total, stage, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_moments_dev(const AuxView *views, const IoBlock *blocks,
+                                     long long nblocks, const long long *poff, long long total,
+                                     double *stage, cudaStream_t st) {
+  if (nblocks < 1) return cudaSuccess;
+  k_batch_moments_dev<<<(unsigned)nblocks, 256, 0, st>>>(views, blocks, poff, total, stage);
   return cudaGetLastError();
 }
 

@@ -70,16 +70,6 @@ int sm_count() {
   return n;
 }
 
-struct DevGuard {
-  int prev = -1, want;
-  explicit DevGuard(int d) : want(d) {
-    if (cudaGetDevice(&prev) == cudaSuccess && prev != d) cudaSetDevice(d);
-  }
-  ~DevGuard() {
-    if (prev >= 0 && prev != want) cudaSetDevice(prev);
-  }
-};
-
 }  // namespace lbm
 
 using namespace lbm;
@@ -96,6 +86,9 @@ struct lbm_ctx {
   double *partials = nullptr, *drift_out = nullptr;
   unsigned int *maxbits = nullptr;
   double *stage = nullptr;  // 3 * N doubles, lazily allocated
+  void *alloc[2] = {nullptr, nullptr};  // the buffers' allocations (one halo row
+                                        // before L.buf[k] for slabs)
+  bool slab = false;  // rows of a larger lattice, with halo rows (slabs.cu)
   size_t bytes = 0;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
@@ -522,10 +515,19 @@ int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void *ctx) {
   return LBM_OK;
 }
 
-int lbm_create(int nx, int ny, const double S[9], double rho0, const double u0[2],
-               int storage_dtype, lbm_handle *out) {
+}  // extern "C"
+
+namespace lbm {
+// lbm_create, or (halo) a slab of ny rows of a larger periodic lattice: its
+// buffers get one stored row below row 0 and one above row ny - 1, and the
+// geometry's y wrap is the identity (Geom::nyw = 0), so the pull reads the
+// neighbouring slabs' rows from those halo rows.
+int create_lattice(int nx, int ny, const double S[9], double rho0, const double u0[2],
+                   int storage_dtype, bool halo, lbm_handle *out) {
   REQUIRE(out != nullptr && S != nullptr && u0 != nullptr, "null argument");
-  REQUIRE(nx >= 2 && ny >= 2, "nx and ny must be >= 2");
+  // a slab of a larger lattice may be one row high (its halo rows hold the
+  // neighbouring rows)
+  REQUIRE(nx >= 2 && ny >= (halo ? 1 : 2), "nx and ny must be >= 2");
   REQUIRE((long long)nx * ny <= (1LL << 40), "lattice too large");
   REQUIRE(rho0 > 0.0 && isfinite(rho0), "rho0 must be positive");
   REQUIRE(isfinite(u0[0]) && isfinite(u0[1]), "u0 must be finite");
@@ -548,6 +550,8 @@ int lbm_create(int nx, int ny, const double S[9], double rho0, const double u0[2
   }
   h->device = dev;
   h->L.g = make_geom(nx, ny, V, esize);
+  if (halo) h->L.g.nyw = 0;
+  h->slab = halo;
   h->L.dtype = storage_dtype;
   h->L.V = V;
   h->L.variant = default_variant(storage_dtype);
@@ -597,9 +601,13 @@ int lbm_create(int nx, int ny, const double S[9], double rho0, const double u0[2
   fp.s7 = h->S_paper[7];
   fp.s8 = h->S_paper[8];
 
-  const size_t buf_bytes = (size_t)9 * h->L.g.pitch * h->L.g.ny * esize;
-  h->L.buf[0] = dev_alloc(buf_bytes);
-  h->L.buf[1] = dev_alloc(buf_bytes);
+  const size_t row_bytes = (size_t)9 * h->L.g.pitch * esize;
+  const size_t buf_bytes = row_bytes * (h->L.g.ny + (halo ? 2 : 0));
+  for (int k = 0; k < 2; ++k) {
+    h->alloc[k] = dev_alloc(buf_bytes);
+    h->L.buf[k] = h->alloc[k] && halo ? static_cast<char *>(h->alloc[k]) + row_bytes
+                                      : h->alloc[k];
+  }
   h->partials = (double *)dev_alloc(sizeof(double) * 4 * drift_blocks());
   h->drift_out = (double *)dev_alloc(sizeof(double) * 4);
   h->maxbits = (unsigned int *)dev_alloc(sizeof(unsigned int));
@@ -617,8 +625,8 @@ int lbm_create(int nx, int ny, const double S[9], double rho0, const double u0[2
   }
   h->stream = h->own_stream;
   // start from the uniform equilibrium f^eq(rho0, u0)
-  if (cudaMemsetAsync(h->L.buf[0], 0, buf_bytes, h->stream) != cudaSuccess ||
-      cudaMemsetAsync(h->L.buf[1], 0, buf_bytes, h->stream) != cudaSuccess) {
+  if (cudaMemsetAsync(h->alloc[0], 0, buf_bytes, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->alloc[1], 0, buf_bytes, h->stream) != cudaSuccess) {
     cudaGetLastError();
     lbm_destroy(h);
     set_error("memset failed");
@@ -641,14 +649,32 @@ int lbm_create(int nx, int ny, const double S[9], double rho0, const double u0[2
   return LBM_OK;
 }
 
+Lattice &lattice_of(lbm_handle h) { return h->L; }
+int block_of(lbm_handle h) { return h->block; }
+bool is_slab(lbm_handle h) { return h->slab; }
+cudaStream_t stream_of(lbm_handle h) { return h->stream; }
+int device_of(lbm_handle h) { return h->device; }
+void advance_one(lbm_handle h) {
+  h->L.cur ^= 1;
+  h->t += 1;
+}
+}  // namespace lbm
+
+extern "C" {
+
+int lbm_create(int nx, int ny, const double S[9], double rho0, const double u0[2],
+               int storage_dtype, lbm_handle *out) {
+  return create_lattice(nx, ny, S, rho0, u0, storage_dtype, false, out);
+}
+
 int lbm_destroy(lbm_handle h) {
   if (!h) return LBM_EINVAL;
   DevGuard g(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   free_graph(h);
   dev_free(h->src_tab);
-  dev_free(h->L.buf[0]);
-  dev_free(h->L.buf[1]);
+  dev_free(h->alloc[0]);
+  dev_free(h->alloc[1]);
   dev_free(h->partials);
   dev_free(h->drift_out);
   dev_free(h->maxbits);
@@ -705,6 +731,7 @@ int lbm_init_field(lbm_handle h, const double *rho, const double *ux, const doub
 
 int lbm_init_analytic(lbm_handle h, int kind, const double params[8]) {
   REQUIRE(h && params, "null argument");
+  REQUIRE(!h->slab, "analytic fields are defined on whole lattices; give a slab its rows' fields");
   REQUIRE(kind == LBM_INIT_GAUSSIAN || kind == LBM_INIT_PLANE, "unknown init kind");
   for (int k = 0; k < 8; ++k) REQUIRE(isfinite(params[k]), "params must be finite");
   if (kind == LBM_INIT_GAUSSIAN) REQUIRE(params[1] > 0.0, "half-width must be positive");
@@ -716,6 +743,7 @@ int lbm_step(lbm_handle h, long n) {
   NvtxRange nvtx("lbm_step");
   REQUIRE(h != nullptr, "null handle");
   REQUIRE(n >= 0, "negative step count");
+  REQUIRE(!h->slab || n <= 1, "a slab takes one step between halo exchanges");
   REQUIRE(h->batch == nullptr, "lattice is a batch member; step the batch");
   DevGuard g(h->device);
   if (n > 0) {
@@ -779,6 +807,7 @@ int lbm_step(lbm_handle h, long n) {
 
 int lbm_set_source(lbm_handle h, int x, int y, double amplitude, double period) {
   REQUIRE(h != nullptr, "null handle");
+  REQUIRE(!h->slab, "no point source on a slab");
   REQUIRE(x >= 0 && x < h->L.g.nx && y >= 0 && y < h->L.g.ny, "source outside the lattice");
   REQUIRE(isfinite(amplitude) && isfinite(period) && period > 0, "bad source amplitude or period");
   REQUIRE(h->batch == nullptr, "lattice is a batch member");
@@ -942,8 +971,9 @@ struct lbm_batch_ctx {
   double *dpart = nullptr, *dout = nullptr;
   unsigned int *dflags = nullptr;         // per-member counters (2 per member)
   int parity = 0;                        // steps taken mod 2
-  cudaGraphExec_t graph = nullptr;
-  int graph_steps = 0;
+  // captured step sequences, keyed by step count, each starting at batch
+  // parity 0 (64 steps, and the remainders of longer calls)
+  std::map<long, cudaGraphExec_t> graphs;
   int block = 64;                        // threads per block (see lbm_ctx::block)
   int variant = 2;                       // launch variant (tuner)
   bool tuned = false;
@@ -957,6 +987,40 @@ struct lbm_batch_ctx {
   // pstage holds rho, ux, uy of all members (3 x nodes doubles, lazily)
   std::vector<size_t> poff;
   double *pstage = nullptr;
+  // pipelined solves (lbm_batch_solve_packed / lbm_batch_wait): two slots,
+  // each with device staging for the fields in and the moments out and its
+  // own drift sums, so that solve k's upload (copy stream `up`) and solve
+  // k-1's download (copy stream `down`) run while the batch stream steps.
+  // Events per slot, in stream order: up stream E_UP0 .. E_UP1 (H2D); batch
+  // stream E_B0 (upload landed), E_INIT, E_STEP, E_DRIFT, E_MOM; down stream
+  // E_DN0 .. E_DN1 (D2H).
+  enum { E_UP0, E_UP1, E_B0, E_INIT, E_STEP, E_DRIFT, E_MOM, E_DN0, E_DN1, E_COUNT };
+  // The caller's drift array may be pageable memory, and a copy into
+  // pageable memory would block the host until the solve ends (which
+  // serialises the next solve's upload behind it): the sums land in a
+  // page-locked array of the slot and a host function on the download
+  // stream copies them out.
+  struct DriftOut {
+    double *dst = nullptr;
+    const double *src = nullptr;
+    size_t bytes = 0;
+  };
+  struct Slot {
+    double *in = nullptr, *out = nullptr;  // 3 x nodes doubles each
+    double *dout = nullptr;                // drift sums, 4 per member
+    double *hdrift = nullptr;              // page-locked copy of dout
+    cudaEvent_t ev[E_COUNT] = {};
+    bool used = false;
+  };
+  Slot slot[2];
+  cudaStream_t up = nullptr, down = nullptr;
+  unsigned int *sbad = nullptr;  // per member: this solve's invalid nodes, then the total
+  IoBlock *ioblk = nullptr;      // blocks of the batched init / moments launches
+  long long nioblk = 0;
+  long long *poff_dev = nullptr;  // members' offsets in the packed arrays
+  long long solves = 0;          // solves queued since the batch was made
+  int last_slot = -1;
+  std::vector<double *> pending_drift;  // caller's drift arrays since the last wait
 };
 
 static int ensure_io(lbm_batch_ctx *b) {
@@ -990,6 +1054,43 @@ static cudaError_t batch_launch_all(lbm_batch_ctx *b, int parity, cudaStream_t s
   return cudaSuccess;
 }
 
+static void batch_drop_graphs(lbm_batch_ctx *b) {
+  for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+}
+
+// The captured sequence of `steps` batched step launches starting at batch
+// parity 0 (captured on first use, kept until the launch variant changes).
+static int batch_graph(lbm_batch_ctx *b, long steps, cudaGraphExec_t *out) {
+  auto it = b->graphs.find(steps);
+  if (it != b->graphs.end()) {
+    *out = it->second;
+    return LBM_OK;
+  }
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t gr = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (long k = 0; k < steps && e == cudaSuccess; ++k)
+      e = batch_launch_all(b, (int)(k & 1), cs, b->variant);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, gr, 0);
+  if (gr) cudaGraphDestroy(gr);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    set_error(std::string("batch graph capture: ") + cudaGetErrorString(e));
+    cudaGetLastError();
+    return LBM_ECUDA;
+  }
+  b->graphs[steps] = ex;
+  *out = ex;
+  return LBM_OK;
+}
+
 static std::map<std::string, int> g_batch_tune_cache;
 
 static std::string batch_key(const lbm_batch_ctx *b) {
@@ -1021,10 +1122,7 @@ static int tune_batch(lbm_batch_ctx *b, double *times) {
   }
   if (bv != b->variant) {
     b->variant = bv;
-    if (b->graph) {
-      cudaGraphExecDestroy(b->graph);
-      b->graph = nullptr;
-    }
+    batch_drop_graphs(b);
   }
   b->tuned = true;
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1069,10 +1167,7 @@ namespace lbm {
 // tuner.  Used by the server, which tunes once and reuses the choice.
 void batch_pin_variant(lbm_batch_ctx *b, int variant) {
   if (variant < 0 || variant >= kBatchVariants) return;
-  if (b->variant != variant && b->graph) {
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
-  }
+  if (b->variant != variant) batch_drop_graphs(b);
   b->variant = variant;
   b->tuned = true;
 }
@@ -1115,7 +1210,23 @@ long long batch_nodes(const lbm_batch_ctx *b) { return b->nodes; }
 }  // namespace lbm
 
 static void batch_free(lbm_batch_ctx *b) {
-  if (b->graph) cudaGraphExecDestroy(b->graph);
+  batch_drop_graphs(b);
+  for (auto *st : {b->up, b->down})
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+  for (auto &sl : b->slot) {
+    for (auto &e : sl.ev)
+      if (e) cudaEventDestroy(e);
+    dev_free(sl.in);
+    dev_free(sl.out);
+    dev_free(sl.dout);
+    if (sl.hdrift) cudaFreeHost(sl.hdrift);
+  }
+  dev_free(b->sbad);
+  dev_free(b->ioblk);
+  dev_free(b->poff_dev);
   if (b->io) {
     cudaStreamSynchronize(b->io);
     cudaStreamDestroy(b->io);
@@ -1269,12 +1380,18 @@ static int batch_moments_common(lbm_batch_ctx *b, const std::vector<size_t> &end
 }
 
 // packed layout: member offsets and the batch-wide staging buffer
-static int ensure_packed(lbm_batch_ctx *b) {
-  if (b->pstage) return LBM_OK;
+static void ensure_poff(lbm_batch_ctx *b) {
   const size_t nm = b->members.size();
+  if (b->poff.size() == nm + 1) return;
   b->poff.assign(nm + 1, 0);
   for (size_t k = 0; k < nm; ++k)
     b->poff[k + 1] = b->poff[k] + (size_t)b->members[k]->L.g.nx * b->members[k]->L.g.ny;
+}
+
+static int ensure_packed(lbm_batch_ctx *b) {
+  if (b->pstage) return LBM_OK;
+  const size_t nm = b->members.size();
+  ensure_poff(b);
   b->pstage = (double *)dev_alloc(3 * b->poff[nm] * sizeof(double));
   if (!b->pstage) {
     set_error("out of device memory for the packed staging buffer");
@@ -1309,6 +1426,7 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
     REQUIRE(members[k] != nullptr, "null member");
     REQUIRE(members[k]->L.dtype != LBM_F64, "batches take deviation-storage lattices only");
     REQUIRE(members[k]->batch == nullptr, "lattice already in a batch");
+    REQUIRE(!members[k]->slab, "slabs of a split lattice cannot join a batch");
     REQUIRE(members[k]->device == dev, "members on different devices");
     for (int j = 0; j < k; ++j) REQUIRE(members[j] != members[k], "duplicate member");
   }
@@ -1450,41 +1568,30 @@ int lbm_batch_step(lbm_batch b, long n) {
     int rc = maybe_autotune_batch(b);
     if (rc != LBM_OK) return rc;
   }
-  const int G = 64;
+  // whole graphs of 64 steps, the remainder as one graph of its own length
+  // (both cached), so a call of n steps is a handful of graph launches
+  const long G = 64;
   long done = 0;
+  if (b->parity == 1 && n > 0) {
+    CK(batch_launch_all(b, 1, b->stream, b->variant));
+    b->parity = 0;
+    n -= 1;
+    done += 1;
+  }
   while (n > 0) {
-    if (b->parity == 0 && n >= G) {
-      if (!b->graph) {
-        cudaStream_t cs;
-        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaGraph_t gr = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-          for (int k = 0; k < G && e == cudaSuccess; ++k)
-            e = batch_launch_all(b, k & 1, cs, b->variant);
-          cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
-          if (e == cudaSuccess) e = e2;
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, gr, 0);
-        if (gr) cudaGraphDestroy(gr);
-        cudaStreamDestroy(cs);
-        if (e != cudaSuccess) {
-          b->graph = nullptr;
-          set_error(std::string("batch graph capture: ") + cudaGetErrorString(e));
-          cudaGetLastError();
-          return LBM_ECUDA;
-        }
-        b->graph_steps = G;
-      }
-      CK(cudaGraphLaunch(b->graph, b->stream));
-      n -= G;
-      done += G;
+    const long k = n >= G ? G : n;
+    if (k >= 2) {
+      cudaGraphExec_t ex = nullptr;
+      int rc = batch_graph(b, k, &ex);
+      if (rc != LBM_OK) return rc;
+      CK(cudaGraphLaunch(ex, b->stream));
+      b->parity = (int)(k & 1);
     } else {
-      CK(batch_launch_all(b, b->parity, b->stream, b->variant));
-      b->parity ^= 1;
-      n -= 1;
-      done += 1;
+      CK(batch_launch_all(b, 0, b->stream, b->variant));
+      b->parity = 1;
     }
+    n -= k;
+    done += k;
   }
   for (size_t k = 0; k < b->members.size(); ++k) {
     b->members[k]->L.cur = b->offs[k] ^ b->parity;
@@ -1617,6 +1724,208 @@ int lbm_batch_moments_packed(lbm_batch b, double *rho, double *ux, double *uy) {
     return e;
   };
   return batch_moments_common(b, ends, download, fields);
+}
+
+// Set up the two solve slots, the copy streams and the invalid-field
+// counters on first use.
+static int ensure_solve(lbm_batch_ctx *b) {
+  if (b->up) return LBM_OK;
+  const size_t T = (size_t)b->nodes, nm = b->members.size();
+  ensure_poff(b);  // member offsets of the packed arrays
+  for (auto &sl : b->slot) {
+    sl.in = (double *)dev_alloc(3 * T * sizeof(double));
+    sl.out = (double *)dev_alloc(3 * T * sizeof(double));
+    sl.dout = (double *)dev_alloc(4 * nm * sizeof(double));
+    if (cudaHostAlloc(&sl.hdrift, 4 * nm * sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      sl.hdrift = nullptr;
+    }
+    if (!sl.in || !sl.out || !sl.dout || !sl.hdrift) {
+      set_error("out of device memory for the pipelined solve staging");
+      return LBM_ENOMEM;
+    }
+    for (auto &e : sl.ev) CK(cudaEventCreate(&e));
+  }
+  b->sbad = (unsigned int *)dev_alloc(2 * nm * sizeof(unsigned int));
+  if (!b->sbad) {
+    set_error("out of device memory for the solve counters");
+    return LBM_ENOMEM;
+  }
+  // blocks of kIoBlockNodes nodes of one member each, and the members'
+  // packed offsets, for the one-launch init and moments
+  std::vector<IoBlock> blk;
+  for (size_t k = 0; k < nm; ++k) {
+    const long long n = (long long)b->members[k]->L.g.nx * b->members[k]->L.g.ny;
+    for (long long s0 = 0; s0 < n; s0 += kIoBlockNodes) {
+      IoBlock io;
+      io.member = (int)k;
+      io.count = (int)std::min<long long>(kIoBlockNodes, n - s0);
+      io.start = s0;
+      blk.push_back(io);
+    }
+  }
+  std::vector<long long> po(b->poff.begin(), b->poff.end());
+  b->ioblk = (IoBlock *)dev_alloc(blk.size() * sizeof(IoBlock));
+  b->poff_dev = (long long *)dev_alloc(po.size() * sizeof(long long));
+  if (!b->ioblk || !b->poff_dev) {
+    set_error("out of device memory for the solve tables");
+    return LBM_ENOMEM;
+  }
+  b->nioblk = (long long)blk.size();
+  CK(cudaMemcpyAsync(b->ioblk, blk.data(), blk.size() * sizeof(IoBlock), cudaMemcpyHostToDevice,
+                     b->stream));
+  CK(cudaMemcpyAsync(b->poff_dev, po.data(), po.size() * sizeof(long long),
+                     cudaMemcpyHostToDevice, b->stream));
+  CK(cudaMemsetAsync(b->sbad, 0, 2 * nm * sizeof(unsigned int), b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  cudaStream_t up = nullptr, down = nullptr;
+  CK(cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking));
+  if (cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaStreamDestroy(up);
+    set_error("cannot create the download stream");
+    cudaGetLastError();
+    return LBM_ECUDA;
+  }
+  b->up = up;
+  b->down = down;
+  return LBM_OK;
+}
+
+int lbm_batch_solve_packed(lbm_batch b, long n, const double *rho_in, const double *ux_in,
+                           const double *uy_in, double *rho_out, double *ux_out, double *uy_out,
+                           double *drift_out) {
+  NvtxRange nvtx("lbm_batch_solve_packed");
+  REQUIRE(b != nullptr && rho_in && ux_in && uy_in && rho_out && ux_out && uy_out,
+          "null argument");
+  REQUIRE(n >= 0, "negative step count");
+  REQUIRE(!b->spent, "batch ran a ragged generation; create a new batch");
+  for (auto *m : b->members)
+    REQUIRE(m->L.dtype != LBM_F16DEV,
+            "pipelined solves take FP32 and BF16 members (an FP16 member's storage scale is "
+            "chosen on the host from its fields: use lbm_batch_init_packed)");
+  DevGuard g(b->device);
+  int rc = ensure_solve(b);
+  if (rc != LBM_OK) return rc;
+  using B = lbm_batch_ctx;
+  const size_t T = (size_t)b->nodes, nm = b->members.size();
+  const int si = (int)(b->solves & 1);
+  B::Slot &sl = b->slot[si];
+  // upload, once the solve two back has initialised from this slot
+  CK(cudaStreamWaitEvent(b->up, sl.ev[B::E_INIT], 0));
+  CK(cudaEventRecord(sl.ev[B::E_UP0], b->up));
+  const double *src[3] = {rho_in, ux_in, uy_in};
+  for (int c = 0; c < 3; ++c)
+    CK(cudaMemcpyAsync(sl.in + c * T, src[c], T * sizeof(double), cudaMemcpyHostToDevice,
+                       b->up));
+  CK(cudaEventRecord(sl.ev[B::E_UP1], b->up));
+  // equilibrium init of every member from the staged fields
+  CK(cudaStreamWaitEvent(b->stream, sl.ev[B::E_UP1], 0));
+  CK(cudaEventRecord(sl.ev[B::E_B0], b->stream));
+  CK(launch_batch_init_dev(b->views[b->parity], b->ioblk, b->nioblk, b->poff_dev, (long long)T,
+                           sl.in, b->sbad, (int)nm, b->stream));
+  CK(launch_add_u32(b->sbad + nm, b->sbad, (int)nm, b->stream));
+  for (auto *m : b->members) m->t = 0;
+  CK(cudaEventRecord(sl.ev[B::E_INIT], b->stream));
+  rc = lbm_batch_step(b, n);
+  if (rc != LBM_OK) return rc;
+  CK(cudaEventRecord(sl.ev[B::E_STEP], b->stream));
+  CK(launch_batch_drift(b->views[b->parity], (int)nm, b->dpart, sl.dout, b->stream));
+  CK(cudaEventRecord(sl.ev[B::E_DRIFT], b->stream));
+  // moments into this slot's output staging, once the solve two back has
+  // downloaded from it
+  CK(cudaStreamWaitEvent(b->stream, sl.ev[B::E_DN1], 0));
+  CK(launch_batch_moments_dev(b->views[b->parity], b->ioblk, b->nioblk, b->poff_dev,
+                              (long long)T, sl.out, b->stream));
+  CK(cudaEventRecord(sl.ev[B::E_MOM], b->stream));
+  // download
+  CK(cudaStreamWaitEvent(b->down, sl.ev[B::E_MOM], 0));
+  CK(cudaEventRecord(sl.ev[B::E_DN0], b->down));
+  double *dst[3] = {rho_out, ux_out, uy_out};
+  for (int c = 0; c < 3; ++c)
+    CK(cudaMemcpyAsync(dst[c], sl.out + c * T, T * sizeof(double), cudaMemcpyDeviceToHost,
+                       b->down));
+  if (drift_out) {
+    CK(cudaMemcpyAsync(sl.hdrift, sl.dout, 4 * nm * sizeof(double), cudaMemcpyDeviceToHost,
+                       b->down));
+    // the host runs ahead of the device by several solves, so each call
+    // gets its own payload (freed by the host function); the page-locked
+    // array itself is reused only after this stream has passed the host
+    // function of the solve two back
+    auto *dc = new (std::nothrow) lbm_batch_ctx::DriftOut();
+    if (!dc) {
+      set_error("out of host memory");
+      return LBM_ENOMEM;
+    }
+    dc->dst = drift_out;
+    dc->src = sl.hdrift;
+    dc->bytes = 4 * nm * sizeof(double);
+    cudaError_t e = cudaLaunchHostFunc(
+        b->down,
+        [](void *p) {
+          auto *d = static_cast<lbm_batch_ctx::DriftOut *>(p);
+          memcpy(d->dst, d->src, d->bytes);
+          delete d;
+        },
+        dc);
+    if (e != cudaSuccess) {
+      delete dc;
+      CK(e);
+    }
+    b->pending_drift.push_back(drift_out);
+  }
+  CK(cudaEventRecord(sl.ev[B::E_DN1], b->down));
+  sl.used = true;
+  b->last_slot = si;
+  ++b->solves;
+  return LBM_OK;
+}
+
+int lbm_batch_wait(lbm_batch b, double *phase_ms) {
+  REQUIRE(b != nullptr, "null batch");
+  DevGuard g(b->device);
+  if (b->up) {
+    CK(cudaStreamSynchronize(b->up));
+    CK(cudaStreamSynchronize(b->stream));
+    CK(cudaStreamSynchronize(b->down));
+  }
+  if (phase_ms) {
+    for (int k = 0; k < 6; ++k) phase_ms[k] = 0.0;
+    if (b->last_slot >= 0) {
+      using B = lbm_batch_ctx;
+      const B::Slot &sl = b->slot[b->last_slot];
+      const int pairs[6][2] = {{B::E_UP0, B::E_UP1},   {B::E_B0, B::E_INIT},
+                               {B::E_INIT, B::E_STEP}, {B::E_STEP, B::E_DRIFT},
+                               {B::E_DRIFT, B::E_MOM}, {B::E_DN0, B::E_DN1}};
+      for (int k = 0; k < 6; ++k) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, sl.ev[pairs[k][0]], sl.ev[pairs[k][1]]));
+        phase_ms[k] = ms;
+      }
+    }
+  }
+  const size_t nm = b->members.size();
+  int rc = LBM_OK;
+  if (b->sbad) {
+    std::vector<unsigned int> tot(nm, 0);
+    CK(cudaMemcpy(tot.data(), b->sbad + nm, nm * sizeof(unsigned int), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(b->sbad + nm, 0, nm * sizeof(unsigned int)));
+    for (size_t j = 0; j < nm; ++j)
+      if (tot[j]) {
+        set_error("member " + std::to_string(j) + ": " + std::to_string(tot[j]) +
+                  " nodes with non-finite fields or rho <= 0 over the solves since the last wait");
+        rc = LBM_EINVAL;
+        break;
+      }
+  }
+  if (rc == LBM_OK)
+    for (double *d : b->pending_drift)
+      for (size_t k = 0; k < nm && rc == LBM_OK; ++k)
+        if (d[4 * k + 3] > 0) {
+          set_error("member " + std::to_string(k) + " holds non-finite populations");
+          rc = LBM_EUNSTABLE;
+        }
+  b->pending_drift.clear();
+  return rc;
 }
 
 int lbm_get_variant(lbm_handle h, int *variant) {

@@ -23,6 +23,19 @@ struct NvtxRange {
 };
 
 
+// Make device d current for the lifetime of a scope (restored afterwards).
+struct DevGuard {
+  int prev = -1, want;
+  explicit DevGuard(int d) : want(d) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != d) cudaSetDevice(d);
+  }
+  ~DevGuard() {
+    if (prev >= 0 && prev != want) cudaSetDevice(prev);
+  }
+  DevGuard(const DevGuard &) = delete;
+  DevGuard &operator=(const DevGuard &) = delete;
+};
+
 // Everything a step launch needs about one lattice.
 struct Lattice {
   Geom g;
@@ -142,6 +155,20 @@ cudaError_t launch_maxdev_dev(const AuxView &a, const double *rho, const double 
                               const double *uy, unsigned int *max_bits, cudaStream_t st);
 cudaError_t launch_moments_dev(const AuxView &a, double *rho, double *ux, double *uy,
                                cudaStream_t st);
+// batched field I/O of a batch's deviation-storage members (one launch for
+// all members): block b covers nodes [start, start + count) of `member`
+struct IoBlock {
+  int member;
+  int count;
+  long long start;
+};
+constexpr int kIoBlockNodes = 1024;
+cudaError_t launch_batch_init_dev(const AuxView *views, const IoBlock *blocks, long long nblocks,
+                                  const long long *poff, long long total, const double *stage,
+                                  unsigned int *bad, int members, cudaStream_t st);
+cudaError_t launch_batch_moments_dev(const AuxView *views, const IoBlock *blocks,
+                                     long long nblocks, const long long *poff, long long total,
+                                     double *stage, cudaStream_t st);
 cudaError_t launch_force_node(const AuxView &a, int x, int y, const double fs[9],
                               cudaStream_t st);
 cudaError_t launch_force_node_tab(const AuxView &a, int x, int y, const double *fs_dev,
@@ -154,6 +181,7 @@ int drift_blocks();
 cudaError_t launch_drift(const AuxView &a, double *partials, double *out,
                          cudaStream_t st);
 int batch_drift_partials(int n);
+cudaError_t launch_add_u32(unsigned int *acc, const unsigned int *add, int n, cudaStream_t st);
 cudaError_t launch_batch_drift(const AuxView *views_dev, int n, double *partials, double *out,
                                cudaStream_t st);
 
@@ -168,6 +196,18 @@ void batch_pin_variant(lbm_batch_ctx *b, int variant);
 int batch_step_ragged(lbm_batch_ctx *b, const long *steps, long n);
 int batch_variant(const lbm_batch_ctx *b);
 long long batch_nodes(const lbm_batch_ctx *b);
+
+// lattice handles (lbm_api.cu): the constructor behind lbm_create, with
+// halo rows for the slabs of a split lattice, and what the slab driver
+// (slabs.cu) reads of a handle
+int create_lattice(int nx, int ny, const double S[9], double rho0, const double u0[2],
+                   int storage_dtype, bool halo, lbm_handle *out);
+Lattice &lattice_of(lbm_handle h);
+int block_of(lbm_handle h);
+bool is_slab(lbm_handle h);
+cudaStream_t stream_of(lbm_handle h);
+int device_of(lbm_handle h);
+void advance_one(lbm_handle h);  // after one step launched by the slab driver
 
 // device memory through the configurable allocator
 void *dev_alloc(size_t bytes);

@@ -87,6 +87,7 @@ struct lbm_server_ctx {
   int policy = LBM_SERVE_FIFO;
   long long max_nodes = 0;  // resident-node cap (0: bytes only)
   long long resident_nodes = 0;
+  std::deque<long long> done_ids;  // finished since the last lbm_server_done
 };
 
 static int ensure_server_stage(lbm_server_ctx *s, size_t nodes) {
@@ -160,6 +161,7 @@ static void finish(lbm_server_ctx *s, Req *q, int err) {
   q->state = err == LBM_OK ? DONE : FAILED;
   q->err = err;
   q->latency = now_s() - q->t_submit;
+  s->done_ids.push_back(q->id);
   if (err == LBM_OK)
     s->st.completed++;
   else
@@ -373,6 +375,21 @@ int lbm_poll(lbm_server s, long long id, double *rho, double *ux, double *uy,
   if (latency_s) *latency_s = q->latency;
   delete q;
   return rc;
+}
+
+int lbm_server_done(lbm_server s, long long *ids, int cap, int *count) {
+  if (!s || !count || cap < 0 || (cap > 0 && !ids)) {
+    set_error("bad lbm_server_done arguments");
+    return LBM_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  int n = 0;
+  while (n < cap && !s->done_ids.empty()) {
+    ids[n++] = s->done_ids.front();
+    s->done_ids.pop_front();
+  }
+  *count = n;
+  return LBM_OK;
 }
 
 int lbm_server_stats(lbm_server s, lbm_server_stats_t *out) {

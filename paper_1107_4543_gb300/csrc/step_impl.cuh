@@ -33,15 +33,22 @@ __device__ __forceinline__ void step_task(const T *__restrict__ src, T *__restri
     pull9_packed<T>(src, g, p, w);
 #pragma unroll
     for (int k = 0; k < V / 2; ++k) {
-      float f[9][2];
+      // the word's two nodes collide together, one per lane of the packed
+      // FP32 pair instructions
+      F2 f[9];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) Elem<T>::unpack2(w[i][k], f[i]);
+      for (int i = 0; i < 9; ++i) {
+        float t[2];
+        Elem<T>::unpack2(w[i][k], t);
+        f[i] = f2(t[0], t[1]);
+      }
+      collide_pair<SCALED>(f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8], P);
 #pragma unroll
-      for (int e = 0; e < 2; ++e)
-        collide_dev<PRECISE, SCALED>(f[0][e], f[1][e], f[2][e], f[3][e], f[4][e], f[5][e],
-                                     f[6][e], f[7][e], f[8][e], P);
-#pragma unroll
-      for (int i = 0; i < 9; ++i) w[i][k] = Elem<T>::pack2(f[i][0], f[i][1]);
+      for (int i = 0; i < 9; ++i) {
+        float t[2];
+        f2split(f[i], t[0], t[1]);
+        w[i][k] = Elem<T>::pack2(t[0], t[1]);
+      }
     }
     store9_packed<T>(dst, g, p, w);
   } else {

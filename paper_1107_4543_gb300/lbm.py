@@ -107,6 +107,28 @@ _SIGS = {
     "lbm_batch_moments": (ctypes.c_int, [_vp, ctypes.POINTER(_dp), ctypes.POINTER(_dp),
                                          ctypes.POINTER(_dp)]),
     "lbm_batch_destroy": (ctypes.c_int, [_vp]),
+    "lbm_batch_solve_packed": (ctypes.c_int, [_vp, ctypes.c_long, _dp, _dp, _dp, _dp, _dp, _dp,
+                                              _dp]),
+    "lbm_slabs_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, _dp,
+                                        ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_vp)]),
+    "lbm_slabs_rows": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "lbm_slabs_init_field": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
+    "lbm_slabs_set_populations": (ctypes.c_int, [_vp, _dp]),
+    "lbm_slabs_step": (ctypes.c_int, [_vp, ctypes.c_long]),
+    "lbm_slabs_moments": (ctypes.c_int, [_vp, _dp, _dp, _dp]),
+    "lbm_slabs_get_populations": (ctypes.c_int, [_vp, _dp]),
+    "lbm_slabs_drift": (ctypes.c_int, [_vp, _dp]),
+    "lbm_slabs_destroy": (ctypes.c_int, [_vp]),
+    "lbm_slab_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       _dp, ctypes.c_double, _dp, ctypes.c_int,
+                                       ctypes.POINTER(_vp)]),
+    "lbm_slab_halo_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "lbm_slab_pack": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "lbm_slab_unpack": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "lbm_batch_wait": (ctypes.c_int, [_vp, _dp]),
     "lbm_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_long, ctypes.POINTER(_vp)]),
     "lbm_submit": (ctypes.c_int, [_vp, ctypes.POINTER(lbm_request),
                                   ctypes.POINTER(ctypes.c_longlong)]),
@@ -114,6 +136,8 @@ _SIGS = {
     "lbm_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(lbm_server_stats_t)]),
     "lbm_server_set_policy": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_longlong]),
     "lbm_server_destroy": (ctypes.c_int, [_vp]),
+    "lbm_server_done": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int)]),
 }
 
 _lib = None
@@ -434,6 +458,138 @@ def lbm_batch_moments_packed(b, out=None):
     return out
 
 
+def lbm_batch_solve_packed(b, n, fields_in, fields_out, drift_out=None):
+    """Queue one whole solve of every member (upload, equilibrium init, n
+    steps, drift sums, moments, download) without waiting; fields_in and
+    fields_out are (rho, ux, uy) triples of packed contiguous float64 arrays
+    (as lbm_batch_init_packed), drift_out an (members, 4) float64 array or
+    None.  The arrays must stay alive and untouched until lbm_batch_wait."""
+    _packed(b, fields_in, "fields")
+    _packed(b, fields_out, "outputs")
+    dp = None
+    if drift_out is not None:
+        m = lbm_batch_size(b)[0]
+        if (drift_out.dtype != np.float64 or not drift_out.flags.c_contiguous
+                or drift_out.size != 4 * m):
+            raise ValueError("drift_out must be a contiguous float64 array of %d values" % (4 * m))
+        dp = _ptr(drift_out)
+    _ck(load().lbm_batch_solve_packed(b, int(n), _ptr(fields_in[0]), _ptr(fields_in[1]),
+                                      _ptr(fields_in[2]), _ptr(fields_out[0]),
+                                      _ptr(fields_out[1]), _ptr(fields_out[2]), dp),
+        "lbm_batch_solve_packed")
+
+
+# ------------------------------------------------------------- slabs
+def lbm_slabs_create(nx, ny, S, rho0=1.0, u0=(0.0, 0.0), dtype=LBM_F32DEV, nslabs=2,
+                     devices=None):
+    """One nx x ny periodic lattice split into nslabs y-slabs (devices: one
+    CUDA device index per slab, default the current device)."""
+    Sa = _f64(S, (9,))
+    u = _f64(u0, (2,))
+    dev = None
+    if devices is not None:
+        if len(devices) != nslabs:
+            raise ValueError("one device per slab")
+        dev = (ctypes.c_int * nslabs)(*devices)
+    s = _vp()
+    _ck(load().lbm_slabs_create(int(nx), int(ny), _ptr(Sa), float(rho0), _ptr(u), int(dtype),
+                                int(nslabs), dev, ctypes.byref(s)), "lbm_slabs_create")
+    return s
+
+
+def lbm_slabs_rows(s, k):
+    """(first row, rows, device) of slab k."""
+    y0, r, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _ck(load().lbm_slabs_rows(s, int(k), ctypes.byref(y0), ctypes.byref(r), ctypes.byref(d)),
+        "lbm_slabs_rows")
+    return y0.value, r.value, d.value
+
+
+def lbm_slabs_init_field(s, rho, ux, uy):
+    rho, ux, uy = (_f64(a) for a in (rho, ux, uy))
+    _ck(load().lbm_slabs_init_field(s, _ptr(rho), _ptr(ux), _ptr(uy)), "lbm_slabs_init_field")
+
+
+def lbm_slabs_set_populations(s, f):
+    f = _f64(f)
+    _ck(load().lbm_slabs_set_populations(s, _ptr(f)), "lbm_slabs_set_populations")
+
+
+def lbm_slabs_step(s, n):
+    _ck(load().lbm_slabs_step(s, int(n)), "lbm_slabs_step")
+
+
+def lbm_slabs_moments(s, ny, nx):
+    rho, ux, uy = (np.empty((ny, nx)) for _ in range(3))
+    _ck(load().lbm_slabs_moments(s, _ptr(rho), _ptr(ux), _ptr(uy)), "lbm_slabs_moments")
+    return rho, ux, uy
+
+
+def lbm_slabs_get_populations(s, ny, nx):
+    f = np.empty((9, ny, nx))
+    _ck(load().lbm_slabs_get_populations(s, _ptr(f)), "lbm_slabs_get_populations")
+    return f
+
+
+def lbm_slabs_drift(s):
+    out = np.zeros(4)
+    rc = load().lbm_slabs_drift(s, _ptr(out))
+    if rc not in (LBM_OK, LBM_EUNSTABLE):
+        raise LbmError(rc, "lbm_slabs_drift")
+    return out
+
+
+def lbm_slabs_destroy(s):
+    _ck(load().lbm_slabs_destroy(s), "lbm_slabs_destroy")
+
+
+def lbm_slab_create(nx, ny_total, y0, rows, S, rho0=1.0, u0=(0.0, 0.0), dtype=LBM_F32DEV):
+    """Handle of rows [y0, y0 + rows) of an nx x ny_total periodic lattice,
+    for one slab per process; the caller exchanges its halo rows."""
+    Sa = _f64(S, (9,))
+    u = _f64(u0, (2,))
+    h = _vp()
+    _ck(load().lbm_slab_create(int(nx), int(ny_total), int(y0), int(rows), _ptr(Sa), float(rho0),
+                               _ptr(u), int(dtype), ctypes.byref(h)), "lbm_slab_create")
+    return h
+
+
+def lbm_slab_halo_bytes(h):
+    n = ctypes.c_size_t()
+    _ck(load().lbm_slab_halo_bytes(h, ctypes.byref(n)), "lbm_slab_halo_bytes")
+    return n.value
+
+
+def lbm_slab_pack(h, reverse, to_below, to_above):
+    """Copy the slab's outgoing rows into two device buffers (torch CUDA
+    tensors or device addresses) of lbm_slab_halo_bytes bytes each."""
+    _ck(load().lbm_slab_pack(h, int(bool(reverse)), _vp(_dev(to_below)), _vp(_dev(to_above))),
+        "lbm_slab_pack")
+
+
+def lbm_slab_unpack(h, reverse, from_below, from_above):
+    _ck(load().lbm_slab_unpack(h, int(bool(reverse)), _vp(_dev(from_below)),
+                               _vp(_dev(from_above))), "lbm_slab_unpack")
+
+
+BATCH_PHASES = ("h2d_ms", "init_ms", "steps_ms", "drift_ms", "moments_ms", "d2h_ms")
+
+
+def lbm_batch_wait(b):
+    """Wait for the queued solves; returns the last solve's device times per
+    phase (dict keyed by BATCH_PHASES) and "unstable": whether a drift array
+    passed since the previous wait reports non-finite populations (as
+    lbm_batch_drift, that is a result, not an error).  Invalid input fields
+    raise LbmError (LBM_EINVAL)."""
+    ms = np.zeros(6)
+    rc = load().lbm_batch_wait(b, _ptr(ms))
+    if rc not in (LBM_OK, LBM_EUNSTABLE):
+        raise LbmError(rc, "lbm_batch_wait")
+    out = dict(zip(BATCH_PHASES, (float(x) for x in ms)))
+    out["unstable"] = rc == LBM_EUNSTABLE
+    return out
+
+
 def cost_spec(kind="F", order=5, part="all", reference=None, u0=0.2, fixed_speed=False):
     """lbm_cost_spec from names: kind 'F' / 'G', part 'all' / 'odd' / 'even',
     reference 'ns' / 'euler' / 'ns-bulk' (default 'ns' for F, 'euler' for G)."""
@@ -549,6 +705,14 @@ def lbm_server_stats(s):
     st = lbm_server_stats_t()
     _ck(load().lbm_server_stats(s, ctypes.byref(st)), "lbm_server_stats")
     return {k: getattr(st, k) for k, _ in lbm_server_stats_t._fields_}
+
+
+def lbm_server_done(s, cap=4096):
+    """Ids of the requests finished since the previous call (at most cap)."""
+    ids = (ctypes.c_longlong * cap)()
+    n = ctypes.c_int()
+    _ck(load().lbm_server_done(s, ids, cap, ctypes.byref(n)), "lbm_server_done")
+    return list(ids[:n.value])
 
 
 def lbm_server_destroy(s):

@@ -1,8 +1,9 @@
 """The multi-rank path of bench.py on CPU: two gloo ranks.
 
-Each rank steps its own independent batch (weak scaling), so the only
-cross-rank operations are the timing barrier and the max over ranks; the
-reported value is all ranks' units over that max time.
+The workload is 2 x `lattices` independent lattices placed on the ranks by
+bytes (weak scaling), so the only cross-rank operations are the timing
+barrier and the max over ranks; the reported value is all ranks' units over
+that max time.
 """
 import os
 import socket
@@ -31,7 +32,7 @@ def _worker(rank, world, port, out):
         lattices = 6
         lbm_steps = 10
 
-    specs = bench.rank_specs(A, rank)
+    specs = bench.rank_specs(A, rank, world)
     nodes = sum(s["nx"] * s["ny"] for s in specs)
     # ranks report different times; everyone must see the slowest
     t = bench.reduce_max(1.0 + rank, device="cpu")
@@ -58,5 +59,11 @@ def test_two_gloo_ranks_shard_and_reduce():
         assert p.exitcode == 0
     (r0, s0, t0, v0, n0), (r1, s1, t1, v1, n1) = res
     assert s0 != s1                      # independent shards
+    # together the shards are the 12-lattice workload, each lattice once
+    import lbm_inputs as inp
+
+    whole = inp.batch_specs(12, seed=1107 + 4, steps=10)
+    assert sorted(s0 + s1) == sorted((s["nx"], s["ny"]) for s in whole)
+    assert abs(n0 - n1) <= max(s["nx"] * s["ny"] for s in whole)  # balanced by bytes
     assert t0 == t1 == 2.0               # max over ranks
     assert v0 == v1 == pytest.approx((n0 + n1) * 10 / 2.0 / 1e6)

@@ -176,6 +176,82 @@ def test_batch_packed_io_equals_per_member_io(L):
             L.lbm_destroy(h)
 
 
+def test_batch_solve_packed_equals_synchronous_calls(L):
+    """lbm_batch_solve_packed (upload, init, steps, drift, moments, download
+    queued without waiting, successive solves overlapping through two
+    staging slots) gives bit for bit what lbm_batch_init_packed +
+    lbm_batch_step + lbm_batch_drift + lbm_batch_moments_packed give, for
+    three solves queued back to back with different fields (both slots
+    reused), FP32 and BF16 members; invalid fields and FP16 members are
+    reported."""
+    torch = pytest.importorskip("torch")
+    specs = inp.batch_specs(7, seed=17, amin=300 * 300, amax=1500 * 1500)
+    specs[2].update(nx=33, ny=17)
+    dtypes = ["f32", "bf16", "f32", "f32", "bf16", "f32", "f32"]
+    steps = [40, 7, 65]
+    total = sum(sp["nx"] * sp["ny"] for sp in specs)
+
+    def pinned(n):
+        return torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+
+    ins = []
+    for rep in range(3):
+        sp2 = [dict(sp, amp=sp["amp"] * (1 + rep), xc=sp["xc"] + 3 * rep) for sp in specs]
+        fields = [inp.batch_fields(sp) for sp in sp2]
+        tri = tuple(pinned(total) for _ in range(3))
+        for c in range(3):
+            np.concatenate([f[c].ravel() for f in fields], out=tri[c])
+        ins.append(tri)
+
+    def make():
+        return [L.lbm_create(sp["nx"], sp["ny"], inp.s_ll(sp["rates"]), 1.0, (0.0, 0.0),
+                             L.DTYPES[dt]) for sp, dt in zip(specs, dtypes)]
+
+    ha, hb = make(), make()
+    try:
+        ba, bb = L.lbm_batch_create(ha), L.lbm_batch_create(hb)
+        outs = [tuple(pinned(total) for _ in range(3)) for _ in range(3)]
+        drifts = [np.zeros((len(specs), 4)) for _ in range(3)]
+        for rep in range(3):
+            L.lbm_batch_solve_packed(bb, steps[rep], ins[rep], outs[rep], drifts[rep])
+        phases = L.lbm_batch_wait(bb)
+        assert set(phases) == set(L.BATCH_PHASES) | {"unstable"} and phases["steps_ms"] > 0
+        assert not phases["unstable"]
+        for rep in range(3):
+            L.lbm_batch_init_packed(ba, *ins[rep])
+            L.lbm_batch_step(ba, steps[rep])
+            d = L.lbm_batch_drift(ba, len(specs))
+            want = L.lbm_batch_moments_packed(ba)
+            for c in range(3):
+                assert np.array_equal(outs[rep][c], want[c]), (rep, c)
+            assert np.array_equal(drifts[rep], d), rep
+        # invalid fields are reported by the wait, naming the member
+        bad = tuple(a.copy() for a in ins[0])
+        bad[0][total - 5] = -1.0
+        L.lbm_batch_solve_packed(bb, 3, bad, outs[0])
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_batch_wait(bb)
+        assert e.value.code == L.LBM_EINVAL and "member 6" in str(e.value)
+        L.lbm_batch_solve_packed(bb, 3, ins[0], outs[0])
+        L.lbm_batch_wait(bb)  # the counters were cleared
+        with pytest.raises(ValueError):
+            L.lbm_batch_solve_packed(bb, 3, (ins[0][0][:-1],) + ins[0][1:], outs[0])
+        L.lbm_batch_destroy(ba)
+        L.lbm_batch_destroy(bb)
+    finally:
+        for h in ha + hb:
+            L.lbm_destroy(h)
+    h = L.lbm_create(16, 16, inp.s_ll(inp.rates("OPT")), 1.0, (0.0, 0.0), L.LBM_F16DEV)
+    try:
+        b = L.lbm_batch_create([h])
+        z = tuple(np.ones(256) for _ in range(3))
+        with pytest.raises(L.LbmError):
+            L.lbm_batch_solve_packed(b, 1, z, tuple(np.empty(256) for _ in range(3)))
+        L.lbm_batch_destroy(b)
+    finally:
+        L.lbm_destroy(h)
+
+
 def test_batch_results_match_oracle(L):
     specs = small_specs(6, seed=12)
     hs = []
@@ -312,9 +388,13 @@ def test_served_result_equals_alone(L, budget_mb, policy, cap):
             kinds.append((kind, params))
         out = wait_all(L, srv, ids, reqs)
         st = L.lbm_server_stats(srv)
+        done = L.lbm_server_done(srv, cap=5) + L.lbm_server_done(srv)
+        assert L.lbm_server_done(srv) == []
     finally:
         L.lbm_server_destroy(srv)
     assert st["completed"] == len(reqs) and st["failed"] == 0
+    # every finished request is reported once, whatever the chunking
+    assert sorted(done) == sorted(ids)
     if budget_mb == 2:
         assert st["peak_bytes"] <= 2 * 2**20
         assert st["generations"] > 3
