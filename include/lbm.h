@@ -248,6 +248,20 @@ int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void *ctx);
 const char *lbm_strerror(int code);
 const char *lbm_last_error(void);
 
+/* (runtime; no counterpart in the paper) Index checks of the debug build
+ * (compiled with -DLBM_DEBUG_BOUNDS: paper_1107_4543_gb300/build.py
+ * build(debug=True) makes _build_debug/liblbm.so).  The von Neumann QR, the
+ * optimizer's polynomial-matrix slots and tables, the batched step's block
+ * records and lane positions and the batched init / moments blocks check
+ * their indices; a failed check sets a bit of a device word and the access
+ * goes to the array's first element instead (no trap, the context stays
+ * usable).  lbm_debug_bounds ORs the words of every translation unit of the
+ * current device into *word (bits: see csrc/bounds.cuh) and, if reset,
+ * clears them; lbm_debug_bounds_selftest runs one checked access past its
+ * bound (bit 31).  Without the flag both return LBM_EINVAL (*word = 0). */
+int lbm_debug_bounds(unsigned int *word, int reset);
+int lbm_debug_bounds_selftest(void);
+
 /* ------------------------------------------------- von Neumann analysis */
 /* lbm_vn_eigs -- eigenvalues of the von Neumann amplification matrix of
  * section 4.1, G(k) = diag(exp(-i k.c_j)) M^-1 Psi M, with Psi the

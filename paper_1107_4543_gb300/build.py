@@ -31,7 +31,11 @@ UNITS = {
     "vn.cu": [],
     "optcost.cu": [],
 }
-HEADERS = ["lbm_internal.h", "d2q9_pull.cuh", "collide.cuh", "step_impl.cuh"]
+HEADERS = ["lbm_internal.h", "d2q9_pull.cuh", "collide.cuh", "step_impl.cuh", "bounds.cuh"]
+# the debug build: device-side index checks that record failures in a word
+# (lbm_debug_bounds) instead of trapping
+OUT_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(OUT_DEBUG, "liblbm.so")
 
 
 def _newest_input():
@@ -41,16 +45,19 @@ def _newest_input():
     return max(os.path.getmtime(p) for p in paths)
 
 
-def build(force=False, verbose=False):
-    """Compile (if stale) and return the path of liblbm.so."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+def build(force=False, verbose=False, debug=False):
+    """Compile (if stale) and return the path of liblbm.so; debug=True builds
+    the index-checking library in _build_debug instead."""
+    out, lib = (OUT_DEBUG, LIB_DEBUG) if debug else (OUT, LIB)
+    flags = COMMON + (["-DLBM_DEBUG_BOUNDS"] if debug else [])
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input():
+        return lib
+    os.makedirs(out, exist_ok=True)
     procs = []
     objs = []
     for unit, extra in UNITS.items():
-        obj = os.path.join(OUT, unit.replace(".cu", ".o"))
-        cmd = ["nvcc"] + COMMON + extra + ["-c", os.path.join(SRC, unit), "-o", obj]
+        obj = os.path.join(out, unit.replace(".cu", ".o"))
+        cmd = ["nvcc"] + flags + extra + ["-c", os.path.join(SRC, unit), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((unit, subprocess.Popen(cmd, stdout=subprocess.PIPE,
@@ -65,11 +72,11 @@ def build(force=False, verbose=False):
             failed.append(unit)
     if failed:
         raise RuntimeError("nvcc failed for " + ", ".join(failed))
-    tmp = LIB + ".tmp.%d" % os.getpid()
+    tmp = lib + ".tmp.%d" % os.getpid()
     subprocess.run(["nvcc"] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"],
                    check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -16,6 +16,7 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include "bounds.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -212,8 +213,14 @@ __global__ void __launch_bounds__(256) k_batch_init_dev(const AuxView *__restric
                                                         const IoBlock *__restrict__ blocks,
                                                         const long long *__restrict__ poff,
                                                         long long total, const double *stage,
-                                                        unsigned int *bad) {
+                                                        unsigned int *bad, int members) {
   const IoBlock B = blocks[blockIdx.x];
+  if (!bounds::ok(B.member >= 0 && B.member < members, bounds::IO_BLOCK)) return;
+  if (!bounds::ok(B.start >= 0 && B.count >= 0 &&
+                      B.start + B.count <= (long long)views[B.member].g.nx * views[B.member].g.ny &&
+                      poff[B.member] + B.start + B.count <= total,
+                  bounds::IO_BLOCK))
+    return;
   const AuxView &a = views[B.member];
   const double *r = stage + poff[B.member];
   switch (a.dtype) {
@@ -237,8 +244,15 @@ __device__ __forceinline__ void batch_moments_block(const AuxView &a, const IoBl
 __global__ void __launch_bounds__(256) k_batch_moments_dev(const AuxView *__restrict__ views,
                                                            const IoBlock *__restrict__ blocks,
                                                            const long long *__restrict__ poff,
-                                                           long long total, double *stage) {
+                                                           long long total, double *stage,
+                                                           int members) {
   const IoBlock B = blocks[blockIdx.x];
+  if (!bounds::ok(B.member >= 0 && B.member < members, bounds::IO_BLOCK)) return;
+  if (!bounds::ok(B.start >= 0 && B.count >= 0 &&
+                      B.start + B.count <= (long long)views[B.member].g.nx * views[B.member].g.ny &&
+                      poff[B.member] + B.start + B.count <= total,
+                  bounds::IO_BLOCK))
+    return;
   const AuxView &a = views[B.member];
   double *r = stage + poff[B.member];
   switch (a.dtype) {
@@ -290,15 +304,17 @@ cudaError_t launch_batch_init_dev(const AuxView *views, const IoBlock *blocks, l
                                   unsigned int *bad, int members, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned int) * members, st);
   if (e != cudaSuccess || nblocks < 1) return e;
-  k_batch_init_dev<<<(unsigned)nblocks, 256, 0, st>>>(views, blocks, poff, total, stage, bad);
+  k_batch_init_dev<<<(unsigned)nblocks, 256, 0, st>>>(views, blocks, poff, total, stage, bad,
+                                                      members);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch_moments_dev(const AuxView *views, const IoBlock *blocks,
                                      long long nblocks, const long long *poff, long long total,
-                                     double *stage, cudaStream_t st) {
+                                     double *stage, int members, cudaStream_t st) {
   if (nblocks < 1) return cudaSuccess;
-  k_batch_moments_dev<<<(unsigned)nblocks, 256, 0, st>>>(views, blocks, poff, total, stage);
+  k_batch_moments_dev<<<(unsigned)nblocks, 256, 0, st>>>(views, blocks, poff, total, stage,
+                                                         members);
   return cudaGetLastError();
 }
 
@@ -314,5 +330,20 @@ cudaError_t launch_moments_dev(const AuxView &a, double *rho, double *ux, double
   }
   return cudaGetLastError();
 }
+
+// Debug-build self-test of the index checks: one checked access with an
+// index past its bound, which the check turns into index 0 of a one-element
+// array (so nothing outside it is touched) while setting the SELFTEST bit.
+__global__ void k_bounds_selftest(unsigned int *one) {
+  const int i = bounds::ck(threadIdx.x + 1, 1, bounds::SELFTEST);
+  one[i] = 1u;
+}
+
+cudaError_t launch_bounds_selftest(unsigned int *one, cudaStream_t st) {
+  k_bounds_selftest<<<1, 1, 0, st>>>(one);
+  return cudaGetLastError();
+}
+
+unsigned bounds_word_io(bool reset) { return bounds::read_word(reset); }
 
 }  // namespace lbm

@@ -15,6 +15,7 @@
 #include <string>
 #include <vector>
 
+#include "bounds.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -502,6 +503,26 @@ const char *lbm_strerror(int code) {
 }
 
 const char *lbm_last_error(void) { return g_last_error.c_str(); }
+
+int lbm_debug_bounds(unsigned int *word, int reset) {
+  REQUIRE(word != nullptr, "null argument");
+  const bool r = reset != 0;
+  *word = bounds_word_vn(r) | bounds_word_opt(r) | bounds_word_step_f32(r) |
+          bounds_word_step_f16(r) | bounds_word_step_bf16(r) | bounds_word_io(r);
+  REQUIRE(bounds::kEnabled, "built without LBM_DEBUG_BOUNDS");
+  return LBM_OK;
+}
+
+int lbm_debug_bounds_selftest(void) {
+  REQUIRE(bounds::kEnabled, "built without LBM_DEBUG_BOUNDS");
+  unsigned int *one = (unsigned int *)dev_alloc(sizeof(unsigned int));
+  REQUIRE(one != nullptr, "device allocation failed");
+  cudaError_t e = launch_bounds_selftest(one, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  dev_free(one);
+  CK(e);
+  return LBM_OK;
+}
 
 int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void *ctx) {
   if ((alloc == nullptr) != (free_fn == nullptr)) {
@@ -1835,7 +1856,7 @@ int lbm_batch_solve_packed(lbm_batch b, long n, const double *rho_in, const doub
   // downloaded from it
   CK(cudaStreamWaitEvent(b->stream, sl.ev[B::E_DN1], 0));
   CK(launch_batch_moments_dev(b->views[b->parity], b->ioblk, b->nioblk, b->poff_dev,
-                              (long long)T, sl.out, b->stream));
+                              (long long)T, sl.out, (int)nm, b->stream));
   CK(cudaEventRecord(sl.ev[B::E_MOM], b->stream));
   // download
   CK(cudaStreamWaitEvent(b->down, sl.ev[B::E_MOM], 0));

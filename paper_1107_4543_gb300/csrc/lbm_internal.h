@@ -168,7 +168,17 @@ cudaError_t launch_batch_init_dev(const AuxView *views, const IoBlock *blocks, l
                                   unsigned int *bad, int members, cudaStream_t st);
 cudaError_t launch_batch_moments_dev(const AuxView *views, const IoBlock *blocks,
                                      long long nblocks, const long long *poff, long long total,
-                                     double *stage, cudaStream_t st);
+                                     double *stage, int members, cudaStream_t st);
+
+// debug build (-DLBM_DEBUG_BOUNDS): each translation unit's index-check word
+// (bounds.cuh), optionally cleared; 0 without the flag
+unsigned bounds_word_vn(bool reset);
+unsigned bounds_word_opt(bool reset);
+unsigned bounds_word_step_f32(bool reset);
+unsigned bounds_word_step_f16(bool reset);
+unsigned bounds_word_step_bf16(bool reset);
+unsigned bounds_word_io(bool reset);
+cudaError_t launch_bounds_selftest(unsigned int *one, cudaStream_t st);
 cudaError_t launch_force_node(const AuxView &a, int x, int y, const double fs[9],
                               cudaStream_t st);
 cudaError_t launch_force_node_tab(const AuxView &a, int x, int y, const double *fs_dev,

@@ -37,6 +37,7 @@
 #include <string>
 #include <vector>
 
+#include "bounds.cuh"
 #include "lbm_internal.h"
 
 namespace {
@@ -82,7 +83,10 @@ __host__ __device__ __forceinline__ double rnorm(int k) {
                 : (k <= 2 ? 1.0 / 6.0 : (k <= 4 ? 1.0 / 36.0 : (k <= 6 ? 1.0 / 12.0 : 1.0 / 4.0)));
 }
 
-__device__ __forceinline__ int slot(int m, int d) { return m * (m - 1) / 2 + d; }
+__device__ __forceinline__ int slot(int m, int d) {
+  lbm::bounds::ok(m >= 1 && m <= NMAX && d >= 0 && d < m, lbm::bounds::OPT_SLOT);
+  return lbm::bounds::ck(m * (m - 1) / 2 + d, SLOTS, lbm::bounds::OPT_SLOT);
+}
 
 // B_s^p for p >= 2 (degrees 0..s-1) is kept for s = 1..NMAX-1 and
 // p = 2..NMAX-s+1: block index of its degree 0 (blocks of 3 x 3)
@@ -141,7 +145,10 @@ __device__ __forceinline__ double hx(const double *Hl, int r, const double *X, i
 
 // B_s^p, coefficient of degree d
 __device__ __forceinline__ const double *bpow(const PointMem &w, int s, int p, int d) {
-  return p == 1 ? w.B[slot(s, d)] : w.pw[pw_off(s, p) + d];
+  if (p == 1) return w.B[slot(s, d)];
+  lbm::bounds::ok(s >= 1 && s < NMAX && p >= 2 && p <= NMAX - s + 1 && d >= 0 && d < s,
+                  lbm::bounds::OPT_POW);
+  return w.pw[lbm::bounds::ck(pw_off(s, p) + d, PW_BLOCKS, lbm::bounds::OPT_POW)];
 }
 
 // 1 / s_r = sigma_r + 1/2 of a non-conserved row r (sigma_e, sigma_eps,
@@ -216,14 +223,17 @@ k_opt_points(CostSpec cs, const double *__restrict__ tab, const double *__restri
     const int id = (int)(q % cs.n_dir);
     const int iu = (int)(q / cs.n_dir);
     PointMem &P = w.pt[lane];
-    P.it = it;
-    P.kx = tab[T_CTH + it];
-    P.ky = tab[T_STH + it];
+    using lbm::bounds::ck;
+    using lbm::bounds::OPT_TAB;
+    P.it = ck(it, MAX_THETA, OPT_TAB);
+    P.kx = tab[T_CTH + P.it];
+    P.ky = tab[T_STH + P.it];
     double U = 0.0, V = 0.0, weight = cs.w_theta;
     if (cs.kind == 1) {
-      U = tab[T_SU + iu] * tab[T_CPH + id];
-      V = tab[T_SU + iu] * tab[T_SPH + id];
-      weight *= cs.w_dir * tab[T_WU + iu];
+      const int su = ck(iu, MAX_SPEED, OPT_TAB), dr = ck(id, MAX_DIR, OPT_TAB);
+      U = tab[T_SU + su] * tab[T_CPH + dr];
+      V = tab[T_SU + su] * tab[T_SPH + dr];
+      weight *= cs.w_dir * tab[T_WU + su];
     }
     P.U = U;
     P.V = V;
@@ -255,8 +265,11 @@ k_opt_points(CostSpec cs, const double *__restrict__ tab, const double *__restri
   // then columns 3..8 ((1 - s_c) / D_cc times column c of K_l)
   for (int e = lane; e < 27 * n * PPW; e += 32) {
     PointMem &P = w.pt[e % PPW];
-    const int f = e / PPW, l = f / 27, r = (f % 27) / 3, c = f % 3;
-    const double *Kr = ktab + ((long long)P.it * NMAX + l) * 81 + r * 9;
+    const int f = e / PPW, l = lbm::bounds::ck(f / 27, NMAX, lbm::bounds::OPT_H),
+              r = (f % 27) / 3, c = f % 3;
+    const double *Kr =
+        ktab + lbm::bounds::ck(((long long)P.it * NMAX + l) * 81 + r * 9,
+                               (long long)cs.n_theta * NMAX * 81, lbm::bounds::OPT_KTAB);
     double h = Kr[c] * rnorm(c);
 #pragma unroll
     for (int k = 3; k < 9; ++k) h += Kr[k] * P.q[(k - 3) * 3 + c];
@@ -264,8 +277,11 @@ k_opt_points(CostSpec cs, const double *__restrict__ tab, const double *__restri
   }
   for (int e = lane; e < 54 * n * PPW; e += 32) {
     PointMem &P = w.pt[e % PPW];
-    const int f = e / PPW, l = f / 54, r = (f % 54) / 6, c = 3 + f % 6;
-    P.H[l][r * 9 + c] = ktab[((long long)P.it * NMAX + l) * 81 + r * 9 + c] *
+    const int f = e / PPW, l = lbm::bounds::ck(f / 54, NMAX, lbm::bounds::OPT_H),
+              r = (f % 54) / 6, c = 3 + f % 6;
+    P.H[l][r * 9 + c] = ktab[lbm::bounds::ck(((long long)P.it * NMAX + l) * 81 + r * 9 + c,
+                                             (long long)cs.n_theta * NMAX * 81,
+                                             lbm::bounds::OPT_KTAB)] *
                         ((1.0 - rate(c, rs)) * rnorm(c));
   }
   __syncwarp();
@@ -286,7 +302,8 @@ k_opt_points(CostSpec cs, const double *__restrict__ tab, const double *__restri
           for (int k = 0; k < 3; ++k) acc += X[rc - c + k] * Pp[k * 3 + c];
         }
         v -= c_rfact[l] * acc;
-        v += hx(P.H[l - 1], r, P.phi[slot(s, d)], d, c);
+        v += hx(P.H[lbm::bounds::ck(l - 1, NMAX, lbm::bounds::OPT_H)], r, P.phi[slot(s, d)], d,
+                c);
       }
       P.phi[slot(m, t)][rc] = inv_rate(r, sg) * v;
     }
@@ -298,7 +315,8 @@ k_opt_points(CostSpec cs, const double *__restrict__ tab, const double *__restri
       double v = 0.0;
       for (int l = 1; l <= t && l < m; ++l) v -= c_rfact[l + 1] * bpow(P, m - l, l + 1, t - l)[rc];
       for (int l = 1; l <= m && l <= t + 1; ++l)
-        v += hx(P.H[l - 1], r, P.phi[slot(m + 1 - l, t - l + 1)], t - l + 1, c);
+        v += hx(P.H[lbm::bounds::ck(l - 1, NMAX, lbm::bounds::OPT_H)], r,
+                P.phi[slot(m + 1 - l, t - l + 1)], t - l + 1, c);
       P.B[slot(m, t)][rc] = v;
     }
     __syncwarp();
@@ -314,7 +332,7 @@ k_opt_points(CostSpec cs, const double *__restrict__ tab, const double *__restri
 #pragma unroll
           for (int k = 0; k < 3; ++k) acc += X[r * 3 + k] * Bb[k * 3 + c];
         }
-        P.pw[pw_off(m, pp) + d][rc] = acc;
+        P.pw[lbm::bounds::ck(pw_off(m, pp) + d, PW_BLOCKS, lbm::bounds::OPT_POW)][rc] = acc;
       }
       __syncwarp();
     }
@@ -336,7 +354,8 @@ k_opt_points(CostSpec cs, const double *__restrict__ tab, const double *__restri
       if ((cs.part == 1 && !odd_l) || (cs.part == 2 && odd_l)) continue;
       for (int mq = l & 1; mq < n; mq += 2) {  // odd l - mq: Re (-i)^(l-mq) = 0
         const double sgn = ((l - mq) & 3) == 0 ? 1.0 : -1.0;
-        acc += sgn * (E[l][e] * E[mq][e]) * tab[T_KINT + l + mq + 3];
+        acc += sgn * (E[l][e] * E[mq][e]) *
+               tab[T_KINT + lbm::bounds::ck(l + mq + 3, 2 * NMAX + 2, lbm::bounds::OPT_TAB)];
       }
     }
     P.part[e] = acc;
@@ -743,3 +762,7 @@ int lbm_opt_minimize(const lbm_cost_spec *spec, const double sigmas_in[4], unsig
 }
 
 }  // extern "C"
+
+namespace lbm {
+unsigned bounds_word_opt(bool reset) { return bounds::read_word(reset); }
+}  // namespace lbm

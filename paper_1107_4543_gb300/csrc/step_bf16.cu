@@ -13,4 +13,6 @@ cudaError_t launch_step_batch_bf16(const BatchList &bl, int parity, cudaStream_t
   return launch_step_batch_t<__nv_bfloat16>(bl, parity, st, block, variant, limits, k);
 }
 
+unsigned bounds_word_step_bf16(bool reset) { return bounds::read_word(reset); }
+
 }  // namespace lbm

@@ -12,6 +12,7 @@
 #pragma once
 #include <type_traits>
 
+#include "bounds.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -26,6 +27,9 @@ __device__ __forceinline__ void step_task(const T *__restrict__ src, T *__restri
   constexpr bool SCALED = std::is_same<T, __half>::value;
   constexpr bool PRECISE = std::is_same<T, float>::value;
   LanePos p = lane_pos<V>(g, task, lane);
+  if (!bounds::ok(!p.active || (p.y >= 0 && p.y < g.ny && p.x0 >= 0 && p.x0 + V <= g.pitch),
+                  bounds::BATCH_LANE))
+    p.active = false;
   if constexpr (sizeof(T) == 2) {
     // 16-bit storage: pull packed, then unpack / collide / repack two nodes
     // at a time (9 x V floats per lane would not fit the register budget)
@@ -89,11 +93,12 @@ k_step_dev(const T *__restrict__ src, T *__restrict__ dst, Geom g, DevParams P,
 template <typename T, int MINB>
 __global__ void __launch_bounds__(256, MINB)
 k_step_batch(const BatchEntry *__restrict__ ents, const BlockRec *__restrict__ blocks,
-             int parity, const int *__restrict__ limits, int k) {
+             int nents, int parity, const int *__restrict__ limits, int k) {
   const int lane = threadIdx.x & 31;
   const BlockRec &B = blocks[blockIdx.x];
   const long long task = B.task_base + (threadIdx.x >> 5);
   if (task >= B.g.tasks) return;                         // warp-uniform
+  if (!bounds::ok(B.lat >= 0 && B.lat < nents, bounds::BATCH_REC)) return;
   if (limits != nullptr && k >= limits[B.lat]) return;   // block-uniform
   const int from = parity ^ B.off;
   step_task<T>(static_cast<const T *>(B.buf[from]), static_cast<T *>(B.buf[from ^ 1]), B.g,
@@ -112,7 +117,8 @@ static inline long long n_tasks(const Geom &g) { return g.tasks; }
 template <typename T, int MINB>
 __global__ void __launch_bounds__(256, MINB)
 k_step_batch_stride(const BatchEntry *__restrict__ ents, const BlockRec *__restrict__ blocks,
-                    long long nblocks, int parity, const int *__restrict__ limits, int k) {
+                    long long nblocks, int nents, int parity, const int *__restrict__ limits,
+                    int k) {
   constexpr int NW = sizeof(BlockRec) / 4;
   static_assert(sizeof(BlockRec) % 4 == 0 && NW <= 32, "a record must fit one word per lane");
   __shared__ BlockRec rec[2][8];
@@ -131,7 +137,8 @@ k_step_batch_stride(const BatchEntry *__restrict__ ents, const BlockRec *__restr
     if (nb < nblocks && lane < NW) next = __ldg(reinterpret_cast<const uint32_t *>(blocks + nb) + lane);
     const BlockRec &B = rec[s][w];
     const long long task = B.task_base + w;
-    if (task < B.g.tasks && !(limits != nullptr && k >= limits[B.lat])) {  // warp-uniform
+    if (task < B.g.tasks && bounds::ok(B.lat >= 0 && B.lat < nents, bounds::BATCH_REC) &&
+        !(limits != nullptr && k >= limits[B.lat])) {  // warp-uniform
       const int from = parity ^ B.off;
       step_task<T>(static_cast<const T *>(B.buf[from]), static_cast<T *>(B.buf[from ^ 1]), B.g,
                    ents[B.lat].dp, task, lane);
@@ -175,15 +182,15 @@ cudaError_t launch_step_batch_t(const BatchList &bl, int parity, cudaStream_t st
     switch (minb) {
       case 1:
         k_step_batch_stride<T, 1><<<(unsigned)pgrid, block, 0, st>>>(
-            bl.ents, bl.blocks, bl.nblocks, parity, limits, k);
+            bl.ents, bl.blocks, bl.nblocks, bl.n, parity, limits, k);
         break;
       case 2:
         k_step_batch_stride<T, 2><<<(unsigned)pgrid, block, 0, st>>>(
-            bl.ents, bl.blocks, bl.nblocks, parity, limits, k);
+            bl.ents, bl.blocks, bl.nblocks, bl.n, parity, limits, k);
         break;
       default:
         k_step_batch_stride<T, 3><<<(unsigned)pgrid, block, 0, st>>>(
-            bl.ents, bl.blocks, bl.nblocks, parity, limits, k);
+            bl.ents, bl.blocks, bl.nblocks, bl.n, parity, limits, k);
         break;
     }
     return cudaGetLastError();
@@ -191,13 +198,13 @@ cudaError_t launch_step_batch_t(const BatchList &bl, int parity, cudaStream_t st
   const unsigned grid = (unsigned)bl.nblocks;
   switch (variant) {
     case 0:
-      k_step_batch<T, 1><<<grid, block, 0, st>>>(bl.ents, bl.blocks, parity, limits, k);
+      k_step_batch<T, 1><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits, k);
       break;
     case 1:
-      k_step_batch<T, 2><<<grid, block, 0, st>>>(bl.ents, bl.blocks, parity, limits, k);
+      k_step_batch<T, 2><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits, k);
       break;
     default:
-      k_step_batch<T, 3><<<grid, block, 0, st>>>(bl.ents, bl.blocks, parity, limits, k);
+      k_step_batch<T, 3><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits, k);
       break;
   }
   return cudaGetLastError();

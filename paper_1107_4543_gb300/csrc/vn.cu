@@ -20,6 +20,7 @@
 #include <new>
 #include <string>
 
+#include "bounds.cuh"
 #include "lbm_internal.h"
 
 namespace {
@@ -89,13 +90,14 @@ __device__ void hessenberg(cplx A[9][9]) {
     for (int i = k + 1; i < N; ++i) nrm += A[i][k].re * A[i][k].re + A[i][k].im * A[i][k].im;
     nrm = sqrt(nrm);
     if (nrm == 0.0) continue;
-    const cplx x0 = A[k + 1][k];
+    const int k1 = lbm::bounds::ck(k + 1, N, lbm::bounds::VN_HESS);
+    const cplx x0 = A[k1][k];
     const double a0 = cabs(x0);
     const cplx ph = a0 > 0 ? scale(x0, 1.0 / a0) : mk(1, 0);
     cplx v[9];
     for (int i = 0; i < N; ++i) v[i] = mk(0, 0);
     // v = x + e^{i arg x0} ||x|| e1, normalized
-    v[k + 1] = add(x0, scale(ph, nrm));
+    v[k1] = add(x0, scale(ph, nrm));
     for (int i = k + 2; i < N; ++i) v[i] = A[i][k];
     double vn = 0;
     for (int i = k + 1; i < N; ++i) vn += v[i].re * v[i].re + v[i].im * v[i].im;
@@ -131,9 +133,10 @@ __device__ int hqr(cplx H[9][9], cplx ev[9]) {
     }
     int l = hi;
     for (; l > 0; --l) {
-      const double s = cabs(H[l - 1][l - 1]) + cabs(H[l][l]);
-      if (cabs(H[l][l - 1]) <= eps * (s > 0 ? s : 1.0)) {
-        H[l][l - 1] = mk(0, 0);
+      const int lm = lbm::bounds::ck(l - 1, N, lbm::bounds::VN_HQR);
+      const double s = cabs(H[lm][lm]) + cabs(H[l][l]);
+      if (cabs(H[l][lm]) <= eps * (s > 0 ? s : 1.0)) {
+        H[l][lm] = mk(0, 0);
         break;
       }
     }
@@ -153,10 +156,11 @@ __device__ int hqr(cplx H[9][9], cplx ev[9]) {
     // Wilkinson shift from the trailing 2x2 block; an exceptional shift
     // every 11 sweeps breaks cycles
     cplx mu;
+    const int hm = lbm::bounds::ck(hi - 1, N, lbm::bounds::VN_HQR);
     if (iter > 0 && iter % 11 == 0) {
-      mu = add(H[hi][hi], mk(fabs(H[hi][hi - 1].re) + fabs(H[hi - 1][hi > 1 ? hi - 2 : 0].re), 0));
+      mu = add(H[hi][hi], mk(fabs(H[hi][hm].re) + fabs(H[hm][hi > 1 ? hi - 2 : 0].re), 0));
     } else {
-      const cplx a = H[hi - 1][hi - 1], b = H[hi - 1][hi], c = H[hi][hi - 1], d = H[hi][hi];
+      const cplx a = H[hm][hm], b = H[hm][hi], c = H[hi][hm], d = H[hi][hi];
       const cplx half_tr = scale(add(a, d), 0.5);
       const cplx det = sub(mul(a, d), mul(b, c));
       const cplx disc = csqrt(sub(mul(half_tr, half_tr), det));
@@ -169,7 +173,8 @@ __device__ int hqr(cplx H[9][9], cplx ev[9]) {
     cplx gs[9];
     for (int i = l; i <= hi; ++i) H[i][i] = sub(H[i][i], mu);
     for (int k = l; k < hi; ++k) {
-      const cplx x = H[k][k], y = H[k + 1][k];
+      const int k1 = lbm::bounds::ck(k + 1, N, lbm::bounds::VN_HQR);
+      const cplx x = H[k][k], y = H[k1][k];
       const double ax = cabs(x), r = hypot(ax, cabs(y));
       double c;
       cplx s;
@@ -186,19 +191,20 @@ __device__ int hqr(cplx H[9][9], cplx ev[9]) {
       gc[k] = c;
       gs[k] = s;
       for (int j = k; j <= hi; ++j) {
-        const cplx hk = H[k][j], hk1 = H[k + 1][j];
+        const cplx hk = H[k][j], hk1 = H[k1][j];
         H[k][j] = add(scale(hk, c), mul(s, hk1));
-        H[k + 1][j] = sub(scale(hk1, c), mul(conj(s), hk));
+        H[k1][j] = sub(scale(hk1, c), mul(conj(s), hk));
       }
     }
     for (int k = l; k < hi; ++k) {
       const double c = gc[k];
       const cplx s = gs[k];
-      const int top = k + 2 < hi ? k + 2 : hi;
+      const int top = lbm::bounds::ck(k + 2 < hi ? k + 2 : hi, N, lbm::bounds::VN_HQR);
+      const int k1 = lbm::bounds::ck(k + 1, N, lbm::bounds::VN_HQR);
       for (int i = l; i <= top; ++i) {
-        const cplx hk = H[i][k], hk1 = H[i][k + 1];
+        const cplx hk = H[i][k], hk1 = H[i][k1];
         H[i][k] = add(scale(hk, c), mul(hk1, conj(s)));
-        H[i][k + 1] = sub(scale(hk1, c), mul(hk, s));
+        H[i][k1] = sub(scale(hk1, c), mul(hk, s));
       }
     }
     for (int i = l; i <= hi; ++i) H[i][i] = add(H[i][i], mu);
@@ -390,3 +396,7 @@ extern "C" int lbm_vn_eigs(int n, const double *kx, const double *ky, const doub
   if (unconverged) *unconverged = fails;
   return fails ? LBM_ETIMEOUT : LBM_OK;
 }
+
+namespace lbm {
+unsigned bounds_word_vn(bool reset) { return bounds::read_word(reset); }
+}  // namespace lbm

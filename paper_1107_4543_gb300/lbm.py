@@ -129,6 +129,8 @@ _SIGS = {
     "lbm_slab_pack": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "lbm_slab_unpack": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "lbm_batch_wait": (ctypes.c_int, [_vp, _dp]),
+    "lbm_debug_bounds": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint), ctypes.c_int]),
+    "lbm_debug_bounds_selftest": (ctypes.c_int, []),
     "lbm_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_long, ctypes.POINTER(_vp)]),
     "lbm_submit": (ctypes.c_int, [_vp, ctypes.POINTER(lbm_request),
                                   ctypes.POINTER(ctypes.c_longlong)]),
@@ -570,6 +572,18 @@ def lbm_slab_pack(h, reverse, to_below, to_above):
 def lbm_slab_unpack(h, reverse, from_below, from_above):
     _ck(load().lbm_slab_unpack(h, int(bool(reverse)), _vp(_dev(from_below)),
                                _vp(_dev(from_above))), "lbm_slab_unpack")
+
+
+def lbm_debug_bounds(reset=False):
+    """The debug build's index-check word (0: no failed check); raises on a
+    library built without the checks."""
+    w = ctypes.c_uint()
+    _ck(load().lbm_debug_bounds(ctypes.byref(w), int(bool(reset))), "lbm_debug_bounds")
+    return w.value
+
+
+def lbm_debug_bounds_selftest():
+    _ck(load().lbm_debug_bounds_selftest(), "lbm_debug_bounds_selftest")
 
 
 BATCH_PHASES = ("h2d_ms", "init_ms", "steps_ms", "drift_ms", "moments_ms", "d2h_ms")
