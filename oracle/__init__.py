@@ -137,6 +137,32 @@ def run_source(f, s, nsteps, source, t0=0, rho0=1.0):
     return f
 
 
+_lib_ext = None
+
+
+def run_ext(f, s, nsteps):
+    """As run, with the collision and streaming in extended precision (the
+    same C source built with long double arithmetic; FP64 in and out).  The
+    reference for GPU paths whose FP64 rounding differs from the plain
+    oracle's."""
+    global _lib_ext
+    if _lib_ext is None:
+        lib = ctypes.CDLL(_build.build(ext=True))
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.orc_run.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_long]
+        lib.orc_run.restype = ctypes.c_int
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        _lib_ext = lib
+    _lib_ext.orc_set_threads(threads())
+    f = np.array(f, dtype=np.float64, order="C")
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    _, ny, nx = f.shape
+    rc = _lib_ext.orc_run(nx, ny, _p(s), _p(f), int(nsteps))
+    if rc != 0:
+        raise RuntimeError("orc_run (extended) failed (%d)" % rc)
+    return f
+
+
 def moments(f):
     """(rho, ux, uy) of populations f (9, ny, nx)."""
     f = np.ascontiguousarray(f, dtype=np.float64)

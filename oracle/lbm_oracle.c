@@ -30,6 +30,15 @@
  * Periodic in x and y.  All arithmetic is IEEE FP64; build with
  * -ffp-contract=off so that no multiply-add is fused.
  *
+ * The arithmetic type of the collision and streaming is `real`, FP64 unless
+ * the file is compiled with -DORC_REAL="long double": that second build
+ * (oracle/_build/liboracle_ext.so, the same algorithm in extended precision:
+ * 64-bit significand on x86-64, IEEE quadruple on AArch64) is the reference
+ * for GPU paths whose FP64 rounding differs from this file's, since the FP64
+ * oracle's own rounding of populations of size ~0.4 is larger than the
+ * 1e-12 relative gate of a density fluctuation of 1e-3 over hundreds of
+ * steps.  The entry points keep FP64 arguments in both builds.
+ *
  * Parity pins (tests/test_oracle_*.py): M M^T diagonal; M^-1 m^eq equal to the
  * textbook second-order polynomial equilibrium; the Jacobian of m^eq equal to
  * the printed Psi of section 2.3; exact conservation; equilibria as fixed
@@ -45,6 +54,11 @@
 #endif
 
 #define Q 9
+
+#ifndef ORC_REAL
+#define ORC_REAL double
+#endif
+typedef ORC_REAL real;
 
 /* discrete velocities (reading, see header) */
 static const int CX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -86,8 +100,8 @@ void orc_matrices(double M[Q * Q], double Minv[Q * Q]) {
 }
 
 /* equilibrium moments of section 2.3, in the paper's order */
-void orc_meq(double rho, double jx, double jy, double meq[Q]) {
-    double jsq = jx * jx + jy * jy;
+static void meq_r(real rho, real jx, real jy, real meq[Q]) {
+    real jsq = jx * jx + jy * jy;
     meq[0] = rho;
     meq[1] = jx;
     meq[2] = jy;
@@ -99,33 +113,53 @@ void orc_meq(double rho, double jx, double jy, double meq[Q]) {
     meq[8] = jx * jy / rho;
 }
 
-/* M^-1, built once from M */
-static double g_Minv[Q * Q];
+void orc_meq(double rho, double jx, double jy, double meq[Q]) {
+    real m[Q];
+    meq_r(rho, jx, jy, m);
+    for (int k = 0; k < Q; ++k) meq[k] = (double)m[k];
+}
+
+/* M^-1 = M^T D^-1, built once from M in the arithmetic type */
+static real g_Minv[Q * Q];
 static int g_ready = 0;
 
 static void ensure_tables(void) {
-    double M[Q * Q];
-    if (!g_ready) { orc_matrices(M, g_Minv); g_ready = 1; }
+    if (g_ready) return;
+    real D[Q];
+    for (int k = 0; k < Q; ++k) {
+        D[k] = 0.0;
+        for (int j = 0; j < Q; ++j) D[k] += (real)MM[k][j] * (real)MM[k][j];
+    }
+    for (int i = 0; i < Q; ++i)
+        for (int k = 0; k < Q; ++k) g_Minv[i * Q + k] = (real)MM[k][i] / D[k];
+    g_ready = 1;
 }
 
 /* one MRT collision at a node, in place: m = M f; m* = m - S (m - m^eq);
    f* = M^-1 m*, written as f - M^-1 S (m - m^eq).  s[] in paper order. */
-void orc_collide(const double s[Q], double f[Q]) {
-    const double *Minv = g_Minv;
-    double m[Q], meq[Q], r[Q];
-    ensure_tables();
+static void collide_r(const real s[Q], real f[Q]) {
+    const real *Minv = g_Minv;
+    real m[Q], meq[Q], r[Q];
     for (int k = 0; k < Q; ++k) {
-        double acc = 0.0;
-        for (int j = 0; j < Q; ++j) acc += MM[k][j] * f[j];
+        real acc = 0.0;
+        for (int j = 0; j < Q; ++j) acc += (real)MM[k][j] * f[j];
         m[k] = acc;
     }
-    orc_meq(m[0], m[1], m[2], meq);
+    meq_r(m[0], m[1], m[2], meq);
     for (int k = 0; k < Q; ++k) r[k] = s[k] * (m[k] - meq[k]);
     for (int i = 0; i < Q; ++i) {
-        double acc = 0.0;
+        real acc = 0.0;
         for (int k = 0; k < Q; ++k) acc += Minv[i * Q + k] * r[k];
         f[i] = f[i] - acc;
     }
+}
+
+void orc_collide(const double s[Q], double f[Q]) {
+    real sr[Q], fr[Q];
+    ensure_tables();
+    for (int k = 0; k < Q; ++k) { sr[k] = s[k]; fr[k] = f[k]; }
+    collide_r(sr, fr);
+    for (int k = 0; k < Q; ++k) f[k] = (double)fr[k];
 }
 
 static inline int wrap(int a, int n) { a %= n; return a < 0 ? a + n : a; }
@@ -137,26 +171,31 @@ int orc_run(int nx, int ny, const double s[Q], double *f, long nsteps) {
     if (nx < 1 || ny < 1 || nsteps < 0) return -1;
     ensure_tables(); /* built once, before any thread starts */
     size_t plane = (size_t)nx * (size_t)ny;
-    double *g = (double *)malloc(sizeof(double) * Q * plane);
-    if (!g) return -1;
-    double *src = f, *dst = g;
+    real *a = (real *)malloc(sizeof(real) * Q * plane);
+    real *g = (real *)malloc(sizeof(real) * Q * plane);
+    if (!a || !g) { free(a); free(g); return -1; }
+    real sr[Q];
+    for (int k = 0; k < Q; ++k) sr[k] = s[k];
+    for (size_t n = 0; n < Q * plane; ++n) a[n] = f[n];
+    real *src = a, *dst = g;
     for (long t = 0; t < nsteps; ++t) {
 #pragma omp parallel for num_threads(g_threads) schedule(static)
         for (int y = 0; y < ny; ++y) {
             for (int x = 0; x < nx; ++x) {
-                double fn[Q];
+                real fn[Q];
                 size_t n = (size_t)y * nx + x;
                 for (int i = 0; i < Q; ++i) fn[i] = src[i * plane + n];
-                orc_collide(s, fn);
+                collide_r(sr, fn);
                 for (int i = 0; i < Q; ++i) {
                     int xd = wrap(x + CX[i], nx), yd = wrap(y + CY[i], ny);
                     dst[i * plane + (size_t)yd * nx + xd] = fn[i];
                 }
             }
         }
-        double *tmp = src; src = dst; dst = tmp;
+        real *tmp = src; src = dst; dst = tmp;
     }
-    if (src != f) memcpy(f, src, sizeof(double) * Q * plane);
+    for (size_t n = 0; n < Q * plane; ++n) f[n] = (double)src[n];
+    free(a);
     free(g);
     return 0;
 }

@@ -660,3 +660,30 @@ def test_llstar_mean_flow_has_growing_mode():
     assert 1.0009 < g[j] < 1.0011
     assert abs(abs(kx[j]) - 3 * np.pi / 4) < 0.05
     assert 6.0 < g[j] ** 2000 < 8.5
+
+
+# ------------------------------------------- the extended-precision build
+def test_extended_oracle_is_the_same_scheme():
+    """oracle.run_ext is lbm_oracle.c built with long double arithmetic.  It
+    must be the same scheme: on config 1 it agrees with the FP64 build to the
+    FP64 build's own rounding (6e-12 relative L2 of rho' after 200 steps,
+    the populations of size ~0.4 rounded every step against a 1e-3
+    fluctuation), it is not bit-identical to it (the wider type is in
+    effect), and at amplitude 1e-7 it follows the exact linear evolution of
+    section 4.1 as the FP64 build does."""
+    r = inp.rates("LL", nu=1e-3)
+    s = inp.s_paper(r)
+    f0 = orc.init_eq(*inp.gaussian_pulse(64, 64, 1e-3, 4.0))
+    fe = orc.run_ext(f0, s, 200)
+    fd = orc.run(f0, s, 200)
+    re, rd = fe.sum(axis=0) - 1.0, fd.sum(axis=0) - 1.0
+    rel = np.linalg.norm(rd - re) / np.linalg.norm(re)
+    assert 1e-13 < rel < 2e-11
+    nx, ny, T = 24, 16, 40
+    s = inp.s_paper(inp.rates("OPT"))
+    rng = np.random.default_rng(5)
+    base = orc.init_eq(np.ones((ny, nx)), np.full((ny, nx), 0.1), np.zeros((ny, nx)))
+    fp = 1e-7 * rng.standard_normal((9, ny, nx)) * base
+    got = orc.run_ext(base + fp, s, T) - base
+    want = vn.propagate_linear(fp, T, 0.1, 0.0, s)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-6
