@@ -45,9 +45,10 @@ sys.path.insert(0, ROOT)
 
 import lbm_inputs as inp  # noqa: E402
 
-BYTES_PER_LU = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}
+BYTES_PER_LU = {"f64": 144, "f64dev": 144, "f32": 72, "f16": 36, "bf16": 36}
 KERNEL_SOURCES = ["csrc/step_impl.cuh", "csrc/d2q9_pull.cuh", "csrc/collide.cuh",
-                  "csrc/step_f32.cu", "csrc/step_f16.cu", "csrc/step_bf16.cu", "csrc/step_f64.cu"]
+                  "csrc/step_f32.cu", "csrc/step_f16.cu", "csrc/step_bf16.cu", "csrc/step_f64.cu",
+                  "csrc/step_f64dev.cu"]
 
 
 def parser():
@@ -68,7 +69,7 @@ def parser():
     p.add_argument("--policy", default="fifo", choices=["fifo", "shortest"])
     p.add_argument("--max-nodes", type=int, default=0, help="server resident-node cap")
     p.add_argument("--size", type=int, default=8192, help="side of the large lattice")
-    p.add_argument("--dtypes", default="f32,f16,bf16,f64", help="storage types (large)")
+    p.add_argument("--dtypes", default="f32,f16,bf16,f64,f64dev", help="storage types (large)")
     p.add_argument("--batch-dtype", default="f32", choices=["f32", "f16", "bf16"],
                    help="storage type of the batched workload")
     p.add_argument("--batch-variant", type=int, default=-1,
@@ -270,10 +271,12 @@ def setup_batch(L, torch, specs, dtype, stream):
     return hs, fields
 
 
-def fp64_plain(L, torch, stream, n=8192, steps=20):
-    """Plain FP64 path on one n x n lattice (pulse + vortices), MLUPS."""
+def fp64_plain(L, torch, stream, n=8192, steps=20, dtype=None):
+    """An FP64 path on one n x n lattice (Gaussian pulse), MLUPS: the plain
+    one (bit-identical to the FP64 oracle) or, with dtype LBM_F64DEV, FP64
+    deviations collided with fused multiply-adds."""
     r = inp.rates("OPT")
-    h = L.lbm_create(n, n, inp.s_ll(r), 1.0, (0.0, 0.0), L.LBM_F64)
+    h = L.lbm_create(n, n, inp.s_ll(r), 1.0, (0.0, 0.0), L.LBM_F64 if dtype is None else dtype)
     try:
         L.lbm_set_stream(h, stream)
         L.lbm_init_analytic(h, L.LBM_INIT_GAUSSIAN, (1e-3, 20.0, n / 2, n / 2))
@@ -385,8 +388,14 @@ def bench_batched(args, L, torch, rank, ws):
     fp64 = None
     if not args.no_fp64:
         mlups64, ms64 = fp64_plain(L, torch, stream)
-        fp64 = {"workload": "single 8192x8192 lattice, plain FP64 full populations",
-                "mlups": round(mlups64, 1), "ms_per_lbm_step": round(ms64, 3)}
+        mlupsd, msd = fp64_plain(L, torch, stream, dtype=L.LBM_F64DEV)
+        fp64 = {"workload": "single 8192x8192 lattice, plain FP64 full populations "
+                            "(bit-identical to the FP64 oracle)",
+                "mlups": round(mlups64, 1), "ms_per_lbm_step": round(ms64, 3),
+                "fp64_fma": {"workload": "the same lattice in FP64 deviation storage, FP64 "
+                                         "collision with fused multiply-adds (within 1e-12 of "
+                                         "the extended-precision oracle)",
+                             "mlups": round(mlupsd, 1), "ms_per_lbm_step": round(msd, 3)}}
     for h in hs:
         L.lbm_destroy(h)
 
@@ -484,7 +493,7 @@ def bench_large(args, L, torch, rank, ws):
     lines = []
     peak, peak_kind = peaks()
     for dtype in args.dtypes.split(","):
-        lbm_steps = 50 if dtype != "f64" else 10
+        lbm_steps = 50 if not dtype.startswith("f64") else 10
         mlups, launch_ms = large_one(L, torch, stream, n, dtype, lbm_steps, args.steps,
                                      args.warmup)
         achieved = BYTES_PER_LU[dtype] * n * n / (launch_ms * 1e-3) / 1e9
@@ -510,12 +519,13 @@ def config3_record(L, torch):
     out = {"workload": "single-8192x8192-1000-steps", "note": "one timed run of 1000 steps "
            "after 2 x 50 warm-up steps; 2.4-9.7 GB of populations per type (> L2)"}
     kern = {"f32": "k_step_dev<float>", "f16": "k_step_dev<__half>",
-            "bf16": "k_step_dev<__nv_bfloat16>", "f64": "k_step_f64"}
-    for dtype in ("f32", "f16", "bf16", "f64"):
+            "bf16": "k_step_dev<__nv_bfloat16>", "f64": "k_step_f64",
+            "f64dev": "k_step_dev<double>"}
+    for dtype in ("f32", "f16", "bf16", "f64", "f64dev"):
         mlups, ms = large_one(L, torch, stream, n, dtype, steps, 1, 2)
         achieved = BYTES_PER_LU[dtype] * n * n / (ms * 1e-3) / 1e9
         out[dtype] = {"mlups": round(mlups, 1), "ms_per_lbm_step": round(ms, 4),
-                      "roofline": {"bound": "hbm" if dtype != "f64" else "fp64-alu",
+                      "roofline": {"bound": "hbm" if not dtype.startswith("f64") else "fp64-alu",
                                    "kernel": kern[dtype], "achieved": round(achieved, 1),
                                    "peak": peak, "unit": "GB/s",
                                    "frac": round(achieved / peak, 4), "peak_source": peak_kind}}

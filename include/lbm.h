@@ -54,13 +54,18 @@ extern "C" {
 #define LBM_ECLOSED (-7)   /* server shutting down                         */
 
 /* storage types of the populations.  The *DEV types store the deviation
- * f' = f - f^eq(rho0, u0) and collide in FP32; LBM_F64 stores the full
+ * f' = f - f^eq(rho0, u0); the 32- and 16-bit ones collide in FP32,
+ * LBM_F64DEV in FP64 with fused multiply-adds.  LBM_F64 stores the full
  * populations and computes in FP64 with the operation order of a plain
- * matrix-vector implementation of section 2.1. */
+ * matrix-vector implementation of section 2.1 (bit-identical to a plain
+ * FP64 implementation); LBM_F64DEV is the faster FP64 path, within 1e-12
+ * relative of an extended-precision implementation of the same scheme.
+ * Batches and the server take the 32- and 16-bit types. */
 #define LBM_F64 0
 #define LBM_F32DEV 1
 #define LBM_F16DEV 2  /* FP16, scaled by a power of two fixed at init */
 #define LBM_BF16DEV 3
+#define LBM_F64DEV 4
 
 typedef struct lbm_ctx *lbm_handle;
 
@@ -75,7 +80,8 @@ typedef struct lbm_ctx *lbm_handle;
  *          p entries.
  *   rho0, u0[2]  reference state: the base f^eq(rho0, u0) of the
  *          deviation storage types and the initial uniform state.
- *   storage_dtype  LBM_F64 / LBM_F32DEV / LBM_F16DEV / LBM_BF16DEV.
+ *   storage_dtype  LBM_F64 / LBM_F32DEV / LBM_F16DEV / LBM_BF16DEV /
+ *                  LBM_F64DEV.
  * The lattice starts as the uniform equilibrium f^eq(rho0, u0).
  * Errors: LBM_EINVAL (nx or ny < 2, rates out of range, rho0 <= 0, null
  * out), LBM_ENOMEM, LBM_ECUDA (no GPU).  *out is set only on success. */
@@ -224,7 +230,7 @@ int lbm_drift_pop_noalloc(const double *f_dev, int nx, int ny, double rho0,
 typedef struct {
   int nx, ny;
   int pitch;          /* elements per stored row (>= nx)                */
-  int dtype;          /* LBM_F64 ... LBM_BF16DEV                         */
+  int dtype;          /* LBM_F64 ... LBM_F64DEV                          */
   int elem_bytes;     /* bytes per stored population                     */
   long t;             /* time steps taken since the last init/set        */
   double qscale;      /* LBM_F16DEV: stored value = f' * qscale          */

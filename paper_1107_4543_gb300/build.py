@@ -22,6 +22,7 @@ UNITS = {
     "step_f32.cu": [],
     "step_f16.cu": [],
     "step_bf16.cu": [],
+    "step_f64dev.cu": [],
     "step_f64.cu": ["-fmad=false"],
     "aux.cu": ["-fmad=false"],
     "io_dev.cu": [],

@@ -57,7 +57,8 @@ __device__ __forceinline__ int wrapi(int a, int n) {
 
 __device__ __forceinline__ double load_stored(const AuxView &a, long long idx) {
   switch (a.dtype) {
-    case LBM_F64: return static_cast<const double *>(a.buf)[idx];
+    case LBM_F64:
+    case LBM_F64DEV: return static_cast<const double *>(a.buf)[idx];
     case LBM_F32DEV: return (double)static_cast<const float *>(a.buf)[idx];
     case LBM_F16DEV: return (double)__half2float(static_cast<const __half *>(a.buf)[idx]) / a.scale;
     default: return (double)__bfloat162float(static_cast<const __nv_bfloat16 *>(a.buf)[idx]);
@@ -68,6 +69,7 @@ __device__ __forceinline__ double load_stored(const AuxView &a, long long idx) {
 __device__ __forceinline__ void store_value(const AuxView &a, long long idx, int i, double fv) {
   switch (a.dtype) {
     case LBM_F64: static_cast<double *>(a.buf)[idx] = fv; break;
+    case LBM_F64DEV: static_cast<double *>(a.buf)[idx] = fv - a.f0[i]; break;
     case LBM_F32DEV: static_cast<float *>(a.buf)[idx] = (float)(fv - a.f0[i]); break;
     case LBM_F16DEV:
       static_cast<__half *>(a.buf)[idx] = __float2half_rn((float)((fv - a.f0[i]) * a.scale));
@@ -287,16 +289,18 @@ struct FF {
 // many times its FP64 rate, and the 9-term sums keep ~48 bits).
 __device__ __forceinline__ void node_sums(const AuxView &a, long long off, double &r, double &jx,
                                           double &jy, double &bad) {
-  if (a.dtype == LBM_F64) {
+  if (a.dtype == LBM_F64 || a.dtype == LBM_F64DEV) {
     // deviations from the base populations first: f_i - f0_i is exact while
     // f_i stays within a factor two of f0_i (Sterbenz), so the node's sums
     // round at the size of the perturbation, not at the size of f
+    // (LBM_F64DEV stores the deviations themselves)
+    const double sub = a.dtype == LBM_F64 ? 1.0 : 0.0;
     double d[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const double v = static_cast<const double *>(a.buf)[(long long)i * a.g.plane + off];
       if (!isfinite(v)) { bad += 1.0; d[i] = 0.0; }
-      else d[i] = v - a.f0[i];
+      else d[i] = v - sub * a.f0[i];
     }
     r = d[0] + d[1] + d[2] + d[3] + d[4] + d[5] + d[6] + d[7] + d[8];
     jx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];

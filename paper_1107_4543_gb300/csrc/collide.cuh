@@ -245,6 +245,65 @@ __device__ __forceinline__ void collide_pair(F2 &f0, F2 &f1, F2 &f2_, F2 &f3, F2
   f8 = f8 - ((bp - r6) - r8);
 }
 
+// ------------------------------------------------------------------
+// FP64 deviation storage (LBM_F64DEV): the deviation form of collide_dev in
+// FP64 with fused multiply-adds -- fewer and cheaper FP64 operations than the
+// plain path's canonical operation order (GB300's FP64 units bound both),
+// and rounding at the size of the perturbation, not of f.
+struct DevParams64 {
+  double rho0, jx0, jy0;          // reference state
+  double k3, k4, k5, k6, k7, k8;  // s/D: s_e/36, s_eps/36, s_qx/12, s_qy/12, s_pxx/4, s_pxy/4
+  double q0, d0, x0;              // |j0|^2, jx0^2 - jy0^2, jx0 jy0
+  double i2;                      // 1 / rho0^2
+};
+
+__device__ __forceinline__ void collide_dev64(double &f0, double &f1, double &f2, double &f3,
+                                              double &f4, double &f5, double &f6, double &f7,
+                                              double &f8, const DevParams64 &P) {
+  const double s13 = f1 + f3, s24 = f2 + f4;
+  const double d13 = f1 - f3, d24 = f2 - f4;
+  const double s57 = f5 + f7, s68 = f6 + f8;
+  const double d57 = f5 - f7, d68 = f6 - f8;
+  const double axis = s13 + s24;
+  const double diag = s57 + s68;
+  const double dxd = d57 - d68;
+  const double dyd = d57 + d68;
+  const double rho_p = f0 + axis + diag;
+  const double jx_p = d13 + dxd;
+  const double jy_p = d24 + dyd;
+  // rho'/rho: only scales the quadratic terms, but in FP64 it is formed as
+  // an IEEE quotient all the same (the error budget is 1e-12 of rho')
+  const double c = rho_p / (P.rho0 + rho_p);
+  const double tx = fma(2.0 * P.jx0, jx_p, jx_p * jx_p);  // jx^2 - jx0^2
+  const double ty = fma(2.0 * P.jy0, jy_p, jy_p * jy_p);
+  const double txy = fma(P.jx0, jy_p, fma(jx_p, P.jy0, jx_p * jy_p));
+  const double nj = fma(P.rho0, tx + ty, -rho_p * P.q0) * P.i2;
+  const double np = fma(P.rho0, tx - ty, -rho_p * P.d0) * P.i2;
+  const double nx = fma(P.rho0, txy, -rho_p * P.x0) * P.i2;
+  const double djsq = fma(-nj, c, nj);
+  const double dpxx = fma(-np, c, np);
+  const double dpxy = fma(-nx, c, nx);
+  const double n3 = fma(4.0, diag, axis - 2.0 * f0) - 3.0 * djsq;
+  const double n4 = fma(3.0, djsq, 3.0 * (f0 - axis));
+  const double n5 = fma(2.0, dxd, -d13);
+  const double n6 = fma(2.0, dyd, -d24);
+  const double n7 = (s13 - s24) - dpxx;
+  const double n8 = (s57 - s68) - dpxy;
+  const double r3 = n3 * P.k3, r4 = n4 * P.k4, r5 = n5 * P.k5;
+  const double r6 = n6 * P.k6, r7 = n7 * P.k7, r8 = n8 * P.k8;
+  const double a = fma(2.0, r4, r3);
+  const double b = fma(2.0, r3, r4);
+  f0 = fma(-4.0, r4 - r3, f0);
+  f1 += fma(2.0, r5, a - r7);
+  f3 += fma(-2.0, r5, a - r7);
+  f2 += fma(2.0, r6, a + r7);
+  f4 += fma(-2.0, r6, a + r7);
+  f5 -= b + r5 + r6 + r8;
+  f6 -= b - r5 + r6 - r8;
+  f7 -= b - r5 - r6 + r8;
+  f8 -= b + r5 - r6 - r8;
+}
+
 // FP64 rates of the plain path: s3 = s_e, s4 = s_eps, s5 = s_qx, s6 = s_qy,
 // s7 = s_pxx, s8 = s_pxy.
 struct F64Params {

@@ -81,6 +81,10 @@ template <>
 __device__ __forceinline__ __nv_bfloat16 encode<__nv_bfloat16>(double d, double) {
   return __float2bfloat16_rn((float)d);
 }
+template <>
+__device__ __forceinline__ double encode<double>(double d, double) {
+  return d;
+}
 
 template <typename T>
 __device__ __forceinline__ double decode(T s, double inv_scale);
@@ -95,6 +99,10 @@ __device__ __forceinline__ double decode<__half>(__half s, double inv_scale) {
 template <>
 __device__ __forceinline__ double decode<__nv_bfloat16>(__nv_bfloat16 s, double) {
   return (double)__bfloat162float(s);
+}
+template <>
+__device__ __forceinline__ double decode<double>(double s, double) {
+  return s;
 }
 
 // Population i of node x goes to slot x - c_i, where the next step's pull
@@ -285,6 +293,7 @@ cudaError_t launch_init_dev(const AuxView &a, const double *rho, const double *u
     case LBM_BF16DEV:
       k_init_dev<__nv_bfloat16><<<grid, 256, 0, st>>>(a, R, rho, ux, uy, bad);
       break;
+    case LBM_F64DEV: k_init_dev<double><<<grid, 256, 0, st>>>(a, R, rho, ux, uy, bad); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -326,6 +335,7 @@ cudaError_t launch_moments_dev(const AuxView &a, double *rho, double *ux, double
     case LBM_F32DEV: k_moments_dev<float><<<grid, 256, 0, st>>>(a, rho, ux, uy); break;
     case LBM_F16DEV: k_moments_dev<__half><<<grid, 256, 0, st>>>(a, rho, ux, uy); break;
     case LBM_BF16DEV: k_moments_dev<__nv_bfloat16><<<grid, 256, 0, st>>>(a, rho, ux, uy); break;
+    case LBM_F64DEV: k_moments_dev<double><<<grid, 256, 0, st>>>(a, rho, ux, uy); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

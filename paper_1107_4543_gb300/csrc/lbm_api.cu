@@ -555,7 +555,8 @@ int create_lattice(int nx, int ny, const double S[9], double rho0, const double 
   REQUIRE(check_rates(S), "rates: non-conserved entries must lie in (0, 2], all finite");
   int esize, V;
   switch (storage_dtype) {
-    case LBM_F64: esize = 8; break;
+    case LBM_F64:
+    case LBM_F64DEV: esize = 8; break;
     case LBM_F32DEV: esize = 4; break;
     case LBM_F16DEV:
     case LBM_BF16DEV: esize = 2; break;
@@ -589,7 +590,7 @@ int create_lattice(int nx, int ny, const double S[9], double rho0, const double 
   dp.rho0 = (float)rho0;
   dp.jx0 = (float)(rho0 * u0[0]);
   dp.jy0 = (float)(rho0 * u0[1]);
-  if (storage_dtype == LBM_F64) {
+  if (storage_dtype == LBM_F64 || storage_dtype == LBM_F64DEV) {
     h->rho0 = rho0;
     h->j0[0] = rho0 * u0[0];
     h->j0[1] = rho0 * u0[1];
@@ -614,6 +615,23 @@ int create_lattice(int nx, int ny, const double S[9], double rho0, const double 
   }
   dp.scale = 1.0f;
   dp.inv_scale = 1.0f;
+  {
+    // FP64 deviation storage: the reference state and rates in FP64
+    DevParams64 &q = h->L.dp64;
+    q.rho0 = h->rho0;
+    q.jx0 = h->j0[0];
+    q.jy0 = h->j0[1];
+    q.k3 = h->S_paper[3] / 36.0;
+    q.k4 = h->S_paper[4] / 36.0;
+    q.k5 = h->S_paper[5] / 12.0;
+    q.k6 = h->S_paper[6] / 12.0;
+    q.k7 = h->S_paper[7] / 4.0;
+    q.k8 = h->S_paper[8] / 4.0;
+    q.q0 = q.jx0 * q.jx0 + q.jy0 * q.jy0;
+    q.d0 = q.jx0 * q.jx0 - q.jy0 * q.jy0;
+    q.x0 = q.jx0 * q.jy0;
+    q.i2 = 1.0 / (q.rho0 * q.rho0);
+  }
   F64Params &fp = h->L.fp;
   fp.s3 = h->S_paper[3];
   fp.s4 = h->S_paper[4];
@@ -1445,7 +1463,8 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
   int dev = members[0] ? members[0]->device : 0;
   for (int k = 0; k < n; ++k) {
     REQUIRE(members[k] != nullptr, "null member");
-    REQUIRE(members[k]->L.dtype != LBM_F64, "batches take deviation-storage lattices only");
+    REQUIRE(members[k]->L.dtype != LBM_F64 && members[k]->L.dtype != LBM_F64DEV,
+            "batches take the 32- and 16-bit deviation storage types");
     REQUIRE(members[k]->batch == nullptr, "lattice already in a batch");
     REQUIRE(!members[k]->slab, "slabs of a split lattice cannot join a batch");
     REQUIRE(members[k]->device == dev, "members on different devices");

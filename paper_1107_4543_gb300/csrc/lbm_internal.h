@@ -45,7 +45,8 @@ struct Lattice {
   int esize;         // bytes per stored population
   void *buf[2];      // double buffer (each 9 planes)
   int cur;           // buffer holding the current state
-  DevParams dp;      // deviation types
+  DevParams dp;      // deviation types stored in 32 or 16 bits
+  DevParams64 dp64;  // LBM_F64DEV
   F64Params fp;      // LBM_F64
 };
 
@@ -93,6 +94,8 @@ cudaError_t launch_step_dev_f16(const Lattice &L, const void *src, void *dst, cu
                                 int block, int variant);
 cudaError_t launch_step_dev_bf16(const Lattice &L, const void *src, void *dst, cudaStream_t st,
                                  int block, int variant);
+cudaError_t launch_step_dev_f64dev(const Lattice &L, const void *src, void *dst, cudaStream_t st,
+                                   int block, int variant);
 cudaError_t launch_step_batch_f32(const BatchList &bl, int parity, cudaStream_t st, int block,
                                   int variant, const int *limits, int k);
 cudaError_t launch_step_batch_f16(const BatchList &bl, int parity, cudaStream_t st, int block,
@@ -108,6 +111,7 @@ inline cudaError_t launch_step_dev(const Lattice &L, const void *src, void *dst,
     case LBM_F32DEV: return launch_step_dev_f32(L, src, dst, st, block, variant);
     case LBM_F16DEV: return launch_step_dev_f16(L, src, dst, st, block, variant);
     case LBM_BF16DEV: return launch_step_dev_bf16(L, src, dst, st, block, variant);
+    case LBM_F64DEV: return launch_step_dev_f64dev(L, src, dst, st, block, variant);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -125,7 +129,7 @@ inline cudaError_t launch_step_batch(int dtype, const BatchList &bl, int parity,
 
 // Nodes per vector of a storage type (host side of d2q9_pull.cuh's Elem).
 inline int vec_nodes(int dtype) {
-  return dtype == LBM_F64 ? 2
+  return dtype == LBM_F64 || dtype == LBM_F64DEV ? 2
          : dtype == LBM_F32DEV ? 4
          : dtype == LBM_F16DEV ? LBM_VF16 : LBM_VBF16;
 }

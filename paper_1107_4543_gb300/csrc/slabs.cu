@@ -219,9 +219,10 @@ int lbm_slabs_create(int nx, int ny, const double S[9], double rho0, const doubl
                      int storage_dtype, int nslabs, const int *devices, lbm_slabs *out) {
   SREQ(out != nullptr && S != nullptr && u0 != nullptr, "null argument");
   SREQ(nslabs >= 1 && ny >= nslabs, "need 1 <= nslabs <= ny");
-  SREQ(storage_dtype == LBM_F64 || storage_dtype == LBM_F32DEV || storage_dtype == LBM_BF16DEV,
-       "slabs take FP64, FP32 or BF16 storage (FP16 slabs would need one storage scale for "
-       "the whole lattice)");
+  SREQ(storage_dtype == LBM_F64 || storage_dtype == LBM_F32DEV ||
+           storage_dtype == LBM_BF16DEV || storage_dtype == LBM_F64DEV,
+       "slabs take FP64, FP32, BF16 or FP64-deviation storage (FP16 slabs would need one "
+       "storage scale for the whole lattice)");
   int cur_dev = 0;
   SCK(cudaGetDevice(&cur_dev));
   lbm_slabs_ctx *s = new (std::nothrow) lbm_slabs_ctx();

@@ -17,9 +17,14 @@
 
 namespace lbm {
 
+// collision parameters of a storage type: FP32 constants (hi + lo pairs
+// for FP32 storage) for the 32- and 16-bit types, FP64 ones for LBM_F64DEV
+template <typename T> struct ParamsOf { using type = DevParams; };
+template <> struct ParamsOf<double> { using type = DevParams64; };
+
 template <typename T>
 __device__ __forceinline__ void step_task(const T *__restrict__ src, T *__restrict__ dst,
-                                          const Geom &g, const DevParams &P,
+                                          const Geom &g, const typename ParamsOf<T>::type &P,
                                           long long task, int lane) {
   constexpr int V = Elem<T>::V;
   // FP16 is stored scaled and collided in the scaled units; FP32 carries
@@ -55,6 +60,14 @@ __device__ __forceinline__ void step_task(const T *__restrict__ src, T *__restri
       }
     }
     store9_packed<T>(dst, g, p, w);
+  } else if constexpr (std::is_same<T, double>::value) {
+    double f[9][V];
+    pull9<T, false>(src, g, p, 1.0, f);
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+      collide_dev64(f[0][e], f[1][e], f[2][e], f[3][e], f[4][e], f[5][e], f[6][e], f[7][e],
+                    f[8][e], P);
+    store9<T, false>(dst, g, p, 1.0, f);
   } else {
     float f[9][V];
     pull9<T, false>(src, g, p, 1.0f, f);
@@ -73,8 +86,8 @@ __device__ __forceinline__ void step_task(const T *__restrict__ src, T *__restri
 // tuner are MINB = 1, 2, 3.
 template <typename T, int MINB>
 __global__ void __launch_bounds__(256, MINB)
-k_step_dev(const T *__restrict__ src, T *__restrict__ dst, Geom g, DevParams P,
-           long long ntasks) {
+k_step_dev(const T *__restrict__ src, T *__restrict__ dst, Geom g,
+           typename ParamsOf<T>::type P, long long ntasks) {
   const int lane = threadIdx.x & 31;
   const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -172,10 +185,13 @@ cudaError_t launch_step_dev_t(const Lattice &L, const void *src, void *dst, cuda
   if (grid < 1) grid = 1;
   const T *s = static_cast<const T *>(src);
   T *d = static_cast<T *>(dst);
+  const typename ParamsOf<T>::type *P;
+  if constexpr (std::is_same<T, double>::value) P = &L.dp64;
+  else P = &L.dp;
   switch (variant) {
-    case 0: k_step_dev<T, 1><<<(unsigned)grid, block, 0, st>>>(s, d, L.g, L.dp, nt); break;
-    case 1: k_step_dev<T, 2><<<(unsigned)grid, block, 0, st>>>(s, d, L.g, L.dp, nt); break;
-    default: k_step_dev<T, 3><<<(unsigned)grid, block, 0, st>>>(s, d, L.g, L.dp, nt); break;
+    case 0: k_step_dev<T, 1><<<(unsigned)grid, block, 0, st>>>(s, d, L.g, *P, nt); break;
+    case 1: k_step_dev<T, 2><<<(unsigned)grid, block, 0, st>>>(s, d, L.g, *P, nt); break;
+    default: k_step_dev<T, 3><<<(unsigned)grid, block, 0, st>>>(s, d, L.g, *P, nt); break;
   }
   return cudaGetLastError();
 }

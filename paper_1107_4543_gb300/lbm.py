@@ -17,9 +17,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
 LBM_OK, LBM_PENDING = 0, 1
 LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE = -1, -2, -3, -4
 LBM_ETIMEOUT, LBM_ENOTFOUND, LBM_ECLOSED = -5, -6, -7
-LBM_F64, LBM_F32DEV, LBM_F16DEV, LBM_BF16DEV = 0, 1, 2, 3
+LBM_F64, LBM_F32DEV, LBM_F16DEV, LBM_BF16DEV, LBM_F64DEV = 0, 1, 2, 3, 4
 LBM_INIT_FIELDS, LBM_INIT_GAUSSIAN, LBM_INIT_PLANE = 0, 1, 2
-DTYPES = {"f64": LBM_F64, "f32": LBM_F32DEV, "f16": LBM_F16DEV, "bf16": LBM_BF16DEV}
+DTYPES = {"f64": LBM_F64, "f32": LBM_F32DEV, "f16": LBM_F16DEV, "bf16": LBM_BF16DEV,
+          "f64dev": LBM_F64DEV}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _vp = ctypes.c_void_p

@@ -19,7 +19,7 @@ torch.distributed and works on CPU tensors with the gloo backend as well.
 """
 import numpy as np
 
-ESIZE = {0: 8, 1: 4, 2: 2, 3: 2}  # bytes per stored population, by storage type
+ESIZE = {0: 8, 1: 4, 2: 2, 3: 2, 4: 8}  # bytes per stored population, by storage type
 
 
 def lattice_bytes(nx, ny, dtype):

@@ -47,7 +47,7 @@ def unsplit(L, nx, ny, r, dtype, steps, fields=None, pops=None, u0=(0.0, 0.0)):
         L.lbm_destroy(h)
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f64dev"])
 @pytest.mark.parametrize("nx,ny,nslabs", [(64, 48, 3), (37, 29, 4), (33, 4, 4), (40, 17, 1),
                                           (130, 9, 2)])
 def test_slabs_equal_unsplit_lattice(L, dtype, nx, ny, nslabs):
