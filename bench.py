@@ -58,7 +58,8 @@ def parser():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="batched",
-                   choices=["batched", "large", "serving", "vn", "opt", "source", "oracle"])
+                   choices=["batched", "large", "serving", "vn", "opt", "source", "oracle",
+                            "slabs"])
     p.add_argument("--lattices", type=int, default=512)
     p.add_argument("--lbm-steps", type=int, default=500)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -583,6 +584,40 @@ def bench_serving(args, L, torch):
             "server": st}
 
 
+def bench_slabs(args, L, torch):
+    """One n x n FP32 lattice split into 1, 2 and 4 y-slabs on this one GPU
+    (lbm_slabs_*), against the unsplit lattice: MLUPS per split, i.e. what
+    the boundary-row launches and the halo copies cost when nothing is
+    gained from more devices."""
+    n, steps = args.size, 200
+    r = inp.rates("OPT")
+    fields = inp.gaussian_pulse(n, n, 1e-3, 20.0)
+    stream = torch.cuda.current_stream()
+    out = {}
+    mlups, _ = large_one(L, torch, stream, n, "f32", steps, 1, 1)
+    out["unsplit"] = round(mlups, 1)
+    for k in (1, 2, 4):
+        s = L.lbm_slabs_create(n, n, inp.s_ll(r), 1.0, (0.0, 0.0), L.LBM_F32DEV, k)
+        try:
+            L.lbm_slabs_init_field(s, *fields)
+            L.lbm_slabs_step(s, 20)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            L.lbm_slabs_step(s, steps)
+            L.lbm_slabs_drift(s)  # synchronizes every slab
+            dt = time.perf_counter() - t0
+        finally:
+            L.lbm_slabs_destroy(s)
+        out["slabs_%d" % k] = round(n * n * steps / dt / 1e6, 1)
+    return {"metric": "MLUPS, one %dx%d FP32 lattice split into y-slabs on one GPU" % (n, n),
+            "value": out["slabs_2"], "unit": "MLUPS", "higher_is_better": True,
+            "config": {"workload": "slabs-%dx%d-fp32-%d-steps" % (n, n, steps)},
+            "per_split": out,
+            "note": "host-timed over the steps (slab steps are issued from the host: one "
+                    "boundary-row pair and one interior launch per slab and step, four halo "
+                    "copies per slab and step)"}
+
+
 def bench_vn(args, L, torch):
     """Von Neumann sweep (sections 4.1-4.2): eigenvalues of G(k) on a grid
     of 256 |k| x 64 directions x U in {0, 0.1} x 4 rate sets."""
@@ -813,6 +848,10 @@ def main():
     if args.workload == "vn":
         if rank == 0:
             print(json.dumps(bench_vn(args, L, torch)))
+        return
+    if args.workload == "slabs":
+        if rank == 0:
+            print(json.dumps(bench_slabs(args, L, torch)))
         return
     if args.workload == "opt":
         if rank == 0:

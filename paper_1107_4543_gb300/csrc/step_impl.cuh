@@ -106,7 +106,7 @@ k_step_dev(const T *__restrict__ src, T *__restrict__ dst, Geom g,
 template <typename T, int MINB>
 __global__ void __launch_bounds__(256, MINB)
 k_step_batch(const BatchEntry *__restrict__ ents, const BlockRec *__restrict__ blocks,
-             int nents, int parity, const int *__restrict__ limits, int k, unsigned pfd) {
+             int nents, int parity, const int *__restrict__ limits, int k) {
   const int lane = threadIdx.x & 31;
   const BlockRec &B = blocks[blockIdx.x];
   // The records are read once per launch, so a step's 4.9 GB of streaming
@@ -114,9 +114,12 @@ k_step_batch(const BatchEntry *__restrict__ ents, const BlockRec *__restrict__ b
   // to DRAM precedes its pull: each block prefetches into L2 the record of
   // the block about one wave of resident blocks later (measured +1.7%
   // FP32, +2.9% FP16, +1.8% BF16 on the 512-lattice batch; any distance
-  // from 1024 to 2048 blocks alike)
-  if (threadIdx.x == 0 && blockIdx.x + pfd < gridDim.x) {
-    const char *q = reinterpret_cast<const char *>(blocks + blockIdx.x + pfd);
+  // from 1024 to 2048 blocks alike; 152 SMs hold 1824 of the 64-thread
+  // blocks at the 80-register cap; a compile-time distance keeps the
+  // register budget, a launch parameter cost 20 bytes more of spills)
+  constexpr unsigned kPrefetch = 1536;
+  if (threadIdx.x == 0 && blockIdx.x + kPrefetch < gridDim.x) {
+    const char *q = reinterpret_cast<const char *>(blocks + blockIdx.x + kPrefetch);
     asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
     asm volatile("prefetch.global.L2 [%0];" ::"l"(q + sizeof(BlockRec) - 1));
   }
@@ -223,21 +226,15 @@ cudaError_t launch_step_batch_t(const BatchList &bl, int parity, cudaStream_t st
     return cudaGetLastError();
   }
   const unsigned grid = (unsigned)bl.nblocks;
-  // prefetch distance: the blocks resident at once (MINB 256-thread blocks'
-  // worth of warps per SM)
-  const unsigned pfd = (unsigned)sm_count() * (unsigned)((variant + 1) * 256 / block);
   switch (variant) {
     case 0:
-      k_step_batch<T, 1><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits, k,
-                                                  pfd);
+      k_step_batch<T, 1><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits, k);
       break;
     case 1:
-      k_step_batch<T, 2><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits, k,
-                                                  pfd);
+      k_step_batch<T, 2><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits, k);
       break;
     default:
-      k_step_batch<T, 3><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits, k,
-                                                  pfd);
+      k_step_batch<T, 3><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits, k);
       break;
   }
   return cudaGetLastError();
