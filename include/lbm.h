@@ -510,6 +510,10 @@ typedef struct {
   size_t resident_bytes, peak_bytes;
   double lattice_updates;   /* node-steps done                            */
   double busy_s;            /* wall time with work on the device          */
+  int variant;              /* batch launch variant in use (-1: not yet    *
+                             * tuned; tuned once on the first generation   *
+                             * of >= 2^24 nodes, whose populations exceed  *
+                             * the L2, the default variant until then)     */
 } lbm_server_stats_t;
 int lbm_server_stats(lbm_server s, lbm_server_stats_t *out);
 

@@ -271,9 +271,16 @@ __device__ __forceinline__ void collide_dev64(double &f0, double &f1, double &f2
   const double rho_p = f0 + axis + diag;
   const double jx_p = d13 + dxd;
   const double jy_p = d24 + dyd;
-  // rho'/rho: only scales the quadratic terms, but in FP64 it is formed as
-  // an IEEE quotient all the same (the error budget is 1e-12 of rho')
-  const double c = rho_p / (P.rho0 + rho_p);
+  // rho'/rho: only scales the quadratic terms.  1/rho by the hardware's
+  // approximate FP64 reciprocal refined by two Newton-Raphson steps
+  // (r <- r + r (1 - d r), each squaring the relative error: well below
+  // 2^-50 after two), cheaper on GB300's FP64 pipe than the IEEE quotient
+  const double den = P.rho0 + rho_p;
+  double rinv;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(rinv) : "d"(den));
+  rinv = fma(rinv, fma(-den, rinv, 1.0), rinv);
+  rinv = fma(rinv, fma(-den, rinv, 1.0), rinv);
+  const double c = rho_p * rinv;
   const double tx = fma(2.0 * P.jx0, jx_p, jx_p * jx_p);  // jx^2 - jx0^2
   const double ty = fma(2.0 * P.jy0, jy_p, jy_p * jy_p);
   const double txy = fma(P.jx0, jy_p, fma(jx_p, P.jy0, jx_p * jy_p));

@@ -10,8 +10,8 @@
 // rho - rho0, j - j0, jx^2/rho - jx0^2/rho0, jy^2/rho - jy0^2/rho0 and
 // jx jy/rho - jx0 jy0/rho0: every term is of the size of the perturbation,
 // so nothing of order one is subtracted after rounding, and a node costs
-// one FP64 division and a few dozen FP64 operations (GB300's FP64 rate is
-// what bounds these kernels, not their 60 bytes per node).
+// a few dozen FP64 operations and no division (GB300's FP64 rate is what
+// bounds these kernels, not their 60 bytes per node).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -45,12 +45,13 @@ __device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >=
 __device__ __forceinline__ void feq_deviation(const RefState &R, double r, double u, double v,
                                               double d[9]) {
   const double jx = r * u, jy = r * v;
-  const double inv = 1.0 / r;
   const double dr = r - R.rho0;
   const double ex = 3.0 * (jx - R.jx0), ey = 3.0 * (jy - R.jy0);
-  const double A = jx * jx * inv - R.axx0;
-  const double B = jy * jy * inv - R.ayy0;
-  const double C = jx * jy * inv - R.axy0;
+  // jx^2 / rho = rho u^2 etc.: the fields give u, so no division is needed
+  // (GB300's FP64 divide is the costliest step of this FP64-bound kernel)
+  const double A = jx * u - R.axx0;
+  const double B = jy * v - R.ayy0;
+  const double C = jx * v - R.axy0;
   const double t1 = dr + 3.0 * A - 1.5 * B;  // axis x: 9/2 A - 3/2 (A + B)
   const double t2 = dr + 3.0 * B - 1.5 * A;  // axis y
   const double t5 = dr + 3.0 * (A + B);      // diagonals: 9/2 (A + B +- 2C) - 3/2 (A + B)

@@ -235,11 +235,20 @@ static void worker_loop(lbm_server_ctx *s) {
       lbm_batch b = nullptr;
       rc = lbm_batch_create((int)hs.size(), hs.data(), &b);
       if (rc == LBM_OK) {
-        // tune once, on the first generation large enough to be tuned, and
-        // keep that choice for every later generation
+        // tune once, on the first generation whose populations exceed the
+        // L2 (2^24 nodes: >= 0.6 GB in 16-bit storage), and keep that choice
+        // for every later generation; smaller generations run the default
+        // variant (a tuning run that fits in L2 ranks the variants by their
+        // cache-resident speed, which is not the HBM-bound speed that the
+        // large generations need)
         if (s->variant >= 0) batch_pin_variant(b, s->variant);
+        else if (batch_nodes(b) < (1LL << 24)) batch_pin_variant(b, kStepVariants - 1);
         rc = batch_step_ragged(b, take.data(), n);
-        if (s->variant < 0 && batch_nodes(b) >= (1LL << 20)) s->variant = batch_variant(b);
+        if (s->variant < 0 && batch_nodes(b) >= (1LL << 24)) {
+          s->variant = batch_variant(b);
+          std::lock_guard<std::mutex> lk(s->mu);
+          s->st.variant = s->variant;
+        }
         lbm_batch_destroy(b);
       }
     }
@@ -282,6 +291,7 @@ int lbm_server_create(size_t hbm_budget_bytes, long chunk_steps, lbm_server *out
   if (!s) return LBM_ENOMEM;
   s->budget = hbm_budget_bytes;
   s->chunk = chunk_steps;
+  s->st.variant = -1;
   if (cudaGetDevice(&s->device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();

@@ -47,7 +47,7 @@ class lbm_server_stats_t(ctypes.Structure):
                 ("generations", ctypes.c_longlong), ("resident", ctypes.c_int),
                 ("peak_resident", ctypes.c_int), ("resident_bytes", ctypes.c_size_t),
                 ("peak_bytes", ctypes.c_size_t), ("lattice_updates", ctypes.c_double),
-                ("busy_s", ctypes.c_double)]
+                ("busy_s", ctypes.c_double), ("variant", ctypes.c_int)]
 
 
 class lbm_cost_spec(ctypes.Structure):
