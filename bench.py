@@ -345,7 +345,8 @@ def bench_batched(args, L, torch, rank, ws):
     # from page-locked host arrays, equilibrium init, the 500 steps, the
     # drift sums, moments, download), queued back to back so that one
     # solve's copies overlap its neighbours' stepping; lbm_batch_wait ends
-    # the timed region and reports the last solve's device time per phase
+    # the timed region and reports the device time per phase (median over
+    # the timed solves)
     def pinned_flat():
         return torch.empty(nodes, dtype=torch.float64, pin_memory=True).numpy()
 
@@ -444,7 +445,7 @@ def bench_batched(args, L, torch, rank, ws):
                         "drift out), successive solves overlapped, lbm_batch_wait at the end"
                         if pipelined else "lbm_batch_init_packed, lbm_batch_step, "
                         "lbm_batch_drift, lbm_batch_moments_packed per step (synchronous)"),
-                # device time of each phase of the last solve (events on the
+                # device time of each phase, median over the timed solves (events on the
                 # streams that ran them; the copies overlap the neighbouring
                 # solves' steps)
                 "phases_ms": ({k: round(phases[k], 3) for k in L.BATCH_PHASES} if phases

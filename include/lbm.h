@@ -242,7 +242,8 @@ int lbm_info(lbm_handle h, lbm_info_t *out);
 /* (runtime; no counterpart in the paper) Device allocator used for all
  * later allocations of lattices, batches,
  * servers and cost evaluations (e.g. a caching allocator).  alloc returns
- * NULL on failure.  Passing NULL functions restores cudaMalloc / cudaFree.
+ * NULL on failure, else memory aligned to 256 bytes (as cudaMalloc's;
+ * lbm_create refuses lattice buffers that are not, LBM_EINVAL).  Passing NULL functions restores cudaMalloc / cudaFree.
  * Not thread-safe with respect to concurrent lbm_create calls.  The
  * staging that lbm_vn_eigs keeps for the life of the process uses
  * cudaMalloc / cudaHostAlloc directly, so that it never outlives the
@@ -418,9 +419,10 @@ int lbm_batch_solve_packed(lbm_batch b, long n, const double *rho_in, const doub
                            const double *uy_in, double *rho_out, double *ux_out,
                            double *uy_out, double *drift_out);
 /* Wait for every solve queued by lbm_batch_solve_packed.  phase_ms (may be
- * NULL) receives 6 device times of the last solve, in ms, measured by events
- * on the streams that ran them: upload, init, steps, drift, moments,
- * download.  Returns LBM_EINVAL if any solve since the last wait had invalid
+ * NULL) receives 6 device times per solve, in ms, measured by events on the
+ * streams that ran them: upload, init, steps, drift, moments, download --
+ * each the median over the solves queued since the previous wait (the last
+ * 32 of them at most; the last solve alone when none was queued since).  Returns LBM_EINVAL if any solve since the last wait had invalid
  * fields (message names the member), LBM_EUNSTABLE if a drift array passed
  * since then reports non-finite populations, else 0. */
 int lbm_batch_wait(lbm_batch b, double *phase_ms);

@@ -368,39 +368,52 @@ __device__ __forceinline__ uint32_t raw16(const void *p) {
   return (uint32_t)__ldg(static_cast<const unsigned short *>(p));
 }
 
-template <typename T>
-__device__ __forceinline__ void pull9_packed(const T *__restrict__ src, const Geom &g,
-                                             const LanePos &p,
-                                             uint32_t (&out)[9][Elem<T>::V / 2]) {
-  constexpr int V = Elem<T>::V;
-  constexpr int W = V / 2;
-  static_assert(sizeof(T) == 2 && V % 2 == 0, "16-bit storage types only");
-  const int last = g.nx - 1;
-  const int e_last = (p.x0 <= last && last < p.x0 + V) ? last - p.x0 : -1;
-  const bool need_prev = p.active && p.first;
-  const int x_prev = p.x0 == 0 ? last : p.x0 - 1;
-  const bool need_next = p.active && p.last && p.x0 + V <= last;
-  const bool need_wrap = p.active && e_last >= 0;
+// Where a lane's +-1 x-shifted elements come from when the neighbouring
+// lane does not hold them: the previous element for the planes with
+// cx = +1 (x_prev: x0 - 1, or column nx - 1 across the wrap), the next one
+// for cx = -1, and column 0 for the element of the last real node.
+struct EdgeInfo {
+  int e_last;  // which element of this chunk is the last real node (or -1)
+  int x_prev;
+  bool need_prev, need_next, need_wrap;
+};
 
-  using RawT = typename Elem<T>::R::type;
-  RawT raw[9];
-  uint32_t edge[9], wrap0[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const int cx = CXd(i), cy = CYd(i);
-    int ys = p.y - cy;
-    ys = ys < 0 ? ys + g.nyw : (ys >= g.nyw ? ys - g.nyw : ys);
-    const T *row = src + (long long)i * g.plane + (long long)ys * g.rstride;
-    raw[i] = p.active ? __ldg(reinterpret_cast<const RawT *>(row + p.x0)) : Elem<T>::R::zero();
-    edge[i] = 0u;
-    wrap0[i] = 0u;
-    if (cx == 1) {
-      if (need_prev) edge[i] = raw16(row + x_prev);
-    } else if (cx == -1) {
-      if (need_next) edge[i] = raw16(row + p.x0 + V);
-      if (need_wrap) wrap0[i] = raw16(row);
-    }
+__device__ __forceinline__ EdgeInfo edge_info(const Geom &g, const LanePos &p, int V) {
+  EdgeInfo E;
+  const int last = g.nx - 1;
+  E.e_last = (p.x0 <= last && last < p.x0 + V) ? last - p.x0 : -1;
+  E.need_prev = p.active && p.first;
+  E.x_prev = p.x0 == 0 ? last : p.x0 - 1;
+  E.need_next = p.active && p.last && p.x0 + V <= last;
+  E.need_wrap = p.active && E.e_last >= 0;
+  return E;
+}
+
+// the (predicated) scalar edge loads of plane i; raw16 values
+template <typename T>
+__device__ __forceinline__ void edge_loads_packed(const T *row, const LanePos &p,
+                                                  const EdgeInfo &E, int i, uint32_t &edge,
+                                                  uint32_t &wrap0) {
+  constexpr int V = Elem<T>::V;
+  const int cx = CXd(i);
+  edge = 0u;
+  wrap0 = 0u;
+  if (cx == 1) {
+    if (E.need_prev) edge = raw16(row + E.x_prev);
+  } else if (cx == -1) {
+    if (E.need_next) edge = raw16(row + p.x0 + V);
+    if (E.need_wrap) wrap0 = raw16(row);
   }
+}
+
+// Second phase of the packed pull: the shifted vectors from this lane's
+// chunks (raw), the neighbouring lanes' (shuffles) and the edge values.
+template <typename T>
+__device__ __forceinline__ void assemble_packed(const typename Elem<T>::R::type (&raw)[9],
+                                                const EdgeInfo &E, const uint32_t (&edge)[9],
+                                                const uint32_t (&wrap0)[9],
+                                                uint32_t (&out)[9][Elem<T>::V / 2]) {
+  constexpr int W = Elem<T>::V / 2;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const int cx = CXd(i);
@@ -412,28 +425,54 @@ __device__ __forceinline__ void pull9_packed(const T *__restrict__ src, const Ge
     } else if (cx == 1) {
       // node x pulls from x - 1: word k = (high half of v[k-1], low half of v[k])
       uint32_t prevw = __shfl_up_sync(0xffffffffu, v[W - 1], 1);
-      if (need_prev) prevw = edge[i] << 16;
+      if (E.need_prev) prevw = edge[i] << 16;
       out[i][0] = __byte_perm(prevw, v[0], 0x5432);
 #pragma unroll
       for (int k = 1; k < W; ++k) out[i][k] = __byte_perm(v[k - 1], v[k], 0x5432);
     } else {
       // node x pulls from x + 1 (column 0 for the last real node)
       uint32_t nextw = __shfl_down_sync(0xffffffffu, v[0], 1);
-      if (need_next) nextw = edge[i];
+      if (E.need_next) nextw = edge[i];
 #pragma unroll
       for (int k = 0; k < W - 1; ++k) out[i][k] = __byte_perm(v[k], v[k + 1], 0x5432);
       out[i][W - 1] = __byte_perm(v[W - 1], nextw, 0x5432);
-      if (need_wrap) {
+      if (E.need_wrap) {
         // the last real node's element takes column 0 (a select per word,
         // so that the array stays in registers)
-        const int kw = e_last >> 1;
-        const uint32_t keep = (e_last & 1) ? 0xffffu : 0xffff0000u;
-        const uint32_t put = (e_last & 1) ? (wrap0[i] << 16) : wrap0[i];
+        const int kw = E.e_last >> 1;
+        const uint32_t keep = (E.e_last & 1) ? 0xffffu : 0xffff0000u;
+        const uint32_t put = (E.e_last & 1) ? (wrap0[i] << 16) : wrap0[i];
 #pragma unroll
         for (int k = 0; k < W; ++k) out[i][k] = k == kw ? ((out[i][k] & keep) | put) : out[i][k];
       }
     }
   }
+}
+
+// source row of plane i for destination row y (periodic wrap over nyw rows;
+// nyw = 0 for a slab, whose rows -1 and ny are stored halo rows)
+__device__ __forceinline__ int src_row(const Geom &g, int y, int i) {
+  int ys = y - CYd(i);
+  return ys < 0 ? ys + g.nyw : (ys >= g.nyw ? ys - g.nyw : ys);
+}
+
+template <typename T>
+__device__ __forceinline__ void pull9_packed(const T *__restrict__ src, const Geom &g,
+                                             const LanePos &p,
+                                             uint32_t (&out)[9][Elem<T>::V / 2]) {
+  constexpr int V = Elem<T>::V;
+  static_assert(sizeof(T) == 2 && V % 2 == 0, "16-bit storage types only");
+  const EdgeInfo E = edge_info(g, p, V);
+  using RawT = typename Elem<T>::R::type;
+  RawT raw[9];
+  uint32_t edge[9], wrap0[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const T *row = src + (long long)i * g.plane + (long long)src_row(g, p.y, i) * g.rstride;
+    raw[i] = p.active ? __ldg(reinterpret_cast<const RawT *>(row + p.x0)) : Elem<T>::R::zero();
+    edge_loads_packed<T>(row, p, E, i, edge[i], wrap0[i]);
+  }
+  assemble_packed<T>(raw, E, edge, wrap0, out);
 }
 
 template <typename T>

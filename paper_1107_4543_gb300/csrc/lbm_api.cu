@@ -655,6 +655,12 @@ int create_lattice(int nx, int ny, const double S[9], double rho0, const double 
     set_error("device allocation failed");
     return LBM_ENOMEM;
   }
+  // the step kernels move 16-byte vectors and bulk copies of them
+  if ((reinterpret_cast<uintptr_t>(h->alloc[0]) | reinterpret_cast<uintptr_t>(h->alloc[1])) & 255) {
+    lbm_destroy(h);
+    set_error("the device allocator returned memory not aligned to 256 bytes");
+    return LBM_EINVAL;
+  }
   h->bytes = 2 * buf_bytes + sizeof(double) * (4 * drift_blocks() + 4) + sizeof(unsigned int);
   if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -1030,10 +1036,15 @@ struct lbm_batch_ctx {
   // each with device staging for the fields in and the moments out and its
   // own drift sums, so that solve k's upload (copy stream `up`) and solve
   // k-1's download (copy stream `down`) run while the batch stream steps.
-  // Events per slot, in stream order: up stream E_UP0 .. E_UP1 (H2D); batch
+  // Events per solve, in stream order: up stream E_UP0 .. E_UP1 (H2D); batch
   // stream E_B0 (upload landed), E_INIT, E_STEP, E_DRIFT, E_MOM; down stream
-  // E_DN0 .. E_DN1 (D2H).
+  // E_DN0 .. E_DN1 (D2H).  They sit in a ring of kRing solves: solve s waits
+  // on the events of solve s - 2 (the last user of its slot), and
+  // lbm_batch_wait reads the phase times of every solve still in the ring.
   enum { E_UP0, E_UP1, E_B0, E_INIT, E_STEP, E_DRIFT, E_MOM, E_DN0, E_DN1, E_COUNT };
+  static constexpr int kRing = 32;
+  cudaEvent_t ring[kRing][E_COUNT] = {};
+  long long waited = 0;  // solves queued before the last lbm_batch_wait
   // The caller's drift array may be pageable memory, and a copy into
   // pageable memory would block the host until the solve ends (which
   // serialises the next solve's upload behind it): the sums land in a
@@ -1048,7 +1059,6 @@ struct lbm_batch_ctx {
     double *in = nullptr, *out = nullptr;  // 3 x nodes doubles each
     double *dout = nullptr;                // drift sums, 4 per member
     double *hdrift = nullptr;              // page-locked copy of dout
-    cudaEvent_t ev[E_COUNT] = {};
     bool used = false;
   };
   Slot slot[2];
@@ -1255,9 +1265,10 @@ static void batch_free(lbm_batch_ctx *b) {
       cudaStreamSynchronize(st);
       cudaStreamDestroy(st);
     }
-  for (auto &sl : b->slot) {
-    for (auto &e : sl.ev)
+  for (auto &r : b->ring)
+    for (auto &e : r)
       if (e) cudaEventDestroy(e);
+  for (auto &sl : b->slot) {
     dev_free(sl.in);
     dev_free(sl.out);
     dev_free(sl.dout);
@@ -1784,8 +1795,9 @@ static int ensure_solve(lbm_batch_ctx *b) {
       set_error("out of device memory for the pipelined solve staging");
       return LBM_ENOMEM;
     }
-    for (auto &e : sl.ev) CK(cudaEventCreate(&e));
   }
+  for (auto &r : b->ring)
+    for (auto &e : r) CK(cudaEventCreate(&e));
   b->sbad = (unsigned int *)dev_alloc(2 * nm * sizeof(unsigned int));
   if (!b->sbad) {
     set_error("out of device memory for the solve counters");
@@ -1850,36 +1862,39 @@ int lbm_batch_solve_packed(lbm_batch b, long n, const double *rho_in, const doub
   const size_t T = (size_t)b->nodes, nm = b->members.size();
   const int si = (int)(b->solves & 1);
   B::Slot &sl = b->slot[si];
+  cudaEvent_t *ev = b->ring[b->solves % B::kRing];
+  const cudaEvent_t *back2 = b->ring[(b->solves + B::kRing - 2) % B::kRing];
+  const bool reuse = b->solves >= 2;  // the slot was used by solve - 2
   // upload, once the solve two back has initialised from this slot
-  CK(cudaStreamWaitEvent(b->up, sl.ev[B::E_INIT], 0));
-  CK(cudaEventRecord(sl.ev[B::E_UP0], b->up));
+  if (reuse) CK(cudaStreamWaitEvent(b->up, back2[B::E_INIT], 0));
+  CK(cudaEventRecord(ev[B::E_UP0], b->up));
   const double *src[3] = {rho_in, ux_in, uy_in};
   for (int c = 0; c < 3; ++c)
     CK(cudaMemcpyAsync(sl.in + c * T, src[c], T * sizeof(double), cudaMemcpyHostToDevice,
                        b->up));
-  CK(cudaEventRecord(sl.ev[B::E_UP1], b->up));
+  CK(cudaEventRecord(ev[B::E_UP1], b->up));
   // equilibrium init of every member from the staged fields
-  CK(cudaStreamWaitEvent(b->stream, sl.ev[B::E_UP1], 0));
-  CK(cudaEventRecord(sl.ev[B::E_B0], b->stream));
+  CK(cudaStreamWaitEvent(b->stream, ev[B::E_UP1], 0));
+  CK(cudaEventRecord(ev[B::E_B0], b->stream));
   CK(launch_batch_init_dev(b->views[b->parity], b->ioblk, b->nioblk, b->poff_dev, (long long)T,
                            sl.in, b->sbad, (int)nm, b->stream));
   CK(launch_add_u32(b->sbad + nm, b->sbad, (int)nm, b->stream));
   for (auto *m : b->members) m->t = 0;
-  CK(cudaEventRecord(sl.ev[B::E_INIT], b->stream));
+  CK(cudaEventRecord(ev[B::E_INIT], b->stream));
   rc = lbm_batch_step(b, n);
   if (rc != LBM_OK) return rc;
-  CK(cudaEventRecord(sl.ev[B::E_STEP], b->stream));
+  CK(cudaEventRecord(ev[B::E_STEP], b->stream));
   CK(launch_batch_drift(b->views[b->parity], (int)nm, b->dpart, sl.dout, b->stream));
-  CK(cudaEventRecord(sl.ev[B::E_DRIFT], b->stream));
+  CK(cudaEventRecord(ev[B::E_DRIFT], b->stream));
   // moments into this slot's output staging, once the solve two back has
   // downloaded from it
-  CK(cudaStreamWaitEvent(b->stream, sl.ev[B::E_DN1], 0));
+  if (reuse) CK(cudaStreamWaitEvent(b->stream, back2[B::E_DN1], 0));
   CK(launch_batch_moments_dev(b->views[b->parity], b->ioblk, b->nioblk, b->poff_dev,
                               (long long)T, sl.out, (int)nm, b->stream));
-  CK(cudaEventRecord(sl.ev[B::E_MOM], b->stream));
+  CK(cudaEventRecord(ev[B::E_MOM], b->stream));
   // download
-  CK(cudaStreamWaitEvent(b->down, sl.ev[B::E_MOM], 0));
-  CK(cudaEventRecord(sl.ev[B::E_DN0], b->down));
+  CK(cudaStreamWaitEvent(b->down, ev[B::E_MOM], 0));
+  CK(cudaEventRecord(ev[B::E_DN0], b->down));
   double *dst[3] = {rho_out, ux_out, uy_out};
   for (int c = 0; c < 3; ++c)
     CK(cudaMemcpyAsync(dst[c], sl.out + c * T, T * sizeof(double), cudaMemcpyDeviceToHost,
@@ -1913,7 +1928,7 @@ int lbm_batch_solve_packed(lbm_batch b, long n, const double *rho_in, const doub
     }
     b->pending_drift.push_back(drift_out);
   }
-  CK(cudaEventRecord(sl.ev[B::E_DN1], b->down));
+  CK(cudaEventRecord(ev[B::E_DN1], b->down));
   sl.used = true;
   b->last_slot = si;
   ++b->solves;
@@ -1932,14 +1947,25 @@ int lbm_batch_wait(lbm_batch b, double *phase_ms) {
     for (int k = 0; k < 6; ++k) phase_ms[k] = 0.0;
     if (b->last_slot >= 0) {
       using B = lbm_batch_ctx;
-      const B::Slot &sl = b->slot[b->last_slot];
       const int pairs[6][2] = {{B::E_UP0, B::E_UP1},   {B::E_B0, B::E_INIT},
                                {B::E_INIT, B::E_STEP}, {B::E_STEP, B::E_DRIFT},
                                {B::E_DRIFT, B::E_MOM}, {B::E_DN0, B::E_DN1}};
+      // the median over the solves since the previous wait that are still
+      // in the event ring (the last one alone when no new solve was queued)
+      const long long last = b->solves - 1;
+      long long first = std::max(b->waited, b->solves - (long long)B::kRing);
+      if (first > last) first = last;
       for (int k = 0; k < 6; ++k) {
-        float ms = 0.0f;
-        CK(cudaEventElapsedTime(&ms, sl.ev[pairs[k][0]], sl.ev[pairs[k][1]]));
-        phase_ms[k] = ms;
+        std::vector<double> t;
+        for (long long s = first; s <= last; ++s) {
+          float ms = 0.0f;
+          CK(cudaEventElapsedTime(&ms, b->ring[s % B::kRing][pairs[k][0]],
+                                  b->ring[s % B::kRing][pairs[k][1]]));
+          t.push_back(ms);
+        }
+        std::sort(t.begin(), t.end());
+        const size_t m = t.size();
+        phase_ms[k] = m % 2 ? t[m / 2] : 0.5 * (t[m / 2 - 1] + t[m / 2]);
       }
     }
   }
@@ -1965,6 +1991,7 @@ int lbm_batch_wait(lbm_batch b, double *phase_ms) {
           rc = LBM_EUNSTABLE;
         }
   b->pending_drift.clear();
+  b->waited = b->solves;
   return rc;
 }
 

@@ -22,6 +22,34 @@ namespace lbm {
 template <typename T> struct ParamsOf { using type = DevParams; };
 template <> struct ParamsOf<double> { using type = DevParams64; };
 
+// 16-bit storage: unpack / collide / repack the packed populations two
+// nodes at a time (9 x V floats per lane would not fit the register
+// budget); the word's two nodes collide together, one per lane of the
+// packed FP32 pair instructions.  FP16 is stored scaled and collided in the
+// scaled units.
+template <typename T>
+__device__ __forceinline__ void collide_packed(uint32_t (&w)[9][Elem<T>::V / 2],
+                                               const DevParams &P) {
+  constexpr bool SCALED = std::is_same<T, __half>::value;
+#pragma unroll
+  for (int k = 0; k < Elem<T>::V / 2; ++k) {
+    F2 f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      float t[2];
+      Elem<T>::unpack2(w[i][k], t);
+      f[i] = f2(t[0], t[1]);
+    }
+    collide_pair<SCALED>(f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8], P);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      float t[2];
+      f2split(f[i], t[0], t[1]);
+      w[i][k] = Elem<T>::pack2(t[0], t[1]);
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void step_task(const T *__restrict__ src, T *__restrict__ dst,
                                           const Geom &g, const typename ParamsOf<T>::type &P,
@@ -36,29 +64,9 @@ __device__ __forceinline__ void step_task(const T *__restrict__ src, T *__restri
                   bounds::BATCH_LANE))
     p.active = false;
   if constexpr (sizeof(T) == 2) {
-    // 16-bit storage: pull packed, then unpack / collide / repack two nodes
-    // at a time (9 x V floats per lane would not fit the register budget)
     uint32_t w[9][V / 2];
     pull9_packed<T>(src, g, p, w);
-#pragma unroll
-    for (int k = 0; k < V / 2; ++k) {
-      // the word's two nodes collide together, one per lane of the packed
-      // FP32 pair instructions
-      F2 f[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        float t[2];
-        Elem<T>::unpack2(w[i][k], t);
-        f[i] = f2(t[0], t[1]);
-      }
-      collide_pair<SCALED>(f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8], P);
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        float t[2];
-        f2split(f[i], t[0], t[1]);
-        w[i][k] = Elem<T>::pack2(t[0], t[1]);
-      }
-    }
+    collide_packed<T>(w, P);
     store9_packed<T>(dst, g, p, w);
   } else if constexpr (std::is_same<T, double>::value) {
     double f[9][V];

@@ -591,8 +591,9 @@ BATCH_PHASES = ("h2d_ms", "init_ms", "steps_ms", "drift_ms", "moments_ms", "d2h_
 
 
 def lbm_batch_wait(b):
-    """Wait for the queued solves; returns the last solve's device times per
-    phase (dict keyed by BATCH_PHASES) and "unstable": whether a drift array
+    """Wait for the queued solves; returns the device times per phase (dict
+    keyed by BATCH_PHASES; each the median over the solves queued since the
+    previous wait, the last 32 at most) and "unstable": whether a drift array
     passed since the previous wait reports non-finite populations (as
     lbm_batch_drift, that is a result, not an error).  Invalid input fields
     raise LbmError (LBM_EINVAL)."""
