@@ -48,7 +48,7 @@ import lbm_inputs as inp  # noqa: E402
 BYTES_PER_LU = {"f64": 144, "f64dev": 144, "f32": 72, "f16": 36, "bf16": 36}
 KERNEL_SOURCES = ["csrc/step_impl.cuh", "csrc/d2q9_pull.cuh", "csrc/collide.cuh",
                   "csrc/step_f32.cu", "csrc/step_f16.cu", "csrc/step_bf16.cu", "csrc/step_f64.cu",
-                  "csrc/step_f64dev.cu"]
+                  "csrc/step_f64dev.cu", "csrc/resident.cuh"]
 
 
 def parser():
@@ -59,7 +59,7 @@ def parser():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="batched",
                    choices=["batched", "large", "serving", "vn", "opt", "source", "oracle",
-                            "slabs"])
+                            "slabs", "small"])
     p.add_argument("--lattices", type=int, default=512)
     p.add_argument("--lbm-steps", type=int, default=500)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -306,6 +306,11 @@ def bench_batched(args, L, torch, rank, ws):
     if args.batch_variant >= 0:
         L.lbm_batch_set_variant(b, args.batch_variant)
     lbm_steps = args.lbm_steps
+    # members held in shared memory for all the steps of a call (one launch
+    # beside the per-step launches; no per-step HBM traffic)
+    resident = L.lbm_batch_resident(b)
+    res_nodes = sum(s["nx"] * s["ny"] for s, r in zip(specs, resident) if r)
+    step_nodes = nodes - res_nodes  # the per-step kernel's lattice updates
 
     def one_step():
         L.lbm_batch_step(b, lbm_steps)
@@ -338,7 +343,9 @@ def bench_batched(args, L, torch, rank, ws):
     lu_job = reduce_sum(lu_per_step * args.steps)  # every rank's lattice updates
     value = job_mlups(lu_job, total_ms * 1e-3)
     launch_ms = float(np.mean(step_ms)) / lbm_steps  # one batched kernel per time step
-    launches = args.steps * (lbm_steps + 2)  # batched steps + one drift launch pair
+    # batched steps, the resident launch (one per storage type) and one
+    # drift launch pair
+    launches = args.steps * (lbm_steps + 2 + (1 if resident.any() else 0))
 
     # e2e: host fields in, moments out, through the public API: one
     # lbm_batch_solve_packed call per benchmark step (upload of the fields
@@ -404,24 +411,24 @@ def bench_batched(args, L, torch, rank, ws):
     peak, peak_kind = peaks()
     kname = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16"}[bdt]
     sname = {"f32": "FP32", "f16": "FP16", "bf16": "BF16"}[bdt]
-    achieved = BYTES_PER_LU[bdt] * nodes / (launch_ms * 1e-3) / 1e9
+    achieved = BYTES_PER_LU[bdt] * step_nodes / (launch_ms * 1e-3) / 1e9
     tr = traffic_record("k_step_batch<%s>" % kname)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
                 # ncu DRAM bytes per lattice update of a smaller capture of the
                 # same kernel, scaled to this launch's lattice updates
-                "traffic": (round(tr["dram_bytes_per_lu"] * nodes) if tr else None),
+                "traffic": (round(tr["dram_bytes_per_lu"] * step_nodes) if tr else None),
                 "kernel": "k_step_batch<%s> (launch variant %d)" % (kname, variant),
                 "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": BYTES_PER_LU[bdt] * nodes,
+                "algorithmic_bytes_per_launch": BYTES_PER_LU[bdt] * step_nodes,
                 "avg_launch_ms": round(launch_ms, 4),
                 # against GB300's nominal 7.9 TB/s HBM3e, and the DRAM bytes
                 # ncu counted (traffic) over the same launch time
                 "nominal_peak": NOMINAL_HBM_GBS,
                 "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
-                "achieved_dram": (round(tr["dram_bytes_per_lu"] * nodes / (launch_ms * 1e-3) / 1e9, 1)
+                "achieved_dram": (round(tr["dram_bytes_per_lu"] * step_nodes / (launch_ms * 1e-3) / 1e9, 1)
                                   if tr else None),
-                "dram_frac_of_nominal": (round(tr["dram_bytes_per_lu"] * nodes / (launch_ms * 1e-3)
+                "dram_frac_of_nominal": (round(tr["dram_bytes_per_lu"] * step_nodes / (launch_ms * 1e-3)
                                                / 1e9 / NOMINAL_HBM_GBS, 4) if tr else None)}
     line = {
         "metric": "MLUPS (lattice updates/s, millions), batched %s-deviation D2Q9 MRT" % sname,
@@ -433,6 +440,7 @@ def bench_batched(args, L, torch, rank, ws):
                        args.lattices, {"f32": "fp32", "f16": "fp16", "bf16": "bf16"}[bdt],
                        lbm_steps),
                    "lattices_per_gpu": len(specs), "nodes_per_gpu": nodes,
+                   "resident_lattices": int(resident.sum()), "resident_nodes": res_nodes,
                    "lbm_steps_per_step": lbm_steps, "storage": "%s deviation" % sname.lower(),
                    "l2": "working set %.1f GB per time step > L2 (129 MB)" % (
                        BYTES_PER_LU[bdt] * nodes / 1e9),
@@ -617,6 +625,53 @@ def bench_slabs(args, L, torch):
             "note": "host-timed over the steps (slab steps are issued from the host: one "
                     "boundary-row pair and one interior launch per slab and step, four halo "
                     "copies per slab and step)"}
+
+
+def bench_small(args, L, torch):
+    """A sweep of small lattices (config 4's sampling with areas 32^2 - 56^2,
+    `--lattices` of them, FP32 deviation storage, 500 steps per call): MLUPS
+    with the members held in shared memory for all the steps of a call
+    (k_batch_resident) and with the per-step launches alone
+    (LBM_RESIDENT_BYTES=0), the same handles re-initialised in between."""
+    n = args.lattices
+    specs = inp.batch_specs(n, seed=1107 + 6, amin=32 * 32, amax=56 * 56, steps=500)
+    stream = torch.cuda.current_stream()
+    hs, fields = setup_batch(L, torch, specs, "f32", stream)
+    nodes = sum(sp["nx"] * sp["ny"] for sp in specs)
+    out = {}
+    try:
+        for mode in ("resident", "per_step"):
+            if mode == "per_step":
+                os.environ["LBM_RESIDENT_BYTES"] = "0"
+            for h, f in zip(hs, fields):
+                L.lbm_init_field(h, *f)
+            b = L.lbm_batch_create(hs)
+            try:
+                nres = int(L.lbm_batch_resident(b).sum())
+                L.lbm_batch_step(b, 500)  # warm-up (and tuning)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(args.steps):
+                    L.lbm_batch_step(b, 500)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+            finally:
+                L.lbm_batch_destroy(b)
+            out[mode] = {"mlups": round(nodes * 500 * args.steps / (ms * 1e-3) / 1e6, 1),
+                         "ms_per_500_steps": round(ms / args.steps, 3),
+                         "resident_lattices": nres}
+    finally:
+        os.environ.pop("LBM_RESIDENT_BYTES", None)
+        for h in hs:
+            L.lbm_destroy(h)
+    return {"metric": "MLUPS, a sweep of %d small FP32-deviation lattices" % n,
+            "value": out["resident"]["mlups"], "unit": "MLUPS", "higher_is_better": True,
+            "config": {"workload": "sweep-%d-lattices-32to56-fp32dev-500-steps" % n,
+                       "nodes": nodes},
+            "modes": out,
+            "speedup": round(out["resident"]["mlups"] / out["per_step"]["mlups"], 2)}
 
 
 def bench_vn(args, L, torch):
@@ -853,6 +908,10 @@ def main():
     if args.workload == "slabs":
         if rank == 0:
             print(json.dumps(bench_slabs(args, L, torch)))
+        return
+    if args.workload == "small":
+        if rank == 0:
+            print(json.dumps(bench_small(args, L, torch)))
         return
     if args.workload == "opt":
         if rank == 0:

@@ -441,6 +441,18 @@ int lbm_batch_tune(lbm_batch b, double *times_ms, int *chosen);
  * batch). */
 int lbm_batch_set_variant(lbm_batch b, int variant);
 int lbm_batch_get_variant(lbm_batch b, int *variant);
+/* (runtime; no counterpart in the paper) Which members the batch keeps in
+ * shared memory for all the steps of a launch (flags: one int per member, 1
+ * for such a member): lattices whose two step buffers of 9 compact planes,
+ * 2 x 9 x nx x ny x element bytes, fit one block's shared memory (227 KB on
+ * GB300: up to 56 x 56 nodes in FP32, 80 x 80 in FP16 / BF16), unless the
+ * environment variable LBM_RESIDENT_BYTES, read when the batch is made,
+ * caps that size (0: none).  One thread block per such member runs all the
+ * steps of an lbm_batch_step call (or of a server generation) in one launch
+ * beside the per-step launches of the other members, reading and writing
+ * the member's populations in HBM once; results are bit-identical either
+ * way. */
+int lbm_batch_resident(lbm_batch b, int *flags);
 /* The sums of lbm_drift for every member at once (out: 4 doubles per member,
  * in member order): one reduction launch pair for the whole batch,
  * reproducible per member.  Synchronizes the batch stream; returns

@@ -61,6 +61,21 @@ void dev_free(void *p) {
     cudaFree(p);
 }
 
+size_t resident_limit(int device) {
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    optin = 0;
+  }
+  size_t lim = (size_t)(optin > 0 ? optin : 0);
+  if (const char *v = getenv("LBM_RESIDENT_BYTES")) {
+    const size_t cap = (size_t)strtoull(v, nullptr, 10);
+    if (cap < lim) lim = cap;
+  }
+  return lim;
+}
+
 int sm_count() {
   int d = 0, n = 0;
   if (cudaGetDevice(&d) != cudaSuccess ||
@@ -1006,10 +1021,22 @@ struct lbm_batch_ctx {
     BatchEntry *ents = nullptr;
     BlockRec *blocks = nullptr;
     int *limits = nullptr;  // per-entry step limits of a ragged generation
+    // entries held in shared memory for all the steps of a launch (small
+    // lattices; k_batch_resident), which the block records leave out; in
+    // three classes by size (up to a third, a half, all of a block's shared
+    // memory), one launch each, so that small ones share an SM
+    int nres = 0;
+    int *res = nullptr;
+    int res_count[3] = {0, 0, 0};
+    size_t res_smem[3] = {0, 0, 0};  // shared memory of a block of the class
   };
   std::vector<int> member_group, member_local;  // member -> (group, entry)
+  std::vector<int> member_res;                  // member stepped as a resident entry
   bool spent = false;  // a ragged generation ran: members' parities differ
   std::vector<Group> groups;
+  bool resident = false;                 // some group has resident entries
+  cudaStream_t res_stream = nullptr;     // their launches, beside the batch stream
+  cudaEvent_t res_fork = nullptr, res_join = nullptr;
   std::vector<int> offs;                 // member buffer index at creation
   std::vector<cudaStream_t> saved_streams;
   AuxView *views[2] = {nullptr, nullptr}; // drift views at batch parity 0 / 1
@@ -1092,6 +1119,34 @@ static BatchList batch_list(const lbm_batch_ctx::Group &gr) {
   bl.nblocks = gr.nblocks;
   bl.ntasks = gr.ntasks;
   return bl;
+}
+
+// Launch the resident entries of every group for `steps` steps from batch
+// parity `parity` (limits: per-entry step limits of a ragged generation, or
+// null) on the side stream, forked from the batch stream; resident_join
+// makes the batch stream wait for them.
+static int resident_fork(lbm_batch_ctx *b, int parity, long steps, bool ragged) {
+  if (!b->resident || steps < 1) return LBM_OK;
+  if (!b->res_stream) {
+    CK(cudaStreamCreateWithFlags(&b->res_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&b->res_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&b->res_join, cudaEventDisableTiming));
+  }
+  CK(cudaEventRecord(b->res_fork, b->stream));
+  CK(cudaStreamWaitEvent(b->res_stream, b->res_fork, 0));
+  for (auto &gr : b->groups)
+    for (int c = 0, off = 0; c < 3; off += gr.res_count[c++])
+      if (gr.res_count[c] > 0)
+        CK(launch_batch_resident(gr.dtype, gr.ents, gr.res + off, gr.res_count[c],
+                                 gr.res_smem[c], parity, steps, ragged ? gr.limits : nullptr,
+                                 b->res_stream));
+  CK(cudaEventRecord(b->res_join, b->res_stream));
+  return LBM_OK;
+}
+
+static int resident_join(lbm_batch_ctx *b) {
+  if (b->resident && b->res_join) CK(cudaStreamWaitEvent(b->stream, b->res_join, 0));
+  return LBM_OK;
 }
 
 static cudaError_t batch_launch_all(lbm_batch_ctx *b, int parity, cudaStream_t st,
@@ -1242,10 +1297,14 @@ int batch_step_ragged(lbm_batch_ctx *b, const long *steps, long n) {
   for (size_t gi = 0; gi < b->groups.size(); ++gi)
     CK(cudaMemcpyAsync(b->groups[gi].limits, lim[gi].data(), sizeof(int) * lim[gi].size(),
                        cudaMemcpyHostToDevice, b->stream));
+  int rrc = resident_fork(b, 0, n, true);
+  if (rrc != LBM_OK) return rrc;
   for (long k = 0; k < n; ++k)
     for (auto &gr : b->groups)
       CK(launch_step_batch(gr.dtype, batch_list(gr), (int)(k & 1), b->stream, b->block,
                            b->variant, gr.limits, (int)k));
+  rrc = resident_join(b);
+  if (rrc != LBM_OK) return rrc;
   for (size_t mi = 0; mi < nm; ++mi) {
     b->members[mi]->L.cur = b->offs[mi] ^ (int)(take[mi] & 1);
     b->members[mi]->t += take[mi];
@@ -1260,11 +1319,13 @@ long long batch_nodes(const lbm_batch_ctx *b) { return b->nodes; }
 
 static void batch_free(lbm_batch_ctx *b) {
   batch_drop_graphs(b);
-  for (auto *st : {b->up, b->down})
+  for (auto *st : {b->up, b->down, b->res_stream})
     if (st) {
       cudaStreamSynchronize(st);
       cudaStreamDestroy(st);
     }
+  for (auto *ev : {b->res_fork, b->res_join})
+    if (ev) cudaEventDestroy(ev);
   for (auto &r : b->ring)
     for (auto &e : r)
       if (e) cudaEventDestroy(e);
@@ -1287,6 +1348,7 @@ static void batch_free(lbm_batch_ctx *b) {
     dev_free(gr.ents);
     dev_free(gr.blocks);
     dev_free(gr.limits);
+    dev_free(gr.res);
   }
   dev_free(b->views[0]);
   dev_free(b->views[1]);
@@ -1507,9 +1569,13 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
   const int wpb = b->block / 32;
   b->member_group.assign(b->members.size(), -1);
   b->member_local.assign(b->members.size(), -1);
+  b->member_res.assign(b->members.size(), 0);
+  const size_t res_max = resident_limit(dev);
   for (int dt : {LBM_F32DEV, LBM_F16DEV, LBM_BF16DEV}) {
     std::vector<BatchEntry> ents;
     std::vector<BlockRec> bl;  // the plain grid's blocks
+    std::vector<int> res_cls[3];  // resident entries by size class
+    size_t res_smem[3] = {0, 0, 0};
     long long t0 = 0;
     for (size_t mi = 0; mi < b->members.size(); ++mi) {
       auto *m = b->members[mi];
@@ -1522,6 +1588,15 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
       e.buf[0] = m->L.buf[0];
       e.buf[1] = m->L.buf[1];
       e.off = m->L.cur;
+      const size_t rb = resident_bytes(m->L.g.nx, m->L.g.ny, m->L.esize);
+      if (rb <= res_max) {
+        b->member_res[mi] = 1;
+        const int c = rb <= res_max / 3 ? 0 : (rb <= res_max / 2 ? 1 : 2);
+        res_cls[c].push_back((int)ents.size());
+        res_smem[c] = std::max(res_smem[c], rb);
+        ents.push_back(e);
+        continue;
+      }
       t0 += m->L.g.tasks;
       for (long long tb = 0; tb < m->L.g.tasks; tb += wpb) {
         BlockRec r;
@@ -1544,16 +1619,29 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
     gr.ents = (BatchEntry *)dev_alloc(sizeof(BatchEntry) * ents.size());
     gr.blocks = (BlockRec *)dev_alloc(sizeof(BlockRec) * bl.size());
     gr.limits = (int *)dev_alloc(sizeof(int) * ents.size());
+    std::vector<int> res;
+    for (int c = 0; c < 3; ++c) {
+      res.insert(res.end(), res_cls[c].begin(), res_cls[c].end());
+      gr.res_count[c] = (int)res_cls[c].size();
+      gr.res_smem[c] = res_smem[c];
+    }
+    gr.nres = (int)res.size();
+    if (gr.nres > 0) {
+      gr.res = (int *)dev_alloc(sizeof(int) * res.size());
+      b->resident = true;
+    }
     b->groups.push_back(gr);
-    if (!gr.ents || !gr.blocks || !gr.limits) {
+    if (!gr.ents || !gr.blocks || !gr.limits || (gr.nres > 0 && !gr.res)) {
       set_error("cannot allocate batch tables");
       batch_free(b);
       return LBM_ENOMEM;
     }
     if (cudaMemcpyAsync(gr.ents, ents.data(), sizeof(BatchEntry) * ents.size(),
                         cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
-        cudaMemcpyAsync(gr.blocks, bl.data(), sizeof(BlockRec) * bl.size(),
-                        cudaMemcpyHostToDevice, b->stream) != cudaSuccess) {
+        (!bl.empty() && cudaMemcpyAsync(gr.blocks, bl.data(), sizeof(BlockRec) * bl.size(),
+                                        cudaMemcpyHostToDevice, b->stream) != cudaSuccess) ||
+        (gr.nres > 0 && cudaMemcpyAsync(gr.res, res.data(), sizeof(int) * res.size(),
+                                        cudaMemcpyHostToDevice, b->stream) != cudaSuccess)) {
       set_error("cannot upload batch tables");
       cudaGetLastError();
       batch_free(b);
@@ -1619,6 +1707,10 @@ int lbm_batch_step(lbm_batch b, long n) {
     int rc = maybe_autotune_batch(b);
     if (rc != LBM_OK) return rc;
   }
+  // resident members: all n steps in one launch per storage type, beside
+  // the per-step launches of the others
+  int rrc = resident_fork(b, b->parity, n, false);
+  if (rrc != LBM_OK) return rrc;
   // whole graphs of 64 steps, the remainder as one graph of its own length
   // (both cached), so a call of n steps is a handful of graph launches
   const long G = 64;
@@ -1644,6 +1736,8 @@ int lbm_batch_step(lbm_batch b, long n) {
     n -= k;
     done += k;
   }
+  rrc = resident_join(b);
+  if (rrc != LBM_OK) return rrc;
   for (size_t k = 0; k < b->members.size(); ++k) {
     b->members[k]->L.cur = b->offs[k] ^ b->parity;
     b->members[k]->t += done;
@@ -1998,6 +2092,12 @@ int lbm_batch_wait(lbm_batch b, double *phase_ms) {
 int lbm_get_variant(lbm_handle h, int *variant) {
   REQUIRE(h != nullptr && variant != nullptr, "null argument");
   *variant = h->L.dtype == LBM_F64 ? 0 : (h->tuned ? h->L.variant : -1);
+  return LBM_OK;
+}
+
+int lbm_batch_resident(lbm_batch b, int *flags) {
+  REQUIRE(b != nullptr && flags != nullptr, "null argument");
+  for (size_t k = 0; k < b->members.size(); ++k) flags[k] = b->member_res[k];
   return LBM_OK;
 }
 

@@ -127,6 +127,37 @@ inline cudaError_t launch_step_batch(int dtype, const BatchList &bl, int parity,
   }
 }
 
+// Batch members small enough to stay in shared memory for all the steps of
+// a launch (k_batch_resident, resident.cuh): both step buffers of 9 compact
+// planes.  resident_limit: the device's shared memory per block, lowered by
+// the environment variable LBM_RESIDENT_BYTES (0 turns resident members off).
+inline size_t resident_bytes(int nx, int ny, int esize) {
+  return (size_t)2 * 9 * (size_t)nx * (size_t)ny * (size_t)esize;
+}
+size_t resident_limit(int device);
+cudaError_t launch_batch_resident_f32(const BatchEntry *ents, const int *idx, int nres,
+                                      size_t smem, int parity, long steps, const int *limits,
+                                      cudaStream_t st);
+cudaError_t launch_batch_resident_f16(const BatchEntry *ents, const int *idx, int nres,
+                                      size_t smem, int parity, long steps, const int *limits,
+                                      cudaStream_t st);
+cudaError_t launch_batch_resident_bf16(const BatchEntry *ents, const int *idx, int nres,
+                                       size_t smem, int parity, long steps, const int *limits,
+                                       cudaStream_t st);
+inline cudaError_t launch_batch_resident(int dtype, const BatchEntry *ents, const int *idx,
+                                         int nres, size_t smem, int parity, long steps,
+                                         const int *limits, cudaStream_t st) {
+  switch (dtype) {
+    case LBM_F32DEV:
+      return launch_batch_resident_f32(ents, idx, nres, smem, parity, steps, limits, st);
+    case LBM_F16DEV:
+      return launch_batch_resident_f16(ents, idx, nres, smem, parity, steps, limits, st);
+    case LBM_BF16DEV:
+      return launch_batch_resident_bf16(ents, idx, nres, smem, parity, steps, limits, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // Nodes per vector of a storage type (host side of d2q9_pull.cuh's Elem).
 inline int vec_nodes(int dtype) {
   return dtype == LBM_F64 || dtype == LBM_F64DEV ? 2

@@ -207,6 +207,13 @@ cudaError_t launch_step_dev_t(const Lattice &L, const void *src, void *dst, cuda
   return cudaGetLastError();
 }
 
+}  // namespace lbm
+
+// small batch members held in shared memory (uses the collisions above)
+#include "resident.cuh"
+
+namespace lbm {
+
 template <typename T>
 cudaError_t launch_step_batch_t(const BatchList &bl, int parity, cudaStream_t st, int block,
                                 int variant, const int *limits, int k) {

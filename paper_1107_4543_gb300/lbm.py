@@ -76,6 +76,7 @@ _SIGS = {
     "lbm_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_batch_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_batch_get_variant": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_resident": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "lbm_get_variant": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "lbm_opt_cost": (ctypes.c_int, [ctypes.POINTER(lbm_cost_spec), ctypes.c_int, _dp, _dp]),
     "lbm_opt_minimize": (ctypes.c_int, [ctypes.POINTER(lbm_cost_spec), _dp, ctypes.c_uint, _dp,
@@ -285,6 +286,16 @@ def lbm_batch_get_variant(b):
     v = ctypes.c_int()
     _ck(load().lbm_batch_get_variant(b, ctypes.byref(v)), "lbm_batch_get_variant")
     return v.value
+
+
+def lbm_batch_resident(b):
+    """Per member: whether the batch keeps it in shared memory for all the
+    steps of a launch (bool array in member order)."""
+    n = lbm_batch_size(b)[0]
+    f = np.zeros(n, dtype=np.int32)
+    _ck(load().lbm_batch_resident(b, f.ctypes.data_as(ctypes.POINTER(ctypes.c_int))),
+        "lbm_batch_resident")
+    return f.astype(bool)
 
 
 def lbm_batch_tune(b):

@@ -100,6 +100,55 @@ def test_every_batch_launch_variant_equals_alone(L, variant):
         assert np.array_equal(got[k], want, equal_nan=True), (variant, k, dt)
 
 
+RESIDENT_CASES = [(5, 3, "f32"), (56, 56, "f32"), (58, 56, "f32"), (2, 7, "f32"),
+                  (33, 17, "f16"), (80, 80, "f16"), (81, 80, "f16"), (80, 80, "bf16"),
+                  (9, 2, "bf16"), (130, 40, "f32"), (200, 90, "bf16")]
+
+
+@pytest.mark.parametrize("cap", [None, "0"])
+def test_resident_members_equal_alone(L, cap, monkeypatch):
+    """Members small enough for one block's shared memory (both step buffers
+    of 9 compact planes) are stepped there for all the steps of a launch,
+    beside the per-step launches of the others (lbm_batch_resident says
+    which); every member equals its standalone run bit for bit, with the
+    resident path on and off (LBM_RESIDENT_BYTES=0), over calls of odd and
+    even length, one of them starting at batch parity 1."""
+    torch = pytest.importorskip("torch")
+    optin = torch.cuda.get_device_properties(0).shared_memory_per_block_optin
+    if cap is not None:
+        monkeypatch.setenv("LBM_RESIDENT_BYTES", cap)
+    specs = small_specs(len(RESIDENT_CASES), seed=17)
+    for sp, (nx, ny, _) in zip(specs, RESIDENT_CASES):
+        sp.update(nx=nx, ny=ny, xc=nx / 2, yc=ny / 2, b=2.0)
+    dtypes = [dt for _, _, dt in RESIDENT_CASES]
+    esize = {"f32": 4, "f16": 2, "bf16": 2}
+    want_res = [cap is None and 2 * 9 * nx * ny * esize[dt] <= optin for nx, ny, dt in RESIDENT_CASES]
+    # the cases straddle the limit on GB300 (227 KB): 56 x 56 FP32 and
+    # 80 x 80 FP16 fit, 58 x 56 and 81 x 80 do not
+    assert cap is not None or (any(want_res) and not all(want_res))
+    hs = []
+    try:
+        for spec, dt in zip(specs, dtypes):
+            h = L.lbm_create(spec["nx"], spec["ny"], inp.s_ll(spec["rates"]), 1.0, (0.0, 0.0),
+                             L.DTYPES[dt])
+            L.lbm_init_field(h, *inp.batch_fields(spec))
+            hs.append(h)
+        b = L.lbm_batch_create(hs)
+        assert list(L.lbm_batch_resident(b)) == want_res
+        for n in (37, 1, 64, 2):
+            L.lbm_batch_step(b, n)
+        drift = L.lbm_batch_drift(b, len(hs))
+        got = [L.lbm_get_populations(h) for h in hs]
+        L.lbm_batch_destroy(b)
+    finally:
+        for h in hs:
+            L.lbm_destroy(h)
+    for k, (spec, dt) in enumerate(zip(specs, dtypes)):
+        want, _ = alone(L, spec, dt, 104)
+        assert np.array_equal(got[k], want), (k, dt, spec["nx"], spec["ny"], want_res[k])
+    assert np.all(np.isfinite(drift))
+
+
 def test_batch_host_io_equals_member_calls(L):
     """lbm_batch_init_fields / lbm_batch_moments give exactly what the
     per-member calls give, keep the batch usable across re-inits, and reject
