@@ -554,8 +554,17 @@ def bench_serving(args, L, torch):
     pending = {}
     lat = []
     failed = 0
+    # the admitted-concurrency trace: every 2 s, [time s, resident lattices,
+    # resident GB, requests waiting for admission]
+    trace = []
+    next_sample = 0.0
     while k < len(reqs) or pending:
         now = time.perf_counter() - t0
+        if now >= next_sample:
+            st = L.lbm_server_stats(srv)
+            trace.append([round(now, 1), st["resident"], round(st["resident_bytes"] / 1e9, 2),
+                          st["submitted"] - st["admitted"]])
+            next_sample += 2.0
         while k < len(reqs) and reqs[k]["arrival"] <= now:
             q = reqs[k]
             init = q["init"]
@@ -590,6 +599,8 @@ def bench_serving(args, L, torch):
             "requests": {"completed": len(lat), "failed": failed},
             "peak_resident_lattices": st["peak_resident"],
             "wall_s": round(wall, 2),
+            "admitted_trace": {"columns": ["t_s", "resident_lattices", "resident_gb", "queued"],
+                               "every_s": 2.0, "samples": trace},
             "server": st}
 
 

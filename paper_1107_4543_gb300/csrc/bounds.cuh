@@ -10,8 +10,9 @@
 // Checked: the von Neumann QR's row and column indices that follow the
 // deflation bounds (vn.cu), the optimizer's polynomial-matrix slots, power
 // blocks, point-table and K_l-table offsets (optcost.cu), the batched
-// step's block records and lane positions (step_impl.cuh), and the batched
-// init / moments blocks (io_dev.cu).
+// step's block records and lane positions (step_impl.cuh), the resident
+// batch members' entries (resident.cuh), and the batched init / moments
+// blocks (io_dev.cu).
 #pragma once
 #include <cuda_runtime.h>
 

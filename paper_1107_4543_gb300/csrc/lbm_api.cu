@@ -1137,7 +1137,7 @@ static int resident_fork(lbm_batch_ctx *b, int parity, long steps, bool ragged) 
   for (auto &gr : b->groups)
     for (int c = 0, off = 0; c < 3; off += gr.res_count[c++])
       if (gr.res_count[c] > 0)
-        CK(launch_batch_resident(gr.dtype, gr.ents, gr.res + off, gr.res_count[c],
+        CK(launch_batch_resident(gr.dtype, gr.ents, gr.res + off, gr.res_count[c], gr.n,
                                  gr.res_smem[c], parity, steps, ragged ? gr.limits : nullptr,
                                  b->res_stream));
   CK(cudaEventRecord(b->res_join, b->res_stream));

@@ -136,24 +136,25 @@ inline size_t resident_bytes(int nx, int ny, int esize) {
 }
 size_t resident_limit(int device);
 cudaError_t launch_batch_resident_f32(const BatchEntry *ents, const int *idx, int nres,
-                                      size_t smem, int parity, long steps, const int *limits,
-                                      cudaStream_t st);
+                                      int nents, size_t smem, int parity, long steps,
+                                      const int *limits, cudaStream_t st);
 cudaError_t launch_batch_resident_f16(const BatchEntry *ents, const int *idx, int nres,
-                                      size_t smem, int parity, long steps, const int *limits,
-                                      cudaStream_t st);
+                                      int nents, size_t smem, int parity, long steps,
+                                      const int *limits, cudaStream_t st);
 cudaError_t launch_batch_resident_bf16(const BatchEntry *ents, const int *idx, int nres,
-                                       size_t smem, int parity, long steps, const int *limits,
-                                       cudaStream_t st);
+                                      int nents, size_t smem, int parity, long steps,
+                                      const int *limits, cudaStream_t st);
 inline cudaError_t launch_batch_resident(int dtype, const BatchEntry *ents, const int *idx,
-                                         int nres, size_t smem, int parity, long steps,
-                                         const int *limits, cudaStream_t st) {
+                                         int nres, int nents, size_t smem, int parity,
+                                         long steps, const int *limits, cudaStream_t st) {
   switch (dtype) {
     case LBM_F32DEV:
-      return launch_batch_resident_f32(ents, idx, nres, smem, parity, steps, limits, st);
+      return launch_batch_resident_f32(ents, idx, nres, nents, smem, parity, steps, limits, st);
     case LBM_F16DEV:
-      return launch_batch_resident_f16(ents, idx, nres, smem, parity, steps, limits, st);
+      return launch_batch_resident_f16(ents, idx, nres, nents, smem, parity, steps, limits, st);
     case LBM_BF16DEV:
-      return launch_batch_resident_bf16(ents, idx, nres, smem, parity, steps, limits, st);
+      return launch_batch_resident_bf16(ents, idx, nres, nents, smem, parity, steps, limits,
+                                        st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -12,6 +12,7 @@
 #pragma once
 #include <type_traits>
 
+#include "bounds.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -76,10 +77,11 @@ struct Walk {
 // in the buffer that parity of steps selects, as the per-step launches do.
 template <typename T>
 __global__ void __launch_bounds__(kResidentThreads, 2)
-k_batch_resident(const BatchEntry *__restrict__ ents, const int *__restrict__ idx, int parity,
-                 int steps, const int *__restrict__ limits) {
+k_batch_resident(const BatchEntry *__restrict__ ents, const int *__restrict__ idx, int nents,
+                 int parity, int steps, const int *__restrict__ limits) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int e = idx[blockIdx.x];
+  if (!bounds::ok(e >= 0 && e < nents, bounds::BATCH_REC)) return;  // block-uniform
   const BatchEntry &E = ents[e];
   const int nx = E.g.nx, ny = E.g.ny, N = nx * ny;
   int n = steps;
@@ -149,8 +151,9 @@ k_batch_resident(const BatchEntry *__restrict__ ents, const int *__restrict__ id
 }
 
 template <typename T>
-cudaError_t launch_resident_t(const BatchEntry *ents, const int *idx, int nres, size_t smem,
-                              int parity, long steps, const int *limits, cudaStream_t st) {
+cudaError_t launch_resident_t(const BatchEntry *ents, const int *idx, int nres, int nents,
+                              size_t smem, int parity, long steps, const int *limits,
+                              cudaStream_t st) {
   if (nres < 1 || steps < 1) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_batch_resident<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -160,7 +163,7 @@ cudaError_t launch_resident_t(const BatchEntry *ents, const int *idx, int nres, 
   for (long done = 0; done < steps; done += chunk) {
     const long k = steps - done < chunk ? steps - done : chunk;
     k_batch_resident<T><<<(unsigned)nres, kResidentThreads, smem, st>>>(
-        ents, idx, parity ^ (int)(done & 1), (int)k, limits);
+        ents, idx, nents, parity ^ (int)(done & 1), (int)k, limits);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -14,9 +14,9 @@ cudaError_t launch_step_batch_f16(const BatchList &bl, int parity, cudaStream_t 
 }
 
 cudaError_t launch_batch_resident_f16(const BatchEntry *ents, const int *idx, int nres,
-                                      size_t smem, int parity, long steps, const int *limits,
-                                      cudaStream_t st) {
-  return launch_resident_t<__half>(ents, idx, nres, smem, parity, steps, limits, st);
+                                      int nents, size_t smem, int parity, long steps,
+                                      const int *limits, cudaStream_t st) {
+  return launch_resident_t<__half>(ents, idx, nres, nents, smem, parity, steps, limits, st);
 }
 
 unsigned bounds_word_step_f16(bool reset) { return bounds::read_word(reset); }

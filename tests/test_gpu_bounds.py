@@ -7,8 +7,9 @@ sets a bit of a device word and the access is redirected to the array's
 first element (no trap).  A fresh process loads the debug library and runs
 small cases of every checked kernel -- the von Neumann sweep, the optimizer
 cost (orders 3 - 6, both kinds), batched steps in every launch variant with
-mixed storage types (plain and persistent grids, ragged step counts through
-the server), the pipelined solve's batched init and moments -- and the
+mixed storage types (plain and persistent grids, the small members held in
+shared memory, ragged step counts through the server), the pipelined
+solve's batched init and moments -- and the
 word must stay zero; the self-test (one checked access past its bound) must
 set its bit, which shows the checks are live.
 """
