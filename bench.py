@@ -355,7 +355,10 @@ def bench_batched(args, L, torch, rank, ws):
     # the timed region and reports the device time per phase (median over
     # the timed solves)
     def pinned_flat():
-        return torch.empty(nodes, dtype=torch.float64, pin_memory=True).numpy()
+        # page-locked host memory on huge pages (lbm_host_alloc): copies from
+        # ordinary page-locked memory slowed to 17 - 80 GB/s on a host that
+        # had run for a while
+        return L.host_array(nodes)
 
     fin = tuple(pinned_flat() for _ in range(3))
     for c in range(3):

@@ -248,6 +248,18 @@ int lbm_info(lbm_handle h, lbm_info_t *out);
  * staging that lbm_vn_eigs keeps for the life of the process uses
  * cudaMalloc / cudaHostAlloc directly, so that it never outlives the
  * allocator that made it. */
+/* (runtime; no counterpart in the paper) Page-locked host memory for the
+ * host arrays of the I/O calls (lbm_batch_solve_packed's fields and
+ * moments above all): an anonymous mapping advised for transparent huge
+ * pages -- arrays of at least a quarter huge page start on a huge-page
+ * boundary and fill whole huge pages -- touched, then registered with the
+ * CUDA driver, so that a copy walks few page translations.  Returns NULL
+ * (message in lbm_last_error) when the mapping or the registration fails.
+ * lbm_host_free releases one such array (LBM_EINVAL for any other
+ * pointer; NULL is a no-op). */
+void *lbm_host_alloc(size_t bytes);
+int lbm_host_free(void *p);
+
 typedef void *(*lbm_alloc_fn)(size_t bytes, void *ctx);
 typedef void (*lbm_free_fn)(void *ptr, void *ctx);
 int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void *ctx);

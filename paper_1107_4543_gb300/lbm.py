@@ -8,6 +8,7 @@ fails.
 """
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -99,6 +100,8 @@ _SIGS = {
     "lbm_set_allocator": (ctypes.c_int, [_vp, _vp, _vp]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "lbm_last_error": (ctypes.c_char_p, []),
+    "lbm_host_alloc": (ctypes.c_void_p, [ctypes.c_size_t]),
+    "lbm_host_free": (ctypes.c_int, [ctypes.c_void_p]),
     "lbm_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "lbm_vn_eigs": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp,
                                    ctypes.POINTER(ctypes.c_int)]),
@@ -203,6 +206,31 @@ def lbm_strerror(code):
 
 def lbm_last_error():
     return load().lbm_last_error().decode()
+
+
+def lbm_host_alloc(nbytes):
+    """Address of nbytes of page-locked huge-page host memory (raises on
+    failure); release it with lbm_host_free."""
+    p = load().lbm_host_alloc(int(nbytes))
+    if not p:
+        raise LbmError(LBM_ENOMEM, "lbm_host_alloc")
+    return p
+
+
+def lbm_host_free(p):
+    _ck(load().lbm_host_free(ctypes.c_void_p(p)), "lbm_host_free")
+
+
+def host_array(shape, dtype=np.float64):
+    """A numpy array in page-locked huge-page host memory (lbm_host_alloc),
+    released once the array and every view of it are gone."""
+    dtype = np.dtype(dtype)
+    count = int(np.prod(shape))
+    nbytes = max(count * dtype.itemsize, 1)
+    p = lbm_host_alloc(nbytes)
+    buf = (ctypes.c_char * nbytes).from_address(p)
+    weakref.finalize(buf, load().lbm_host_free, ctypes.c_void_p(p))
+    return np.frombuffer(buf, dtype=dtype, count=count).reshape(shape)
 
 
 def lbm_create(nx, ny, S, rho0=1.0, u0=(0.0, 0.0), dtype=LBM_F32DEV):

@@ -225,6 +225,28 @@ def test_batch_packed_io_equals_per_member_io(L):
             L.lbm_destroy(h)
 
 
+def test_host_array(L):
+    """lbm_host_alloc arrays: any size, written and read through numpy, a
+    device copy round trip, released with the array; other pointers are
+    refused by lbm_host_free."""
+    torch = pytest.importorskip("torch")
+    for n in (1, 1000, 3 << 20):
+        a = L.host_array(n)
+        assert a.shape == (n,) and a.dtype == np.float64 and np.all(a == 0)
+        a[:] = np.arange(n)
+        t = torch.from_numpy(a)
+        assert t.is_pinned()
+        d = t.to("cuda", non_blocking=True)
+        back = L.host_array((n,))
+        torch.from_numpy(back).copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+        assert np.array_equal(back, a)
+        del a, t, back
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_host_free(12345)
+    assert e.value.code == L.LBM_EINVAL
+
+
 def test_batch_solve_packed_equals_synchronous_calls(L):
     """lbm_batch_solve_packed (upload, init, steps, drift, moments, download
     queued without waiting, successive solves overlapping through two
@@ -259,7 +281,9 @@ def test_batch_solve_packed_equals_synchronous_calls(L):
     ha, hb = make(), make()
     try:
         ba, bb = L.lbm_batch_create(ha), L.lbm_batch_create(hb)
-        outs = [tuple(pinned(total) for _ in range(3)) for _ in range(3)]
+        # outputs in page-locked huge-page memory (lbm_host_alloc), inputs
+        # in torch's page-locked memory
+        outs = [tuple(L.host_array(total) for _ in range(3)) for _ in range(3)]
         drifts = [np.zeros((len(specs), 4)) for _ in range(3)]
         for rep in range(3):
             L.lbm_batch_solve_packed(bb, steps[rep], ins[rep], outs[rep], drifts[rep])
