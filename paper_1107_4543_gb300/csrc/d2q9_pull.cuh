@@ -183,7 +183,7 @@ template <> struct Elem<double> {
 struct Geom {
   int nx, ny, pitch;  // pitch: elements per row of one plane (a multiple of 128 bytes)
   int nchunks;      // real vectors per row: ceil(nx / V)
-  int cpr;          // chunk slots per row: pitch / V (>= nchunks)
+  int cpr;          // chunk slots per row of the task mapping: pitch / V, or nchunks
   // y extent of the periodic wrap: ny for a whole periodic lattice; 0 for a
   // slab of rows whose neighbouring rows y = -1 and y = ny are stored halo
   // rows (the wrap is then the identity)
@@ -214,7 +214,13 @@ inline Geom make_geom(int nx, int ny, int V, int esize) {
   g.pitch = (nx + align - 1) / align * align;
   g.nyw = ny;
   g.nchunks = (nx + V - 1) / V;
-  g.cpr = g.pitch / V;  // whole lines of chunks: tasks start on lines
+  // chunk slots per row of the task mapping: whole lines of chunks, so that
+  // every task starts on a line; but rows whose padding slots exceed an
+  // eighth of the row (short rows: a 40-node FP16 row fills 5 of its 8
+  // slots) map their real chunks only, leaving no lane idle, tasks then
+  // starting anywhere in a row
+  const int slots = g.pitch / V;
+  g.cpr = (slots - g.nchunks) * 8 > slots ? g.nchunks : slots;
   // row-interleaved planes: row y of planes 0..8 lie back to back, so the
   // nine rows a warp task streams share DRAM pages (measured +0.6% on the
   // batched step, +2% on one 8192^2 lattice against plane after plane)
