@@ -366,19 +366,11 @@ def bench_batched(args, L, torch, rank, ws):
     fout = tuple(pinned_flat() for _ in range(3))
     dout = np.zeros((len(hs), 4))
 
-    pipelined = bdt != "f16"  # FP16 members take their storage scale on the host
-
     def e2e_solve():
-        if pipelined:
-            L.lbm_batch_solve_packed(b, lbm_steps, fin, fout, dout)
-        else:
-            L.lbm_batch_init_packed(b, *fin)
-            L.lbm_batch_step(b, lbm_steps)
-            dout[...] = L.lbm_batch_drift(b, len(hs))
-            L.lbm_batch_moments_packed(b, fout)
+        L.lbm_batch_solve_packed(b, lbm_steps, fin, fout, dout)
 
     def e2e_wait():
-        return L.lbm_batch_wait(b) if pipelined else None
+        return L.lbm_batch_wait(b)
 
     for _ in range(2):
         e2e_solve()
@@ -452,19 +444,15 @@ def bench_batched(args, L, torch, rank, ws):
         "e2e": {"value": round(e2e_value, 1), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "ms_per_step": round(e2e_s * 1e3 / args.steps, 3),
-                "api": ("lbm_batch_solve_packed per step (pinned host fields in, moments and "
-                        "drift out), successive solves overlapped, lbm_batch_wait at the end"
-                        if pipelined else "lbm_batch_init_packed, lbm_batch_step, "
-                        "lbm_batch_drift, lbm_batch_moments_packed per step (synchronous)"),
+                "api": ("lbm_batch_solve_packed per step (page-locked host fields in, moments "
+                        "and drift out), successive solves overlapped, lbm_batch_wait at the "
+                        "end"),
                 # device time of each phase, median over the timed solves (events on the
                 # streams that ran them; the copies overlap the neighbouring
                 # solves' steps)
-                "phases_ms": ({k: round(phases[k], 3) for k in L.BATCH_PHASES} if phases
-                              else None),
-                "h2d_gbs": (round(h2d / max(phases["h2d_ms"], 1e-9) / 1e6, 1) if phases
-                            else None),
-                "d2h_gbs": (round(d2h / max(phases["d2h_ms"], 1e-9) / 1e6, 1) if phases
-                            else None)},
+                "phases_ms": {k: round(phases[k], 3) for k in L.BATCH_PHASES},
+                "h2d_gbs": round(h2d / max(phases["h2d_ms"], 1e-9) / 1e6, 1),
+                "d2h_gbs": round(d2h / max(phases["d2h_ms"], 1e-9) / 1e6, 1)},
         "roofline": roofline,
         "fp64_plain": fp64,
         "gpu_launches": launches,

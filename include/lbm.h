@@ -425,8 +425,9 @@ int lbm_batch_moments_packed(lbm_batch b, double *rho, double *ux, double *uy);
  * The caller owns every host array and must neither free nor change the
  * inputs, nor read the outputs, before lbm_batch_wait returns.  Invalid
  * fields (non-finite, rho <= 0) and non-finite populations are reported by
- * lbm_batch_wait.  FP16 members are refused (LBM_EINVAL): their storage
- * scale is chosen on the host from the fields (use lbm_batch_init_packed). */
+ * lbm_batch_wait.  FP16 members choose their storage scale on the device
+ * from the staged fields, by lbm_init_field's rule, before the init; the
+ * host copy (lbm_info's qscale) follows the last solve's at lbm_batch_wait. */
 int lbm_batch_solve_packed(lbm_batch b, long n, const double *rho_in, const double *ux_in,
                            const double *uy_in, double *rho_out, double *ux_out,
                            double *uy_out, double *drift_out);

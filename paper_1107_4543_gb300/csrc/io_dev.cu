@@ -277,6 +277,49 @@ unsigned grid_for(long long n) {
   return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
+__global__ void __launch_bounds__(256) k_batch_maxdev_fp16(const AuxView *__restrict__ views,
+                                                           const IoBlock *__restrict__ blocks,
+                                                           const long long *__restrict__ poff,
+                                                           long long total, const double *stage,
+                                                           unsigned int *max_bits, int members) {
+  const IoBlock B = blocks[blockIdx.x];
+  if (!bounds::ok(B.member >= 0 && B.member < members, bounds::IO_BLOCK)) return;
+  if (!bounds::ok(B.start >= 0 && B.count >= 0 &&
+                      B.start + B.count <= (long long)views[B.member].g.nx * views[B.member].g.ny &&
+                      poff[B.member] + B.start + B.count <= total,
+                  bounds::IO_BLOCK))
+    return;
+  const AuxView &a = views[B.member];
+  if (a.dtype != LBM_F16DEV) return;  // block-uniform
+  const RefState R = ref_of(a);
+  const double *r = stage + poff[B.member];
+  float m = 0.0f;
+  for (int j = threadIdx.x; j < B.count; j += blockDim.x) {
+    const long long n = B.start + j;
+    double d[9];
+    feq_deviation(R, r[n], r[total + n], r[2 * total + n], d);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) m = fmaxf(m, (float)fabs(d[i]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(max_bits + B.member, __float_as_uint(m));
+}
+
+__global__ void k_batch_set_scales(AuxView *views0, AuxView *views1, BatchEntry *const *ent,
+                                   const unsigned int *max_bits, const double *floor_,
+                                   double *scale_out, int members) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= members || views0[k].dtype != LBM_F16DEV || ent[k] == nullptr) return;
+  const double m = fmax((double)__uint_as_float(max_bits[k]), floor_[k]);
+  const double s = fp16_scale(m);
+  views0[k].scale = s;
+  views1[k].scale = s;
+  ent[k]->dp.scale = (float)s;
+  ent[k]->dp.inv_scale = (float)(1.0 / s);
+  scale_out[k] = s;
+}
+
 }  // namespace
 
 cudaError_t launch_init_dev(const AuxView &a, const double *rho, const double *ux,
@@ -306,6 +349,21 @@ cudaError_t launch_maxdev_dev(const AuxView &a, const double *rho, const double 
   cudaError_t e = cudaMemsetAsync(max_bits, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
   k_maxdev_dev<<<grid_for(N), 256, 0, st>>>(a, make_ref(a), rho, ux, uy, max_bits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_fp16_scales(AuxView *views0, AuxView *views1, BatchEntry *const *ent,
+                                     const IoBlock *blocks, long long nblocks,
+                                     const long long *poff, long long total, const double *stage,
+                                     unsigned int *max_bits, const double *floor_,
+                                     double *scale_out, int members, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(max_bits, 0, sizeof(unsigned int) * members, st);
+  if (e != cudaSuccess) return e;
+  if (nblocks > 0)
+    k_batch_maxdev_fp16<<<(unsigned)nblocks, 256, 0, st>>>(views0, blocks, poff, total, stage,
+                                                           max_bits, members);
+  k_batch_set_scales<<<(members + 127) / 128, 128, 0, st>>>(views0, views1, ent, max_bits, floor_,
+                                                            scale_out, members);
   return cudaGetLastError();
 }
 

@@ -169,21 +169,15 @@ static double source_maxdev(const lbm_ctx *h) {
 // The captured step graphs hold the storage scale (the step kernel's
 // DevParams, the forced-node kernel's AuxView) by value: a new scale drops
 // them, so the next run recaptures.
-static void set_qscale(lbm_ctx *h, double maxabs) {
-  // stored |f'| * qscale stays near 2^14: 11-bit FP16 mantissas with 4x
-  // headroom below the largest finite FP16 (65504), and no subnormals for
-  // values down to 2^-10 of the largest
-  double s = 1.0;
-  if (maxabs > 0 && isfinite(maxabs)) {
-    int k = 14 - (int)ceil(log2(maxabs));
-    k = std::max(-100, std::min(100, k));
-    s = ldexp(1.0, k);
-  }
+static void set_scale(lbm_ctx *h, double s) {
   if (s != h->qscale) free_graph(h);
   h->qscale = s;
   h->L.dp.scale = (float)s;
   h->L.dp.inv_scale = (float)(1.0 / s);
 }
+
+// stored |f'| * qscale stays near 2^14 (fp16_scale)
+static void set_qscale(lbm_ctx *h, double maxabs) { set_scale(h, fp16_scale(maxabs)); }
 
 static int free_graph(lbm_ctx *h) {
   if (h->graph) {
@@ -1176,6 +1170,13 @@ struct lbm_batch_ctx {
   IoBlock *ioblk = nullptr;      // blocks of the batched init / moments launches
   long long nioblk = 0;
   long long *poff_dev = nullptr;  // members' offsets in the packed arrays
+  // FP16 members of pipelined solves choose their storage scale on the
+  // device: per member the largest |f'| (float bits), the floor (a point
+  // source's amplitude), the scale chosen, and the member's batch entry
+  bool has16 = false;
+  unsigned int *smax = nullptr;
+  double *sfloor = nullptr, *sscale = nullptr;
+  BatchEntry **sent = nullptr;
   long long solves = 0;          // solves queued since the batch was made
   int last_slot = -1;
   std::vector<double *> pending_drift;  // caller's drift arrays since the last wait
@@ -1420,6 +1421,10 @@ static void batch_free(lbm_batch_ctx *b) {
   dev_free(b->sbad);
   dev_free(b->ioblk);
   dev_free(b->poff_dev);
+  dev_free(b->smax);
+  dev_free(b->sfloor);
+  dev_free(b->sscale);
+  dev_free(b->sent);
   if (b->io) {
     cudaStreamSynchronize(b->io);
     cudaStreamDestroy(b->io);
@@ -1522,7 +1527,7 @@ static int batch_init_common(lbm_batch_ctx *b, const std::vector<size_t> &ends, 
       if (b->members[j]->L.dtype == LBM_F16DEV) {
         float mx;
         memcpy(&mx, &bits[j], sizeof(mx));
-        set_qscale(b->members[j], (double)mx);
+        set_qscale(b->members[j], std::max((double)mx, source_maxdev(b->members[j])));
       }
     rc = batch_refresh_params(b);
     if (rc != LBM_OK) return rc;
@@ -2005,6 +2010,31 @@ static int ensure_solve(lbm_batch_ctx *b) {
   CK(cudaMemcpyAsync(b->poff_dev, po.data(), po.size() * sizeof(long long),
                      cudaMemcpyHostToDevice, b->stream));
   CK(cudaMemsetAsync(b->sbad, 0, 2 * nm * sizeof(unsigned int), b->stream));
+  // FP16 members: their scale tables (entry pointers into the groups'
+  // device entry arrays; a point source's amplitude as the floor)
+  std::vector<BatchEntry *> ent(nm, nullptr);
+  std::vector<double> floor_(nm, 0.0);
+  for (size_t k = 0; k < nm; ++k) {
+    auto *m = b->members[k];
+    if (m->L.dtype != LBM_F16DEV) continue;
+    b->has16 = true;
+    ent[k] = b->groups[b->member_group[k]].ents + b->member_local[k];
+    floor_[k] = source_maxdev(m);
+  }
+  if (b->has16) {
+    b->smax = (unsigned int *)dev_alloc(nm * sizeof(unsigned int));
+    b->sfloor = (double *)dev_alloc(nm * sizeof(double));
+    b->sscale = (double *)dev_alloc(nm * sizeof(double));
+    b->sent = (BatchEntry **)dev_alloc(nm * sizeof(BatchEntry *));
+    if (!b->smax || !b->sfloor || !b->sscale || !b->sent) {
+      set_error("out of device memory for the FP16 scale tables");
+      return LBM_ENOMEM;
+    }
+    CK(cudaMemcpyAsync(b->sfloor, floor_.data(), nm * sizeof(double), cudaMemcpyHostToDevice,
+                       b->stream));
+    CK(cudaMemcpyAsync(b->sent, ent.data(), nm * sizeof(BatchEntry *), cudaMemcpyHostToDevice,
+                       b->stream));
+  }
   CK(cudaStreamSynchronize(b->stream));
   cudaStream_t up = nullptr, down = nullptr;
   CK(cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking));
@@ -2027,10 +2057,6 @@ int lbm_batch_solve_packed(lbm_batch b, long n, const double *rho_in, const doub
           "null argument");
   REQUIRE(n >= 0, "negative step count");
   REQUIRE(!b->spent, "batch ran a ragged generation; create a new batch");
-  for (auto *m : b->members)
-    REQUIRE(m->L.dtype != LBM_F16DEV,
-            "pipelined solves take FP32 and BF16 members (an FP16 member's storage scale is "
-            "chosen on the host from its fields: use lbm_batch_init_packed)");
   DevGuard g(b->device);
   int rc = ensure_solve(b);
   if (rc != LBM_OK) return rc;
@@ -2049,9 +2075,14 @@ int lbm_batch_solve_packed(lbm_batch b, long n, const double *rho_in, const doub
     CK(cudaMemcpyAsync(sl.in + c * T, src[c], T * sizeof(double), cudaMemcpyHostToDevice,
                        b->up));
   CK(cudaEventRecord(ev[B::E_UP1], b->up));
-  // equilibrium init of every member from the staged fields
+  // equilibrium init of every member from the staged fields (FP16 members
+  // first choose their storage scale from them, on the device)
   CK(cudaStreamWaitEvent(b->stream, ev[B::E_UP1], 0));
   CK(cudaEventRecord(ev[B::E_B0], b->stream));
+  if (b->has16)
+    CK(launch_batch_fp16_scales(b->views[0], b->views[1], b->sent, b->ioblk, b->nioblk,
+                                b->poff_dev, (long long)T, sl.in, b->smax, b->sfloor, b->sscale,
+                                (int)nm, b->stream));
   CK(launch_batch_init_dev(b->views[b->parity], b->ioblk, b->nioblk, b->poff_dev, (long long)T,
                            sl.in, b->sbad, (int)nm, b->stream));
   CK(launch_add_u32(b->sbad + nm, b->sbad, (int)nm, b->stream));
@@ -2147,6 +2178,13 @@ int lbm_batch_wait(lbm_batch b, double *phase_ms) {
   }
   const size_t nm = b->members.size();
   int rc = LBM_OK;
+  if (b->has16 && b->solves > b->waited) {
+    // the host copies of the FP16 members' scales follow the last solve's
+    std::vector<double> sc(nm, 1.0);
+    CK(cudaMemcpy(sc.data(), b->sscale, nm * sizeof(double), cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < nm; ++k)
+      if (b->members[k]->L.dtype == LBM_F16DEV) set_scale(b->members[k], sc[k]);
+  }
   if (b->sbad) {
     std::vector<unsigned int> tot(nm, 0);
     CK(cudaMemcpy(tot.data(), b->sbad + nm, nm * sizeof(unsigned int), cudaMemcpyDeviceToHost));

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of liblbm.so.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 
 #include <string>
 
@@ -175,6 +176,20 @@ struct AuxView {
   double f0[9];       // base populations f^eq(rho0, j0) (deviation types)
   double scale;       // stored = f' * scale (FP16), 1 otherwise
 };
+// FP16 storage scale for a largest |f'| of maxabs (host and device alike):
+// 2^(14 - ceil(log2 maxabs)), clamped to 2^-100 .. 2^100, so stored values
+// stay near 2^14 -- 11-bit mantissas with 4x headroom below the largest
+// finite FP16 and no subnormals down to 2^-10 of the largest; 1 for a zero
+// or non-finite maxabs
+__host__ __device__ inline double fp16_scale(double maxabs) {
+  if (!(maxabs > 0.0) || isinf(maxabs)) return 1.0;
+  int e = 0;
+  const double f = frexp(maxabs, &e);  // maxabs = f 2^e, f in [0.5, 1)
+  int k = 14 - (f == 0.5 ? e - 1 : e);  // 14 - ceil(log2 maxabs)
+  k = k < -100 ? -100 : (k > 100 ? 100 : k);
+  return ldexp(1.0, k);
+}
+
 cudaError_t launch_init_eq(const AuxView &a, const double *rho, const double *ux,
                            const double *uy, int analytic_kind, const double *params,
                            cudaStream_t st, unsigned int *bad = nullptr);
@@ -199,6 +214,16 @@ struct IoBlock {
   long long start;
 };
 constexpr int kIoBlockNodes = 1024;
+// FP16 members of a pipelined solve: the largest |f'| of each member's
+// equilibrium from the staged fields (max_bits: float bits, zeroed first),
+// then each member's storage scale (fp16_scale of that, or of floor[k] if
+// larger) written into both drift/I-O views, the member's batch entry
+// (ent[k]) and scale_out[k]
+cudaError_t launch_batch_fp16_scales(AuxView *views0, AuxView *views1, BatchEntry *const *ent,
+                                     const IoBlock *blocks, long long nblocks,
+                                     const long long *poff, long long total, const double *stage,
+                                     unsigned int *max_bits, const double *floor_,
+                                     double *scale_out, int members, cudaStream_t st);
 cudaError_t launch_batch_init_dev(const AuxView *views, const IoBlock *blocks, long long nblocks,
                                   const long long *poff, long long total, const double *stage,
                                   unsigned int *bad, int members, cudaStream_t st);

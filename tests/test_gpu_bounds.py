@@ -9,7 +9,7 @@ small cases of every checked kernel -- the von Neumann sweep, the optimizer
 cost (orders 3 - 6, both kinds), batched steps in every launch variant with
 mixed storage types (plain and persistent grids, the small members held in
 shared memory, ragged step counts through the server), the pipelined
-solve's batched init and moments -- and the
+solve's batched FP16 scales, init and moments -- and the
 word must stay zero; the self-test (one checked access past its bound) must
 set its bit, which shows the checks are live.
 """
@@ -86,7 +86,8 @@ out["served_all"] = not left
 # pipelined solves: the batched init and moments kernels
 specs = inp.batch_specs(7, seed=6, amin=20 * 20, amax=200 * 200)
 hs = [L.lbm_create(sp["nx"], sp["ny"], inp.s_ll(sp["rates"]), 1.0, (0.0, 0.0),
-                   (L.LBM_F32DEV, L.LBM_BF16DEV)[k % 2]) for k, sp in enumerate(specs)]
+                   (L.LBM_F32DEV, L.LBM_BF16DEV, L.LBM_F16DEV)[k % 3])
+      for k, sp in enumerate(specs)]
 b = L.lbm_batch_create(hs)
 tot = L.lbm_batch_size(b)[1]
 fin = [np.concatenate([f[c].ravel() for f in (inp.batch_fields(sp) for sp in specs)])
