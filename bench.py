@@ -311,6 +311,13 @@ def bench_batched(args, L, torch, rank, ws):
     resident = L.lbm_batch_resident(b)
     res_nodes = sum(s["nx"] * s["ny"] for s, r in zip(specs, resident) if r)
     step_nodes = nodes - res_nodes  # the per-step kernel's lattice updates
+    # one resident launch per non-empty size class (up to a third, a half,
+    # all of a block's shared memory) per call
+    optin = torch.cuda.get_device_properties(dev).shared_memory_per_block_optin
+    esize = {"f32": 4, "f16": 2, "bf16": 2}[bdt]
+    res_classes = len({0 if rb <= optin // 3 else (1 if rb <= optin // 2 else 2)
+                       for rb in (2 * 9 * s["nx"] * s["ny"] * esize
+                                  for s, r in zip(specs, resident) if r)})
 
     def one_step():
         L.lbm_batch_step(b, lbm_steps)
@@ -343,9 +350,8 @@ def bench_batched(args, L, torch, rank, ws):
     lu_job = reduce_sum(lu_per_step * args.steps)  # every rank's lattice updates
     value = job_mlups(lu_job, total_ms * 1e-3)
     launch_ms = float(np.mean(step_ms)) / lbm_steps  # one batched kernel per time step
-    # batched steps, the resident launch (one per storage type) and one
-    # drift launch pair
-    launches = args.steps * (lbm_steps + 2 + (1 if resident.any() else 0))
+    # batched steps, the resident launches and one drift launch pair
+    launches = args.steps * (lbm_steps + 2 + res_classes)
 
     # e2e: host fields in, moments out, through the public API: one
     # lbm_batch_solve_packed call per benchmark step (upload of the fields
