@@ -295,6 +295,41 @@ def fp64_plain(L, torch, stream, n=8192, steps=20, dtype=None):
     return n * n * steps / (ms * 1e-3) / 1e6, ms / steps
 
 
+_HOST_ARRAYS = {}
+
+
+def host_arrays(kind, n):
+    """Three page-locked huge-page host arrays of n doubles (lbm_host_alloc),
+    kept for the rest of the process."""
+    from paper_1107_4543_gb300 import lbm as L
+
+    key = (kind, n)
+    if key not in _HOST_ARRAYS:
+        _HOST_ARRAYS[key] = tuple(L.host_array(n) for _ in range(3))
+    return _HOST_ARRAYS[key]
+
+
+def huge_page_share(arrays):
+    """Share of the arrays' bytes that the kernel backs with transparent huge
+    pages (from /proc/self/smaps; None where that cannot be read)."""
+    try:
+        spans = [(a.ctypes.data, a.ctypes.data + a.nbytes) for a in arrays]
+        huge = total = 0
+        cur = None
+        with open("/proc/self/smaps") as fh:
+            for line in fh:
+                head = line.split()[0]
+                if "-" in head and not head.endswith(":"):
+                    lo, hi = (int(x, 16) for x in head.split("-"))
+                    cur = (lo, hi) if any(lo < e and s < hi for s, e in spans) else None
+                elif cur and line.startswith("AnonHugePages:"):
+                    huge += int(line.split()[1]) * 1024
+                    total += cur[1] - cur[0]
+        return round(huge / total, 3) if total else None
+    except OSError:
+        return None
+
+
 def bench_batched(args, L, torch, rank, ws):
     dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream()
@@ -360,16 +395,14 @@ def bench_batched(args, L, torch, rank, ws):
     # solve's copies overlap its neighbours' stepping; lbm_batch_wait ends
     # the timed region and reports the device time per phase (median over
     # the timed solves)
-    def pinned_flat():
-        # page-locked host memory on huge pages (lbm_host_alloc): copies from
-        # ordinary page-locked memory slowed to 17 - 80 GB/s on a host that
-        # had run for a while
-        return L.host_array(nodes)
-
-    fin = tuple(pinned_flat() for _ in range(3))
+    # page-locked host memory on huge pages (lbm_host_alloc; copies from
+    # ordinary page-locked memory slowed to 17 - 80 GB/s on a host that had
+    # run for a while), allocated once per process and shared by the
+    # workloads of equal size
+    fin = host_arrays("in", nodes)
     for c in range(3):
         np.concatenate([f[c].ravel() for f in fields], out=fin[c])
-    fout = tuple(pinned_flat() for _ in range(3))
+    fout = host_arrays("out", nodes)
     dout = np.zeros((len(hs), 4))
 
     def e2e_solve():
@@ -458,7 +491,9 @@ def bench_batched(args, L, torch, rank, ws):
                 # solves' steps)
                 "phases_ms": {k: round(phases[k], 3) for k in L.BATCH_PHASES},
                 "h2d_gbs": round(h2d / max(phases["h2d_ms"], 1e-9) / 1e6, 1),
-                "d2h_gbs": round(d2h / max(phases["d2h_ms"], 1e-9) / 1e6, 1)},
+                "d2h_gbs": round(d2h / max(phases["d2h_ms"], 1e-9) / 1e6, 1),
+                "host_huge_page_share": {"in": huge_page_share(fin),
+                                         "out": huge_page_share(fout)}},
         "roofline": roofline,
         "fp64_plain": fp64,
         "gpu_launches": launches,
