@@ -335,8 +335,12 @@ def bench_batched(args, L, torch, rank, ws):
     stream = torch.cuda.current_stream()
     specs = rank_specs(args, rank)
     bdt = args.batch_dtype
-    hs, fields = setup_batch(L, torch, specs, bdt, stream)
     nodes = sum(s["nx"] * s["ny"] for s in specs)
+    # the end-to-end host arrays first, before other host allocations can
+    # break up the memory their huge pages need
+    host_arrays("in", nodes)
+    host_arrays("out", nodes)
+    hs, fields = setup_batch(L, torch, specs, bdt, stream)
     b = L.lbm_batch_create(hs)
     if args.batch_variant >= 0:
         L.lbm_batch_set_variant(b, args.batch_variant)

@@ -581,6 +581,13 @@ void *lbm_host_alloc(size_t bytes) {
     madvise(p, len, MADV_HUGEPAGE);  // a hint: ordinary pages where it is refused
   }
   memset(p, 0, len);  // fault the pages in before they are registered
+#ifdef MADV_COLLAPSE
+  // where faults fell back to base pages, collapse them into huge pages
+  // now (Linux 6.1 and later; a refusal leaves the base pages)
+  if (unit > page) madvise(p, len, MADV_COLLAPSE);
+#else
+  if (unit > page) madvise(p, len, 25);  // MADV_COLLAPSE, as above
+#endif
   if (cudaHostRegister(p, len, cudaHostRegisterDefault) != cudaSuccess) {
     cudaGetLastError();
     munmap(p, len);
