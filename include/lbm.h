@@ -358,7 +358,9 @@ int lbm_opt_minimize(const lbm_cost_spec *spec, const double sigmas_in[4],
  * kernel launch per storage type over a work list of all members (each
  * lattice starts on a block boundary; one record per block gives its
  * lattice, geometry and buffers), and chunks of 64 steps are replayed from a
- * captured CUDA graph.  Members must be deviation-storage lattices
+ * captured CUDA graph; members small enough for one block's shared memory
+ * are instead held there for all the steps of a call (lbm_batch_resident),
+ * with the same arithmetic.  Members must be deviation-storage lattices
  * (LBM_F32DEV, LBM_F16DEV or LBM_BF16DEV) created on the current device,
  * none of them in another batch; they keep their own memory, rates and
  * reference state, and each advances with exactly the arithmetic of
