@@ -2,9 +2,9 @@
 // steps of one launch (section 2.1, Eq. blbs, as the per-step kernels): one
 // thread block per member loads the member's nine planes into shared memory,
 // runs its n steps there (pull with periodic wrap, collide, store into the
-// other buffer, block barrier, swap) and writes the result back once.  A
-// member of nx x ny nodes moves 2 x 9 x nx ny elements through HBM for the
-// whole launch instead of per step.
+// other buffer, block barrier, swap) and writes the result back once: its
+// 9 x nx ny elements cross HBM once in and once out for the whole launch
+// instead of in and out at every step.
 //
 // The arithmetic is the per-step kernels' own (collide_dev for FP32,
 // collide_pair for the 16-bit types, the same storage rounding), node by
