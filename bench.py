@@ -213,11 +213,38 @@ def traffic_record(kernel):
     return rec
 
 
+def code_of(text):
+    """C++ source with its comments and blank space removed (string
+    literals kept), so that a comment edit does not count as a kernel
+    change."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if text.startswith("//", i):
+            i = text.find("\n", i)
+            i = n if i < 0 else i
+        elif text.startswith("/*", i):
+            i = text.find("*/", i + 2)
+            i = n if i < 0 else i + 2
+        elif c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def sources_sha():
+    """Hash of the step kernels' code (comments and spacing ignored): a
+    traffic record taken at other code is not reported."""
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1107_4543_gb300", rel), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1107_4543_gb300", rel), encoding="utf-8") as fh:
+            h.update(code_of(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -46,3 +46,13 @@ def test_traffic_record_is_plausible():
         assert r["dram_bytes_per_lu"] == pytest.approx(
             r["dram_read_bytes_per_lu"] + r["dram_write_bytes_per_lu"], abs=0.02), kernel
         assert len(r["source_sha"]) == 16
+
+
+def test_kernel_hash_ignores_comments_only():
+    """bench.sources_sha hashes the step kernels' code without comments and
+    spacing: a comment edit keeps a traffic record, a code edit drops it."""
+    a = 'x = y + 1; // note\n/* block */ s = "//kept";  z = \'"\';\n'
+    b = 'x = y + 1;   // another note\ns = "//kept"; z = \'"\';'
+    c = 'x = y + 2; s = "//kept"; z = \'"\';'
+    assert bench.code_of(a) == bench.code_of(b) != bench.code_of(c)
+    assert '"//kept"' in bench.code_of(a)
