@@ -12,6 +12,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <unordered_set>
 #include <new>
 #include <string>
 #include <vector>
@@ -1647,13 +1648,18 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
   b->stream = members[0]->stream;
   for (int k = 0; k < n; ++k) b->members.push_back(members[k]);
   // the batch runs on the first member's stream: finish what the members
-  // queued elsewhere, then route their later work to the batch stream
-  for (auto *m : b->members) {
-    if (cudaStreamSynchronize(m->stream) != cudaSuccess) {
-      set_error("member stream failed");
-      cudaGetLastError();
-      batch_free(b);
-      return LBM_ECUDA;
+  // queued elsewhere (each distinct stream once: a server's members share
+  // one), then route their later work to the batch stream
+  {
+    std::unordered_set<cudaStream_t> done;
+    for (auto *m : b->members) {
+      if (!done.insert(m->stream).second) continue;
+      if (cudaStreamSynchronize(m->stream) != cudaSuccess) {
+        set_error("member stream failed");
+        cudaGetLastError();
+        batch_free(b);
+        return LBM_ECUDA;
+      }
     }
   }
   for (auto *m : b->members) {
