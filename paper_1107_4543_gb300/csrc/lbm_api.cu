@@ -1677,6 +1677,12 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
     std::vector<int> res_cls[3];  // resident entries by size class
     size_t res_smem[3] = {0, 0, 0};
     long long t0 = 0;
+    {
+      size_t nb = 0;  // an upper bound of the records (a server builds ~10^5 per generation)
+      for (auto *m : b->members)
+        if (m->L.dtype == dt) nb += (size_t)((m->L.g.tasks + wpb - 1) / wpb);
+      bl.reserve(nb);
+    }
     for (size_t mi = 0; mi < b->members.size(); ++mi) {
       auto *m = b->members[mi];
       if (m->L.dtype != dt) continue;
