@@ -19,6 +19,7 @@ COMMON = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                  "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr"]
 UNITS = {
     "lbm_api.cu": [],
+    "batch.cu": [],
     "step_f32.cu": [],
     "step_f16.cu": [],
     "step_bf16.cu": [],
@@ -33,7 +34,7 @@ UNITS = {
     "optcost.cu": [],
 }
 HEADERS = ["lbm_internal.h", "d2q9_pull.cuh", "collide.cuh", "step_impl.cuh", "bounds.cuh",
-           "resident.cuh"]
+           "resident.cuh", "runtime.h"]
 # the debug build: device-side index checks that record failures in a word
 # (lbm_debug_bounds) instead of trapping
 OUT_DEBUG = os.path.join(HERE, "_build_debug")

@@ -259,7 +259,7 @@ cudaError_t launch_batch_drift(const AuxView *views_dev, int n, double *partials
 // base populations f^eq(rho0, j0) on the host, in the canonical FP64 order
 void host_feq_j(double rho, double jx, double jy, double out[9]);
 
-// batch launch-variant control (lbm_api.cu), for the server
+// batch launch-variant control (batch.cu), for the server
 void batch_pin_variant(lbm_batch_ctx *b, int variant);
 // One generation of a server batch: member k advances min(steps[k], n)
 // steps (n launches; a member's warps return once it is done).  The batch
