@@ -192,27 +192,50 @@ def test_dev_config1_pulse(L, dtype):
 
 # Random populations are a stress case, not a workload: each direction
 # carries an independent deviation as large as the density fluctuation A
-# itself, and each step rounds every stored deviation once.  BF16 keeps 9
-# significant bits (unit roundoff u = 2^-9 ~ 2e-3), so after n steps the
-# error is bounded by about sqrt(n) u sum_i |f'_i| / A ~ 1e-2 for n = 17;
-# the 2e-3 acoustic tolerance is held on the pulse workloads instead.
-RANDOM_TOL = {"f32": 1e-6, "f16": 2e-3, "bf16": 1e-2}
+# itself, and each step rounds every stored deviation once.  The stated
+# bars hold for FP32 and FP16; BF16 keeps 9 significant bits (one rounding
+# is up to 2^-9 = 1.95e-3 of a stored population) and misses 2e-3 here.
+RANDOM_TOL = {"f32": 1e-6, "f16": 2e-3, "bf16": 2e-3}
+BF16_RANDOM_MISS = pytest.mark.xfail(
+    strict=True,
+    reason="BF16 storage misses the stated 2e-3 bar on random non-equilibrium populations "
+           "(measured 3.2e-3 - 4.3e-3 of A after 17 steps): every direction carries a "
+           "deviation as large as A, and one BF16 rounding is up to 2^-9 of a stored population")
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
-@pytest.mark.parametrize("nx,ny", [(5, 3), (33, 17), (130, 7), (96, 40)])
-def test_dev_random_populations_ragged(L, dtype, nx, ny):
+def random_case(L, dtype, nx, ny):
     amp, steps = 1e-3, 17
     r = inp.rates("OPT")
     pops = inp.random_populations(nx, ny, seed=nx + 7 * ny, amp=amp)
     (rho, ux, uy), f = run_gpu(L, nx, ny, r, steps, L.DTYPES[dtype], pops=pops)
     (rho_o, ux_o, uy_o), f_o = run_orc(r, steps, pops=pops)
     A = np.max(np.abs(pops.sum(axis=0) - 1.0))
+    errs = (max_rel(rho, rho_o, A), max_rel(f, f_o, A), max_rel(ux, ux_o, A))
+    return pops, A, steps, errs
+
+
+@pytest.mark.parametrize("dtype", [pytest.param("bf16", marks=BF16_RANDOM_MISS), "f16", "f32"])
+@pytest.mark.parametrize("nx,ny", [(5, 3), (33, 17), (130, 7), (96, 40)])
+def test_dev_random_populations_ragged(L, dtype, nx, ny):
+    _, _, _, errs = random_case(L, dtype, nx, ny)
     print("\n%s random populations %dx%d: max|drho'|/A = %.2e, max|df|/A = %.2e"
-          % (dtype, nx, ny, max_rel(rho, rho_o, A), max_rel(f, f_o, A)))
-    assert max_rel(rho, rho_o, A) <= RANDOM_TOL[dtype]
-    assert max_rel(f, f_o, A) <= RANDOM_TOL[dtype]
-    assert max_rel(ux, ux_o, A) <= RANDOM_TOL[dtype]
+          % (dtype, nx, ny, errs[0], errs[1]))
+    assert max(errs) <= RANDOM_TOL[dtype]
+
+
+@pytest.mark.parametrize("nx,ny", [(5, 3), (33, 17), (130, 7), (96, 40)])
+def test_bf16_random_populations_within_rounding_bound(L, nx, ny):
+    """Not the acceptance bar (that is missed, above) but the BF16 rounding
+    model: after n steps of one rounding per stored deviation (relative
+    2^-9 at most) the error stays below sqrt(n) 2^-9 max_node sum_i |f'_i|,
+    the random-walk growth of the per-step roundings (~1e-2 of A here)."""
+    pops, A, steps, errs = random_case(L, "bf16", nx, ny)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4).reshape(9, 1, 1)  # f^eq(1, 0)
+    dev = np.abs(pops - w).sum(axis=0).max() / A
+    bound = math.sqrt(steps) * 2.0 ** -9 * dev
+    print("\nbf16 random populations %dx%d: %.2e of A against the rounding bound %.2e"
+          % (nx, ny, max(errs), bound))
+    assert max(errs) <= bound
 
 
 # Over the 2000 steps of config 2 the FP32 storage rounding of every step
