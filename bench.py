@@ -326,13 +326,15 @@ _HOST_ARRAYS = {}
 
 
 def host_arrays(kind, n):
-    """Three page-locked huge-page host arrays of n doubles (lbm_host_alloc),
-    kept for the rest of the process."""
+    """Three page-locked huge-page host arrays of n doubles, slices of one
+    lbm_host_alloc array (one allocation fills whole huge pages with less
+    padding than three), kept for the rest of the process."""
     from paper_1107_4543_gb300 import lbm as L
 
     key = (kind, n)
     if key not in _HOST_ARRAYS:
-        _HOST_ARRAYS[key] = tuple(L.host_array(n) for _ in range(3))
+        whole = L.host_array(3 * n)
+        _HOST_ARRAYS[key] = tuple(whole[c * n:(c + 1) * n] for c in range(3))
     return _HOST_ARRAYS[key]
 
 
