@@ -333,8 +333,9 @@ def host_arrays(kind, n):
 
     key = (kind, n)
     if key not in _HOST_ARRAYS:
-        whole = L.host_array(3 * n)
-        _HOST_ARRAYS[key] = tuple(whole[c * n:(c + 1) * n] for c in range(3))
+        stride = (n + 511) // 512 * 512  # each field on a 4 KiB boundary
+        whole = L.host_array(3 * stride)
+        _HOST_ARRAYS[key] = tuple(whole[c * stride:c * stride + n] for c in range(3))
     return _HOST_ARRAYS[key]
 
 
