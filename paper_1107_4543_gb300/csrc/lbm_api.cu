@@ -460,10 +460,10 @@ int lbm_debug_bounds_selftest(void) {
 
 // ------------------------------------------------------------ host memory
 // Page-locked host arrays on transparent huge pages (lbm_host_alloc): the
-// copy engines translate each page of a transfer, and on the GB300 machines
-// (64 KiB base pages, 512 MiB huge pages) copies from ordinary page-locked
-// memory fell from ~210 to 17 - 80 GB/s once the host had run for a while,
-// while a huge-page mapping kept 192 - 211 GB/s.
+// copy engines translate each page of a transfer, and on a GB300 host with
+// 64 KiB base pages and 512 MiB huge pages, copies from ordinary
+// page-locked memory fell from ~210 to 17 - 80 GB/s once the host had run
+// for a while, while a huge-page mapping kept 192 - 211 GB/s.
 static std::mutex g_host_mu;
 struct HostMap {
   void *base;
