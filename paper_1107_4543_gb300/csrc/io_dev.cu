@@ -152,7 +152,9 @@ __global__ void __launch_bounds__(256) k_maxdev_dev(AuxView a, RefState R, const
 #pragma unroll
     for (int i = 0; i < 9; ++i) m = fmaxf(m, (float)fabs(d[i]));
   }
-  atomicMax(max_bits, __float_as_uint(m));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(max_bits, __float_as_uint(m));
 }
 
 // rho = rho0 + sum f', j = j0 + sum c f' of the pre-collision populations
@@ -301,9 +303,16 @@ __global__ void __launch_bounds__(256) k_batch_maxdev_fp16(const AuxView *__rest
 #pragma unroll
     for (int i = 0; i < 9; ++i) m = fmaxf(m, (float)fabs(d[i]));
   }
+  // one atomic per block (a member's blocks all update the same word)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(max_bits + B.member, __float_as_uint(m));
+  __shared__ float wmax[8];
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmax[w]);
+    atomicMax(max_bits + B.member, __float_as_uint(m));
+  }
 }
 
 __global__ void k_batch_set_scales(AuxView *views0, AuxView *views1, BatchEntry *const *ent,
