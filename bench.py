@@ -1002,7 +1002,7 @@ def main():
     if rank == 0 and ws == 1 and not args.no_extras:
         # the other workloads at their stated sizes, as extra keys of the one
         # line: the batch in FP16 deviation storage, config 3 per storage
-        # type, config 5 serving
+        # type, a sweep of small lattices, config 5 serving
         sub = parse(["--batch-dtype", "f16", "--steps", str(max(3, min(args.steps, 5))),
                      "--warmup", "3", "--no-fp64"])
         f16, _ = bench_batched(sub, L, torch, rank, ws)
@@ -1010,6 +1010,10 @@ def main():
                                                   "e2e", "clocks")}
         line["batch_fp16"]["workload"] = f16["config"]["workload"]
         line["config3_large"] = config3_record(L, torch)
+        # small lattices held in shared memory for all the steps of a call,
+        # against per-step launches of the same sweep
+        line["small_sweep"] = bench_small(parse(["--workload", "small", "--lattices", "4096",
+                                                 "--steps", "3"]), L, torch)
         srv = parse(["--workload", "serving", "--policy", "shortest",
                      "--max-nodes", str(1 << 27), "--requests", str(args.requests)])
         line["config5_serving"] = bench_serving(srv, L, torch)
