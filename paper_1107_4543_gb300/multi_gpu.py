@@ -112,7 +112,8 @@ class SlabRank:
     The halo buffers are CUDA tensors on this rank's device; the pack is
     waited for before the transport starts and the transport before the
     unpack (host synchronisation on both sides, whatever streams the
-    transport uses)."""
+    transport uses).  With a process group whose backend moves host tensors
+    only (gloo), the outgoing parts are staged through host memory."""
 
     def __init__(self, L, nx, ny, S, rank, world, rho0=1.0, u0=(0.0, 0.0), dtype=None):
         import torch
@@ -125,6 +126,12 @@ class SlabRank:
         nb = L.lbm_slab_halo_bytes(self.h)
         dev = torch.cuda.current_device()
         self.buf = [torch.empty(nb, dtype=torch.uint8, device=dev) for _ in range(4)]
+        self.host = None
+        if world > 1:
+            import torch.distributed as dist
+
+            if dist.get_backend() != "nccl":
+                self.host = [torch.empty(nb, dtype=torch.uint8) for _ in range(4)]
 
     def _exchange(self, reverse):
         import torch
@@ -132,7 +139,15 @@ class SlabRank:
         tb, ta, fb, fa = self.buf
         self.L.lbm_slab_pack(self.h, reverse, tb, ta)
         self.L.lbm_sync(self.h)
-        exchange(tb, ta, fb, fa, self.rank, self.world)
+        if self.host is None:
+            exchange(tb, ta, fb, fa, self.rank, self.world)
+        else:
+            htb, hta, hfb, hfa = self.host
+            htb.copy_(tb)
+            hta.copy_(ta)
+            exchange(htb, hta, hfb, hfa, self.rank, self.world)
+            fb.copy_(hfb)
+            fa.copy_(hfa)
         torch.cuda.synchronize()
         self.L.lbm_slab_unpack(self.h, reverse, fb, fa)
 

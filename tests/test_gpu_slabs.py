@@ -3,11 +3,12 @@
 Slabs run the same node arithmetic on the same inputs as the unsplit
 lattice, so every check here is bit for bit: the in-process slab group
 (lbm_slabs_*, halo copies overlapped with the interior rows) and the
-one-slab-per-process calls (lbm_slab_pack / unpack, here with the transport
-done by plain device copies between the slabs of one process, and through
-multi_gpu.SlabRank with a single rank) against lbm_create on the whole
-lattice, for FP64, FP32 and BF16 storage, ragged sizes, one-row slabs and a
-single slab; FP64 also against the oracle.
+one-slab-per-process calls (lbm_slab_pack / unpack: with the transport done
+by plain device copies between the slabs of one process, through
+multi_gpu.SlabRank with one rank, and through SlabRank in two or three
+processes on the one GPU exchanging over gloo) against lbm_create on the
+whole lattice, for FP64, FP32 and BF16 storage, ragged sizes, one-row slabs
+and a single slab; FP64 also against the oracle.
 """
 import os
 
@@ -18,6 +19,7 @@ import lbm_inputs as inp
 import oracle as orc
 
 pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -174,3 +176,79 @@ def test_slabs_reject_fp16_and_bad_splits(L):
         L.lbm_slabs_create(16, 3, S, 1.0, (0.0, 0.0), L.LBM_F32DEV, 4)
     with pytest.raises(L.LbmError):
         L.lbm_slab_create(16, 16, 10, 8, S)
+
+
+def _slab_rank_worker(rank, world, port, out_dir, nx, ny, steps):
+    """One rank of a lattice split over `world` processes on the one GPU,
+    its halo rows exchanged over gloo (host-staged): no kernel of one rank
+    waits on another's."""
+    import datetime
+    import sys
+
+    import torch
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=120))
+    try:
+        from paper_1107_4543_gb300 import lbm
+        from paper_1107_4543_gb300 import multi_gpu as mg
+
+        lbm.load()
+        torch.cuda.set_device(0)
+        fields = inp.gaussian_pulse(nx, ny, 1e-3, 3.0, u0=(0.05, -0.02))
+        sr = mg.SlabRank(lbm, nx, ny, inp.s_ll(inp.rates("OPT")), rank, world, u0=(0.05, -0.02))
+        try:
+            assert sr.host is not None  # gloo: staged through host memory
+            sr.init_field(*fields)
+            sr.step(steps)
+            rho, ux, uy = sr.moments()
+            np.savez(os.path.join(out_dir, "rank%d.npz" % rank), y0=sr.y0, rho=rho, ux=ux, uy=uy)
+        finally:
+            sr.close()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_slab_ranks_over_gloo_on_one_gpu(L, tmp_path, world):
+    """multi_gpu.SlabRank across `world` processes (one slab each, halo rows
+    exchanged through torch.distributed, here gloo with host staging, all on
+    the one GPU) equals the unsplit lattice bit for bit; with two ranks both
+    neighbours of a rank are the same rank, which the exchange's message
+    order has to keep apart."""
+    pytest.importorskip("torch")
+    import socket
+
+    import torch.multiprocessing as mp
+
+    nx, ny, steps = 48, 21, 13
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_slab_rank_worker,
+                         args=(k, world, port, str(tmp_path), nx, ny, steps))
+             for k in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+    for p in procs:
+        if p.is_alive():
+            p.kill()
+            p.join()
+    assert [p.exitcode for p in procs] == [0] * world
+    u0 = (0.05, -0.02)
+    fields = inp.gaussian_pulse(nx, ny, 1e-3, 3.0, u0=u0)
+    want = unsplit(L, nx, ny, inp.rates("OPT"), "f32", steps, fields=fields, u0=u0)[1]
+    got = [np.full((ny, nx), np.nan) for _ in range(3)]
+    for k in range(world):
+        z = np.load(os.path.join(str(tmp_path), "rank%d.npz" % k))
+        y0 = int(z["y0"])
+        for c, key in enumerate(("rho", "ux", "uy")):
+            got[c][y0:y0 + z[key].shape[0]] = z[key]
+    for a, b in zip(got, want):
+        assert np.array_equal(a, b)
