@@ -21,6 +21,40 @@
 
 using namespace lbm;
 
+// ------------------------------------------------------------ constant slots
+// Slots of the 16-bit batched step's constant tables (kPairSlots per storage
+// type and device, step_impl.cuh): a batch group holds one contiguous range
+// from its creation to its destruction; a group that finds no room (or runs
+// with LBM_CONST_TABLE=0) reads its entries' parameters instead.
+namespace {
+std::mutex g_slot_mu;
+std::map<std::pair<int, int>, std::vector<char>> g_slot_used;  // (device, dtype) -> slot taken
+
+int slots_reserve(int dev, int dtype, int n) {
+  const char *env = getenv("LBM_CONST_TABLE");
+  if (env != nullptr && strcmp(env, "0") == 0) return -1;
+  if (n < 1 || n > kPairSlots) return -1;
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  auto &used = g_slot_used[{dev, dtype}];
+  if (used.empty()) used.assign(kPairSlots, 0);
+  for (int s = 0, run = 0; s < kPairSlots; ++s) {
+    run = used[s] ? 0 : run + 1;
+    if (run == n) {
+      std::fill(used.begin() + (s - n + 1), used.begin() + (s + 1), 1);
+      return s - n + 1;
+    }
+  }
+  return -1;
+}
+
+void slots_release(int dev, int dtype, int base, int n) {
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  auto &used = g_slot_used[{dev, dtype}];
+  if (base < 0 || base + n > (int)used.size()) return;
+  std::fill(used.begin() + base, used.begin() + base + n, 0);
+}
+}  // namespace
+
 // ------------------------------------------------------------------ batch
 struct lbm_batch_ctx {
   std::vector<lbm_ctx *> members;
@@ -42,6 +76,10 @@ struct lbm_batch_ctx {
     int *res = nullptr;
     int res_count[3] = {0, 0, 0};
     size_t res_smem[3] = {0, 0, 0};  // shared memory of a block of the class
+    // 16-bit types: the group's slots in the constant table (-1: none) and
+    // the device staging of their refresh (n x PC_COUNT floats)
+    int pbase = -1;
+    float *pstage = nullptr;
   };
   std::vector<int> member_group, member_local;  // member -> (group, entry)
   std::vector<int> member_res;                  // member stepped as a resident entry
@@ -138,7 +176,18 @@ static BatchList batch_list(const lbm_batch_ctx::Group &gr) {
   bl.blocks = gr.blocks;
   bl.nblocks = gr.nblocks;
   bl.ntasks = gr.ntasks;
+  bl.pbase = gr.pbase;
   return bl;
+}
+
+// Refresh the groups' constant-table slots from their entries, in the
+// order of the batch stream: before any call steps, since the entries may
+// have changed (a member's FP16 scale, set on the host or by a solve).
+static int batch_upload_pairs(lbm_batch_ctx *b) {
+  for (auto &gr : b->groups)
+    if (gr.pbase >= 0)
+      CK(upload_batch_pairs(gr.dtype, gr.ents, gr.n, gr.pbase, gr.pstage, b->stream));
+  return LBM_OK;
 }
 
 // Launch the resident entries of every group for `steps` steps from batch
@@ -228,6 +277,8 @@ static std::string batch_key(const lbm_batch_ctx *b) {
 // As tune_handle, for the whole batch: trial launches at the current parity
 // write only the idle buffers.
 static int tune_batch(lbm_batch_ctx *b, double *times) {
+  int urc = batch_upload_pairs(b);
+  if (urc != LBM_OK) return urc;
   double bytes = 0;
   for (auto *m : b->members) bytes += (double)m->L.g.nx * m->L.g.ny * 18.0 * m->L.esize;
   const int reps = tune_reps(bytes);
@@ -302,8 +353,9 @@ int batch_step_ragged(lbm_batch_ctx *b, const long *steps, long n) {
   REQUIRE(!b->spent && b->parity == 0, "ragged steps need a fresh batch");
   REQUIRE(n <= 0x3fffffffL, "too many steps for one generation");
   DevGuard g(b->device);
-  if (n > 0 && !b->tuned) {
-    int rc = maybe_autotune_batch(b);
+  if (n > 0) {
+    int rc = batch_upload_pairs(b);
+    if (rc == LBM_OK && !b->tuned) rc = maybe_autotune_batch(b);
     if (rc != LBM_OK) return rc;
   }
   const size_t nm = b->members.size();
@@ -373,6 +425,8 @@ static void batch_free(lbm_batch_ctx *b) {
     dev_free(gr.blocks);
     dev_free(gr.limits);
     dev_free(gr.res);
+    dev_free(gr.pstage);
+    if (gr.pbase >= 0) slots_release(b->device, gr.dtype, gr.pbase, gr.n);
   }
   dev_free(b->views[0]);
   dev_free(b->views[1]);
@@ -665,6 +719,16 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
       gr.res = (int *)dev_alloc(sizeof(int) * res.size());
       b->resident = true;
     }
+    if (dt == LBM_F16DEV || dt == LBM_BF16DEV) {
+      gr.pbase = slots_reserve(b->device, dt, gr.n);
+      if (gr.pbase >= 0) {
+        gr.pstage = (float *)dev_alloc(sizeof(float) * PC_COUNT * (size_t)gr.n);
+        if (!gr.pstage) {
+          slots_release(b->device, dt, gr.pbase, gr.n);
+          gr.pbase = -1;
+        }
+      }
+    }
     b->groups.push_back(gr);
     if (!gr.ents || !gr.blocks || !gr.limits || (gr.nres > 0 && !gr.res)) {
       set_error("cannot allocate batch tables");
@@ -738,8 +802,9 @@ int lbm_batch_step(lbm_batch b, long n) {
   for (size_t k = 0; k < b->members.size(); ++k)
     REQUIRE(b->members[k]->L.cur == (b->offs[k] ^ b->parity),
             "a member was modified outside the batch");
-  if (n > 0 && !b->tuned) {
-    int rc = maybe_autotune_batch(b);
+  if (n > 0) {
+    int rc = batch_upload_pairs(b);
+    if (rc == LBM_OK && !b->tuned) rc = maybe_autotune_batch(b);
     if (rc != LBM_OK) return rc;
   }
   // resident members: all n steps in one launch per storage type, beside
@@ -1166,6 +1231,13 @@ int lbm_get_variant(lbm_handle h, int *variant) {
 int lbm_batch_resident(lbm_batch b, int *flags) {
   REQUIRE(b != nullptr && flags != nullptr, "null argument");
   for (size_t k = 0; k < b->members.size(); ++k) flags[k] = b->member_res[k];
+  return LBM_OK;
+}
+
+int lbm_batch_const_table(lbm_batch b, int *flags) {
+  REQUIRE(b != nullptr && flags != nullptr, "null argument");
+  for (size_t k = 0; k < b->members.size(); ++k)
+    flags[k] = b->groups[b->member_group[k]].pbase >= 0 ? 1 : 0;
   return LBM_OK;
 }
 

@@ -169,14 +169,50 @@ __device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {
   return r;
 }
 
+// The per-lattice constants collide_pair multiplies by, each broadcast to
+// both lanes of an F2; negations and doublings are folded in (exact in
+// FP32, so every source of them gives the same bits).
+enum PairConst {
+  PC_IS, PC_R0, PC_2JX, PC_2JY, PC_JX, PC_JY, PC_I2, PC_NQ0, PC_ND0, PC_NX0,
+  PC_K3, PC_K4, PC_NK5, PC_NK6, PC_K7, PC_K8, PC_COUNT
+};
+
+__host__ __device__ __forceinline__ float pair_const(const DevParams &P, int c) {
+  switch (c) {
+    case PC_IS: return P.inv_scale;
+    case PC_R0: return P.rho0;
+    case PC_2JX: return 2.0f * P.jx0;
+    case PC_2JY: return 2.0f * P.jy0;
+    case PC_JX: return P.jx0;
+    case PC_JY: return P.jy0;
+    case PC_I2: return P.i2h;
+    case PC_NQ0: return -P.q0h;
+    case PC_ND0: return -P.d0h;
+    case PC_NX0: return -P.x0h;
+    case PC_K3: return P.k3;
+    case PC_K4: return P.k4;
+    case PC_NK5: return -P.k5;
+    case PC_NK6: return -P.k6;
+    case PC_K7: return P.k7;
+    default: return P.k8;
+  }
+}
+
+// The constants straight from a DevParams (kernel parameters of a single
+// lattice, or an entry in global memory)
+struct ParamPairs {
+  const DevParams &P;
+  __device__ __forceinline__ F2 operator()(PairConst c) const { return f2s(pair_const(P, c)); }
+};
+
 // collide_dev<false, SCALED> for two nodes, one per lane of the F2 values:
 // the same formulation (partial sums, quadratic differences through
 // rho'/rho, hi parts of the constants), written with explicit multiply-adds.
 // Negations are folded into constants or operands where that is exact
 // (a sign flip never rounds), so no extra instruction carries them.
-template <bool SCALED>
+template <bool SCALED, typename K>
 __device__ __forceinline__ void collide_pair(F2 &f0, F2 &f1, F2 &f2_, F2 &f3, F2 &f4, F2 &f5,
-                                             F2 &f6, F2 &f7, F2 &f8, const DevParams &P) {
+                                             F2 &f6, F2 &f7, F2 &f8, const K &P) {
   const F2 s13 = f1 + f3, s24 = f2_ + f4;
   const F2 d13 = f1 - f3, d24 = f2_ - f4;
   const F2 s57 = f5 + f7, s68 = f6 + f8;
@@ -189,11 +225,11 @@ __device__ __forceinline__ void collide_pair(F2 &f0, F2 &f1, F2 &f2_, F2 &f3, F2
   const F2 jx_p = d13 + dxd;
   const F2 jy_p = d24 + dyd;
 
-  const F2 IS = f2s(P.inv_scale);
+  const F2 IS = P(PC_IS);
   const F2 rho_phys = SCALED ? rho_p * IS : rho_p;
   // -rho'/rho per lane by the hardware reciprocal (the sign folded into
   // the numerator, which is exact)
-  const F2 den = f2s(P.rho0) + rho_phys;
+  const F2 den = P(PC_R0) + rho_phys;
   float rl, rh, dl, dh;
   f2split(rho_phys, rl, rh);
   f2split(den, dl, dh);
@@ -204,13 +240,13 @@ __device__ __forceinline__ void collide_pair(F2 &f0, F2 &f1, F2 &f2_, F2 &f3, F2
     jyy = jyy * IS;
     jxy = jxy * IS;
   }
-  const F2 tx = fma2(f2s(2.0f * P.jx0), jx_p, jxx);  // jx^2 - jx0^2
-  const F2 ty = fma2(f2s(2.0f * P.jy0), jy_p, jyy);
-  const F2 txy = fma2(f2s(P.jx0), jy_p, fma2(jx_p, f2s(P.jy0), jxy));
-  const F2 R0 = f2s(P.rho0), I2 = f2s(P.i2h);
-  const F2 nj = fma2(R0, tx + ty, rho_p * f2s(-P.q0h)) * I2;
-  const F2 np = fma2(R0, tx - ty, rho_p * f2s(-P.d0h)) * I2;
-  const F2 nx = fma2(R0, txy, rho_p * f2s(-P.x0h)) * I2;
+  const F2 tx = fma2(P(PC_2JX), jx_p, jxx);  // jx^2 - jx0^2
+  const F2 ty = fma2(P(PC_2JY), jy_p, jyy);
+  const F2 txy = fma2(P(PC_JX), jy_p, fma2(jx_p, P(PC_JY), jxy));
+  const F2 R0 = P(PC_R0), I2 = P(PC_I2);
+  const F2 nj = fma2(R0, tx + ty, rho_p * P(PC_NQ0)) * I2;
+  const F2 np = fma2(R0, tx - ty, rho_p * P(PC_ND0)) * I2;
+  const F2 nx = fma2(R0, txy, rho_p * P(PC_NX0)) * I2;
   const F2 djsq = fma2(nj, nc, nj);  // |j|^2/rho - |j0|^2/rho0
   const F2 dpxx = fma2(np, nc, np);
   const F2 dpxy = fma2(nx, nc, nx);
@@ -222,12 +258,12 @@ __device__ __forceinline__ void collide_pair(F2 &f0, F2 &f1, F2 &f2_, F2 &f3, F2
   const F2 m6 = fma2(f2s(-2.0f), dyd, d24);
   const F2 n7 = (s13 - s24) - dpxx;
   const F2 n8 = (s57 - s68) - dpxy;
-  const F2 r3 = n3 * f2s(P.k3);
-  const F2 r4 = n4 * f2s(P.k4);
-  const F2 r5 = m5 * f2s(-P.k5);
-  const F2 r6 = m6 * f2s(-P.k6);
-  const F2 r7 = n7 * f2s(P.k7);
-  const F2 r8 = n8 * f2s(P.k8);
+  const F2 r3 = n3 * P(PC_K3);
+  const F2 r4 = n4 * P(PC_K4);
+  const F2 r5 = m5 * P(PC_NK5);
+  const F2 r6 = m6 * P(PC_NK6);
+  const F2 r7 = n7 * P(PC_K7);
+  const F2 r8 = n8 * P(PC_K8);
 
   const F2 TWO = f2s(2.0f), NTWO = f2s(-2.0f);
   const F2 a = fma2(TWO, r4, r3);  // axis velocities: -r3 - 2 r4

@@ -77,6 +77,7 @@ struct BlockRec {
 struct BatchList {
   const BatchEntry *ents;
   int n;
+  int pbase = -1;  // 16-bit types: first slot of the constant table, or -1 (entries)
   const BlockRec *blocks;  // the plain grid's blocks
   long long nblocks;       // sum over lattices of ceil(tasks / warps per block)
   long long ntasks;        // sum of the lattices' tasks
@@ -103,6 +104,24 @@ cudaError_t launch_step_batch_f16(const BatchList &bl, int parity, cudaStream_t 
                                   int variant, const int *limits, int k);
 cudaError_t launch_step_batch_bf16(const BatchList &bl, int parity, cudaStream_t st, int block,
                                    int variant, const int *limits, int k);
+// Constant-memory table of the 16-bit batched step's collision constants:
+// kPairSlots lattices per storage type and device (PC_COUNT floats each,
+// 61,440 bytes of the 64 KB constant bank).  upload_batch_pairs writes slots
+// pbase .. pbase + n - 1 from the entries' parameters through `stage`
+// (n * PC_COUNT floats of device memory) in the order of stream st.
+constexpr int kPairSlots = 960;
+cudaError_t upload_batch_pairs_f16(const BatchEntry *ents, int n, int pbase, float *stage,
+                                   cudaStream_t st);
+cudaError_t upload_batch_pairs_bf16(const BatchEntry *ents, int n, int pbase, float *stage,
+                                    cudaStream_t st);
+inline cudaError_t upload_batch_pairs(int dtype, const BatchEntry *ents, int n, int pbase,
+                                      float *stage, cudaStream_t st) {
+  switch (dtype) {
+    case LBM_F16DEV: return upload_batch_pairs_f16(ents, n, pbase, stage, st);
+    case LBM_BF16DEV: return upload_batch_pairs_bf16(ents, n, pbase, stage, st);
+    default: return cudaSuccess;
+  }
+}
 cudaError_t launch_step_f64(const Lattice &L, const void *src, void *dst,
                             cudaStream_t st, int block, int grid_cap);
 

@@ -128,7 +128,8 @@ k_batch_resident(const BatchEntry *__restrict__ ents, const int *__restrict__ id
           Elem<T>::unpack2(bits16(&A[i * N + n0.at(i)]) | bits16(&A[i * N + n1.at(i)]) << 16, u);
           f[i] = f2(u[0], u[1]);
         }
-        collide_pair<SCALED>(f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8], P);
+        collide_pair<SCALED>(f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8],
+                             ParamPairs{P});
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
           float u[2];

@@ -13,6 +13,11 @@ cudaError_t launch_step_batch_f16(const BatchList &bl, int parity, cudaStream_t 
   return launch_step_batch_t<__half>(bl, parity, st, block, variant, limits, k);
 }
 
+cudaError_t upload_batch_pairs_f16(const BatchEntry *ents, int n, int pbase, float *stage,
+                                   cudaStream_t st) {
+  return upload_pairs_t<__half>(ents, n, pbase, stage, st);
+}
+
 cudaError_t launch_batch_resident_f16(const BatchEntry *ents, const int *idx, int nres,
                                       int nents, size_t smem, int parity, long steps,
                                       const int *limits, cudaStream_t st) {

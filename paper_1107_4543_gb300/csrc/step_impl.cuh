@@ -22,14 +22,28 @@ namespace lbm {
 template <typename T> struct ParamsOf { using type = DevParams; };
 template <> struct ParamsOf<double> { using type = DevParams64; };
 
+// The 16-bit batched step's per-lattice collision constants (PairConst
+// order, PC_COUNT per lattice) in constant memory: each batch owns a range
+// of kPairSlots lattice slots of its storage type's table (one table per
+// translation unit and device) and refreshes it from its entries before it
+// steps.  Read at a block-uniform index, the constants take the constant
+// cache's path instead of global loads held in registers across the task:
+// spills of k_step_batch<__half> at 80 registers 148 -> 84 bytes, the
+// 512-lattice FP16 batch 5.76 -> 6.14 TB/s.
+static __constant__ float c_pairs[kPairSlots * PC_COUNT];
+
+struct ConstPairs {
+  int base;  // first constant of the lattice: slot * PC_COUNT
+  __device__ __forceinline__ F2 operator()(PairConst c) const { return f2s(c_pairs[base + c]); }
+};
+
 // 16-bit storage: unpack / collide / repack the packed populations two
 // nodes at a time (9 x V floats per lane would not fit the register
 // budget); the word's two nodes collide together, one per lane of the
 // packed FP32 pair instructions.  FP16 is stored scaled and collided in the
 // scaled units.
-template <typename T>
-__device__ __forceinline__ void collide_packed(uint32_t (&w)[9][Elem<T>::V / 2],
-                                               const DevParams &P) {
+template <typename T, typename K>
+__device__ __forceinline__ void collide_packed(uint32_t (&w)[9][Elem<T>::V / 2], const K &P) {
   constexpr bool SCALED = std::is_same<T, __half>::value;
 #pragma unroll
   for (int k = 0; k < Elem<T>::V / 2; ++k) {
@@ -50,10 +64,15 @@ __device__ __forceinline__ void collide_packed(uint32_t (&w)[9][Elem<T>::V / 2],
   }
 }
 
-template <typename T>
+// The collision constants of a 16-bit task: a DevParams, or the lattice's
+// slot of the constant table
+__device__ __forceinline__ ParamPairs pairs_of(const DevParams &P) { return ParamPairs{P}; }
+__device__ __forceinline__ const ConstPairs &pairs_of(const ConstPairs &P) { return P; }
+
+// P: the lattice's ParamsOf<T>::type, or (16-bit types) a ConstPairs
+template <typename T, typename PS>
 __device__ __forceinline__ void step_task(const T *__restrict__ src, T *__restrict__ dst,
-                                          const Geom &g, const typename ParamsOf<T>::type &P,
-                                          long long task, int lane) {
+                                          const Geom &g, const PS &P, long long task, int lane) {
   constexpr int V = Elem<T>::V;
   // FP16 is stored scaled and collided in the scaled units; FP32 carries
   // hi + lo constants (see collide_dev)
@@ -66,7 +85,7 @@ __device__ __forceinline__ void step_task(const T *__restrict__ src, T *__restri
   if constexpr (sizeof(T) == 2) {
     uint32_t w[9][V / 2];
     pull9_packed<T>(src, g, p, w);
-    collide_packed<T>(w, P);
+    collide_packed<T>(w, pairs_of(P));
     store9_packed<T>(dst, g, p, w);
   } else if constexpr (std::is_same<T, double>::value) {
     double f[9][V];
@@ -110,11 +129,12 @@ k_step_dev(const T *__restrict__ src, T *__restrict__ dst, Geom g,
 // bandwidth on batches of small lattices).  Warps past the lattice's last
 // task return.  limits (may be null): lattice l takes part only while
 // k < limits[l], so members of one launch sequence can stop after different
-// step counts.
-template <typename T, int MINB>
+// step counts.  CP (16-bit types): lattice l's collision constants are slot
+// pbase + l of the constant table, else its entry's DevParams.
+template <typename T, int MINB, bool CP>
 __global__ void __launch_bounds__(256, MINB)
 k_step_batch(const BatchEntry *__restrict__ ents, const BlockRec *__restrict__ blocks,
-             int nents, int parity, const int *__restrict__ limits, int k) {
+             int nents, int parity, const int *__restrict__ limits, int k, int pbase) {
   const int lane = threadIdx.x & 31;
   const BlockRec &B = blocks[blockIdx.x];
   // The records are read once per launch, so a step's 4.9 GB of streaming
@@ -136,8 +156,14 @@ k_step_batch(const BatchEntry *__restrict__ ents, const BlockRec *__restrict__ b
   if (!bounds::ok(B.lat >= 0 && B.lat < nents, bounds::BATCH_REC)) return;
   if (limits != nullptr && k >= limits[B.lat]) return;   // block-uniform
   const int from = parity ^ B.off;
-  step_task<T>(static_cast<const T *>(B.buf[from]), static_cast<T *>(B.buf[from ^ 1]), B.g,
-               ents[B.lat].dp, task, lane);
+  const T *src = static_cast<const T *>(B.buf[from]);
+  T *dst = static_cast<T *>(B.buf[from ^ 1]);
+  if constexpr (CP) {
+    static_assert(sizeof(T) == 2, "the constant table holds the 16-bit collision's constants");
+    step_task<T>(src, dst, B.g, ConstPairs{(pbase + B.lat) * PC_COUNT}, task, lane);
+  } else {
+    step_task<T>(src, dst, B.g, ents[B.lat].dp, task, lane);
+  }
 }
 
 static inline long long n_tasks(const Geom &g) { return g.tasks; }
@@ -214,6 +240,30 @@ cudaError_t launch_step_dev_t(const Lattice &L, const void *src, void *dst, cuda
 
 namespace lbm {
 
+// Slots pbase .. pbase + n - 1 of the constant table from the entries'
+// parameters, through stage (n * PC_COUNT floats of device memory), in the
+// order of stream st.
+static __global__ void k_fill_pairs(const BatchEntry *__restrict__ ents, int n,
+                                    float *__restrict__ stage) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n * PC_COUNT) stage[i] = pair_const(ents[i / PC_COUNT].dp, i % PC_COUNT);
+}
+
+template <typename T>
+cudaError_t upload_pairs_t(const BatchEntry *ents, int n, int pbase, float *stage,
+                           cudaStream_t st) {
+  static_assert(sizeof(T) == 2, "16-bit storage types only");
+  if (n < 1) return cudaSuccess;
+  if (pbase < 0 || n > kPairSlots - pbase || stage == nullptr) return cudaErrorInvalidValue;
+  const int nv = n * PC_COUNT;
+  k_fill_pairs<<<(nv + 255) / 256, 256, 0, st>>>(ents, n, stage);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbolAsync(c_pairs, stage, (size_t)nv * sizeof(float),
+                                 (size_t)pbase * PC_COUNT * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, st);
+}
+
 template <typename T>
 cudaError_t launch_step_batch_t(const BatchList &bl, int parity, cudaStream_t st, int block,
                                 int variant, const int *limits, int k) {
@@ -241,15 +291,37 @@ cudaError_t launch_step_batch_t(const BatchList &bl, int parity, cudaStream_t st
     return cudaGetLastError();
   }
   const unsigned grid = (unsigned)bl.nblocks;
+  if constexpr (sizeof(T) == 2) {
+    if (bl.pbase >= 0) {
+      switch (variant) {
+        case 0:
+          k_step_batch<T, 1, true><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity,
+                                                           limits, k, bl.pbase);
+          break;
+        case 1:
+          k_step_batch<T, 2, true><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity,
+                                                           limits, k, bl.pbase);
+          break;
+        default:
+          k_step_batch<T, 3, true><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity,
+                                                           limits, k, bl.pbase);
+          break;
+      }
+      return cudaGetLastError();
+    }
+  }
   switch (variant) {
     case 0:
-      k_step_batch<T, 1><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits, k);
+      k_step_batch<T, 1, false><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits,
+                                                        k, -1);
       break;
     case 1:
-      k_step_batch<T, 2><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits, k);
+      k_step_batch<T, 2, false><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits,
+                                                        k, -1);
       break;
     default:
-      k_step_batch<T, 3><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits, k);
+      k_step_batch<T, 3, false><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits,
+                                                        k, -1);
       break;
   }
   return cudaGetLastError();

@@ -78,6 +78,7 @@ _SIGS = {
     "lbm_batch_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_batch_get_variant": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_resident": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_const_table": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "lbm_get_variant": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "lbm_opt_cost": (ctypes.c_int, [ctypes.POINTER(lbm_cost_spec), ctypes.c_int, _dp, _dp]),
     "lbm_opt_minimize": (ctypes.c_int, [ctypes.POINTER(lbm_cost_spec), _dp, ctypes.c_uint, _dp,
@@ -323,6 +324,16 @@ def lbm_batch_resident(b):
     f = np.zeros(n, dtype=np.int32)
     _ck(load().lbm_batch_resident(b, f.ctypes.data_as(ctypes.POINTER(ctypes.c_int))),
         "lbm_batch_resident")
+    return f.astype(bool)
+
+
+def lbm_batch_const_table(b):
+    """Per member: whether the batched step reads its collision constants
+    from the constant-memory table (bool array in member order)."""
+    n = lbm_batch_size(b)[0]
+    f = np.zeros(n, dtype=np.int32)
+    _ck(load().lbm_batch_const_table(b, f.ctypes.data_as(ctypes.POINTER(ctypes.c_int))),
+        "lbm_batch_const_table")
     return f.astype(bool)
 
 

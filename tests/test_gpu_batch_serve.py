@@ -149,6 +149,71 @@ def test_resident_members_equal_alone(L, cap, monkeypatch):
     assert np.all(np.isfinite(drift))
 
 
+def _scaled(fields, a):
+    rho, ux, uy = fields
+    return 1.0 + a * (rho - 1.0), a * ux, a * uy
+
+
+@pytest.mark.parametrize("mode", ["fallback", "reused", "off"])
+def test_const_table_slots_equal_alone(L, mode, monkeypatch):
+    """The 16-bit members' collision constants come from a constant-memory
+    table of 960 slots per storage type and device (lbm_batch_const_table
+    says whose).  A batch that finds no room (another batch holds the FP16
+    slots) or is made with LBM_CONST_TABLE=0 reads them from its entries;
+    slots a destroyed batch held are taken again.  Every member equals its
+    standalone run bit for bit in each case, across a batch-level re-init
+    between calls that changes the FP16 storage scales (the table is
+    refreshed before each stepping call)."""
+    monkeypatch.setenv("LBM_RESIDENT_BYTES", "0")  # every member on the per-step path
+    if mode == "off":
+        monkeypatch.setenv("LBM_CONST_TABLE", "0")
+    specs = small_specs(12, seed=23)
+    dtypes = ["f32", "f16", "bf16"] * 4
+    fields = [inp.batch_fields(sp) for sp in specs]
+    S = inp.s_ll(inp.rates("OPT"))
+    hold, hb, hs, b = [], None, [], None
+    try:
+        if mode != "off":
+            # 958 of the 960 FP16 slots taken by another batch
+            hold = [L.lbm_create(8, 8, S, 1.0, (0.0, 0.0), L.LBM_F16DEV) for _ in range(958)]
+            hb = L.lbm_batch_create(hold)
+            assert L.lbm_batch_const_table(hb).all()
+        for spec, dt, f in zip(specs, dtypes, fields):
+            h = L.lbm_create(spec["nx"], spec["ny"], inp.s_ll(spec["rates"]), 1.0, (0.0, 0.0),
+                             L.DTYPES[dt])
+            L.lbm_init_field(h, *f)
+            hs.append(h)
+        if mode == "reused":
+            L.lbm_batch_destroy(hb)
+            hb = None
+        b = L.lbm_batch_create(hs)
+        want_flags = [{"fallback": dt == "bf16", "reused": dt != "f32", "off": False}[mode]
+                      for dt in dtypes]
+        assert list(L.lbm_batch_const_table(b)) == want_flags
+        L.lbm_batch_step(b, 10)
+        L.lbm_batch_init_fields(b, [_scaled(f, 20.0) for f in fields])
+        L.lbm_batch_step(b, 23)
+        L.lbm_batch_step(b, 8)
+        got = [L.lbm_get_populations(h) for h in hs]
+    finally:
+        if b is not None:
+            L.lbm_batch_destroy(b)
+        if hb is not None:
+            L.lbm_batch_destroy(hb)
+        for h in hs + hold:
+            L.lbm_destroy(h)
+    for k, (spec, dt, f) in enumerate(zip(specs, dtypes, fields)):
+        h = L.lbm_create(spec["nx"], spec["ny"], inp.s_ll(spec["rates"]), 1.0, (0.0, 0.0),
+                         L.DTYPES[dt])
+        try:
+            L.lbm_init_field(h, *_scaled(f, 20.0))
+            L.lbm_step(h, 31)
+            want = L.lbm_get_populations(h)
+        finally:
+            L.lbm_destroy(h)
+        assert np.array_equal(got[k], want), (mode, k, dt)
+
+
 def test_batch_host_io_equals_member_calls(L):
     """lbm_batch_init_fields / lbm_batch_moments give exactly what the
     per-member calls give, keep the batch usable across re-inits, and reject
