@@ -131,10 +131,11 @@ k_step_dev(const T *__restrict__ src, T *__restrict__ dst, Geom g,
 // k < limits[l], so members of one launch sequence can stop after different
 // step counts.  CP (16-bit types): lattice l's collision constants are slot
 // pbase + l of the constant table, else its entry's DevParams.
-template <typename T, int MINB, bool CP>
-__global__ void __launch_bounds__(256, MINB)
-k_step_batch(const BatchEntry *__restrict__ ents, const BlockRec *__restrict__ blocks,
-             int nents, int parity, const int *__restrict__ limits, int k, int pbase) {
+template <typename T, bool CP>
+__device__ __forceinline__ void batch_block(const BatchEntry *__restrict__ ents,
+                                            const BlockRec *__restrict__ blocks, int nents,
+                                            int parity, const int *__restrict__ limits, int k,
+                                            int pbase) {
   const int lane = threadIdx.x & 31;
   const BlockRec &B = blocks[blockIdx.x];
   // The records are read once per launch, so a step's 4.9 GB of streaming
@@ -164,6 +165,28 @@ k_step_batch(const BatchEntry *__restrict__ ents, const BlockRec *__restrict__ b
   } else {
     step_task<T>(src, dst, B.g, ents[B.lat].dp, task, lane);
   }
+}
+
+template <typename T, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+k_step_batch(const BatchEntry *__restrict__ ents, const BlockRec *__restrict__ blocks,
+             int nents, int parity, const int *__restrict__ limits, int k) {
+  batch_block<T, false>(ents, blocks, nents, parity, limits, k, -1);
+}
+
+// The 16-bit types with the constant table.  Register caps by variant: no
+// cap, 128, and 72 (28 warps per SM) where the plain kernel has 80 (24
+// warps): without the constants held in registers the task spills less at
+// 72 than at 80 (ptxas: FP16 64 / 56 bytes stored / loaded against 84 / 80,
+// BF16 100 / 88 against 104 / 104), and the 512-lattice batch streams at
+// 0.962 / 0.920 of the measured copy rate against 0.925 / 0.894 (FP16 /
+// BF16; 64 registers, 32 warps: 0.882 / 0.747).  The cap is written out in
+// the attribute: nvcc takes a plain expression of MINB there.
+template <typename T, int MINB>
+__global__ void __maxnreg__(MINB >= 3 ? 72 : (MINB == 2 ? 128 : 255))
+k_step_batch_table(const BatchEntry *__restrict__ ents, const BlockRec *__restrict__ blocks,
+                   int nents, int parity, const int *__restrict__ limits, int k, int pbase) {
+  batch_block<T, true>(ents, blocks, nents, parity, limits, k, pbase);
 }
 
 static inline long long n_tasks(const Geom &g) { return g.tasks; }
@@ -295,15 +318,15 @@ cudaError_t launch_step_batch_t(const BatchList &bl, int parity, cudaStream_t st
     if (bl.pbase >= 0) {
       switch (variant) {
         case 0:
-          k_step_batch<T, 1, true><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity,
+          k_step_batch_table<T, 1><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity,
                                                            limits, k, bl.pbase);
           break;
         case 1:
-          k_step_batch<T, 2, true><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity,
+          k_step_batch_table<T, 2><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity,
                                                            limits, k, bl.pbase);
           break;
         default:
-          k_step_batch<T, 3, true><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity,
+          k_step_batch_table<T, 3><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity,
                                                            limits, k, bl.pbase);
           break;
       }
@@ -312,16 +335,13 @@ cudaError_t launch_step_batch_t(const BatchList &bl, int parity, cudaStream_t st
   }
   switch (variant) {
     case 0:
-      k_step_batch<T, 1, false><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits,
-                                                        k, -1);
+      k_step_batch<T, 1><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits, k);
       break;
     case 1:
-      k_step_batch<T, 2, false><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits,
-                                                        k, -1);
+      k_step_batch<T, 2><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits, k);
       break;
     default:
-      k_step_batch<T, 3, false><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits,
-                                                        k, -1);
+      k_step_batch<T, 3><<<grid, block, 0, st>>>(bl.ents, bl.blocks, bl.n, parity, limits, k);
       break;
   }
   return cudaGetLastError();
