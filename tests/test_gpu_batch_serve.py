@@ -214,6 +214,41 @@ def test_const_table_slots_equal_alone(L, mode, monkeypatch):
         assert np.array_equal(got[k], want), (mode, k, dt)
 
 
+def test_const_table_two_live_batches(L, monkeypatch):
+    """Two batches alive at once hold neighbouring ranges of the FP16 and
+    BF16 constant tables (the second one's start past slot 0) and step in
+    turns, each call refreshing its own range: every member of both equals
+    its standalone run bit for bit."""
+    monkeypatch.setenv("LBM_RESIDENT_BYTES", "0")
+    specs = small_specs(14, seed=29)
+    dtypes = ["f16", "bf16", "f32", "f16", "bf16", "f16", "bf16"] * 2
+    groups = [(0, 7), (7, 14)]
+    steps = [(9, 4, 13), (6, 17, 2)]  # per batch, its calls in turn
+    hs, bs = [], []
+    try:
+        for spec, dt in zip(specs, dtypes):
+            h = L.lbm_create(spec["nx"], spec["ny"], inp.s_ll(spec["rates"]), 1.0, (0.0, 0.0),
+                             L.DTYPES[dt])
+            L.lbm_init_field(h, *inp.batch_fields(spec))
+            hs.append(h)
+        for lo, hi in groups:
+            bs.append(L.lbm_batch_create(hs[lo:hi]))
+            assert list(L.lbm_batch_const_table(bs[-1])) == [dt != "f32" for dt in dtypes[lo:hi]]
+        for c in range(3):
+            for b, st in zip(bs, steps):
+                L.lbm_batch_step(b, st[c])
+        got = [L.lbm_get_populations(h) for h in hs]
+    finally:
+        for b in bs:
+            L.lbm_batch_destroy(b)
+        for h in hs:
+            L.lbm_destroy(h)
+    for k, (spec, dt) in enumerate(zip(specs, dtypes)):
+        n = sum(steps[0 if k < 7 else 1])
+        want, _ = alone(L, spec, dt, n)
+        assert np.array_equal(got[k], want), (k, dt)
+
+
 def test_batch_host_io_equals_member_calls(L):
     """lbm_batch_init_fields / lbm_batch_moments give exactly what the
     per-member calls give, keep the batch usable across re-inits, and reject
