@@ -470,14 +470,15 @@ int lbm_batch_get_variant(lbm_batch b, int *variant);
 int lbm_batch_resident(lbm_batch b, int *flags);
 /* (runtime; no counterpart in the paper) Which members' collision constants
  * the per-step launches read from a constant-memory table (flags: one int
- * per member, 1 for such a member).  The 16-bit storage types (LBM_F16DEV,
- * LBM_BF16DEV) of a batch reserve one slot per member of that type, out of
- * 960 per storage type and device shared by all live batches, when the
- * batch is made, and release them when it is destroyed; a batch that finds
- * no room, or is made with the environment variable LBM_CONST_TABLE=0, reads
- * the constants from its members' entries in global memory instead.  The
- * slots are refreshed from the members' parameters at the start of every
- * stepping call.  Results are bit-identical either way. */
+ * per member, 1 for such a member).  Each storage type of a batch reserves
+ * one slot per member of that type when the batch is made, out of a table
+ * per storage type and device shared by all live batches (960 slots for
+ * LBM_F16DEV and LBM_BF16DEV, 640 for LBM_F32DEV), and releases them when
+ * it is destroyed; a type that finds no room, or a batch made with the
+ * environment variable LBM_CONST_TABLE=0, reads the constants from its
+ * members' entries in global memory instead.  The slots are refreshed from
+ * the members' parameters at the start of every stepping call.  Results
+ * are bit-identical either way. */
 int lbm_batch_const_table(lbm_batch b, int *flags);
 /* The sums of lbm_drift for every member at once (out: 4 doubles per member,
  * in member order): one reduction launch pair for the whole batch,

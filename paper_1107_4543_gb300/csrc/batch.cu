@@ -22,10 +22,11 @@
 using namespace lbm;
 
 // ------------------------------------------------------------ constant slots
-// Slots of the 16-bit batched step's constant tables (kPairSlots per storage
-// type and device, step_impl.cuh): a batch group holds one contiguous range
-// from its creation to its destruction; a group that finds no room (or runs
-// with LBM_CONST_TABLE=0) reads its entries' parameters instead.
+// Slots of the batched step's constant tables (const_slots(dtype) per
+// storage type and device, step_impl.cuh): a batch group holds one
+// contiguous range from its creation to its destruction; a group that finds
+// no room (or runs with LBM_CONST_TABLE=0) reads its entries' parameters
+// instead.
 namespace {
 std::mutex g_slot_mu;
 std::map<std::pair<int, int>, std::vector<char>> g_slot_used;  // (device, dtype) -> slot taken
@@ -33,11 +34,12 @@ std::map<std::pair<int, int>, std::vector<char>> g_slot_used;  // (device, dtype
 int slots_reserve(int dev, int dtype, int n) {
   const char *env = getenv("LBM_CONST_TABLE");
   if (env != nullptr && strcmp(env, "0") == 0) return -1;
-  if (n < 1 || n > kPairSlots) return -1;
+  const int cap = const_slots(dtype);
+  if (n < 1 || n > cap) return -1;
   std::lock_guard<std::mutex> lk(g_slot_mu);
   auto &used = g_slot_used[{dev, dtype}];
-  if (used.empty()) used.assign(kPairSlots, 0);
-  for (int s = 0, run = 0; s < kPairSlots; ++s) {
+  if (used.empty()) used.assign(cap, 0);
+  for (int s = 0, run = 0; s < cap; ++s) {
     run = used[s] ? 0 : run + 1;
     if (run == n) {
       std::fill(used.begin() + (s - n + 1), used.begin() + (s + 1), 1);
@@ -76,10 +78,10 @@ struct lbm_batch_ctx {
     int *res = nullptr;
     int res_count[3] = {0, 0, 0};
     size_t res_smem[3] = {0, 0, 0};  // shared memory of a block of the class
-    // 16-bit types: the group's slots in the constant table (-1: none) and
-    // the device staging of their refresh (n x PC_COUNT floats)
+    // the group's slots in its type's constant table (-1: none) and the
+    // device staging of their refresh (n x const_slot_bytes(dtype))
     int pbase = -1;
-    float *pstage = nullptr;
+    void *pstage = nullptr;
   };
   std::vector<int> member_group, member_local;  // member -> (group, entry)
   std::vector<int> member_res;                  // member stepped as a resident entry
@@ -186,7 +188,7 @@ static BatchList batch_list(const lbm_batch_ctx::Group &gr) {
 static int batch_upload_pairs(lbm_batch_ctx *b) {
   for (auto &gr : b->groups)
     if (gr.pbase >= 0)
-      CK(upload_batch_pairs(gr.dtype, gr.ents, gr.n, gr.pbase, gr.pstage, b->stream));
+      CK(upload_batch_consts(gr.dtype, gr.ents, gr.n, gr.pbase, gr.pstage, b->stream));
   return LBM_OK;
 }
 
@@ -719,10 +721,10 @@ int lbm_batch_create(int n, const lbm_handle *members, lbm_batch *out) {
       gr.res = (int *)dev_alloc(sizeof(int) * res.size());
       b->resident = true;
     }
-    if (dt == LBM_F16DEV || dt == LBM_BF16DEV) {
+    if (const_slots(dt) > 0) {
       gr.pbase = slots_reserve(b->device, dt, gr.n);
       if (gr.pbase >= 0) {
-        gr.pstage = (float *)dev_alloc(sizeof(float) * PC_COUNT * (size_t)gr.n);
+        gr.pstage = dev_alloc(const_slot_bytes(dt) * (size_t)gr.n);
         if (!gr.pstage) {
           slots_release(b->device, dt, gr.pbase, gr.n);
           gr.pbase = -1;

@@ -77,7 +77,7 @@ struct BlockRec {
 struct BatchList {
   const BatchEntry *ents;
   int n;
-  int pbase = -1;  // 16-bit types: first slot of the constant table, or -1 (entries)
+  int pbase = -1;  // first slot of the type's constant table, or -1 (entries)
   const BlockRec *blocks;  // the plain grid's blocks
   long long nblocks;       // sum over lattices of ceil(tasks / warps per block)
   long long ntasks;        // sum of the lattices' tasks
@@ -104,21 +104,35 @@ cudaError_t launch_step_batch_f16(const BatchList &bl, int parity, cudaStream_t 
                                   int variant, const int *limits, int k);
 cudaError_t launch_step_batch_bf16(const BatchList &bl, int parity, cudaStream_t st, int block,
                                    int variant, const int *limits, int k);
-// Constant-memory table of the 16-bit batched step's collision constants:
-// kPairSlots lattices per storage type and device (PC_COUNT floats each,
-// 61,440 bytes of the 64 KB constant bank).  upload_batch_pairs writes slots
+// Constant-memory tables of the batched step's per-lattice collision
+// constants, one per storage type and device (step_impl.cuh): the 16-bit
+// types keep PC_COUNT broadcast floats per lattice (kPairSlots lattices,
+// 61,440 bytes of the 64 KB constant bank), FP32 whole DevParams records
+// (kDevSlots lattices, 64,000 bytes).  upload_batch_consts writes slots
 // pbase .. pbase + n - 1 from the entries' parameters through `stage`
-// (n * PC_COUNT floats of device memory) in the order of stream st.
+// (n * const_slot_bytes(dtype) bytes of device memory) in the order of
+// stream st.
 constexpr int kPairSlots = 960;
-cudaError_t upload_batch_pairs_f16(const BatchEntry *ents, int n, int pbase, float *stage,
-                                   cudaStream_t st);
-cudaError_t upload_batch_pairs_bf16(const BatchEntry *ents, int n, int pbase, float *stage,
+constexpr int kDevSlots = 640;
+inline int const_slots(int dtype) {
+  return dtype == LBM_F32DEV ? kDevSlots
+                             : (dtype == LBM_F16DEV || dtype == LBM_BF16DEV ? kPairSlots : 0);
+}
+inline size_t const_slot_bytes(int dtype) {
+  return dtype == LBM_F32DEV ? sizeof(DevParams) : PC_COUNT * sizeof(float);
+}
+cudaError_t upload_batch_consts_f32(const BatchEntry *ents, int n, int pbase, void *stage,
                                     cudaStream_t st);
-inline cudaError_t upload_batch_pairs(int dtype, const BatchEntry *ents, int n, int pbase,
-                                      float *stage, cudaStream_t st) {
+cudaError_t upload_batch_consts_f16(const BatchEntry *ents, int n, int pbase, void *stage,
+                                    cudaStream_t st);
+cudaError_t upload_batch_consts_bf16(const BatchEntry *ents, int n, int pbase, void *stage,
+                                     cudaStream_t st);
+inline cudaError_t upload_batch_consts(int dtype, const BatchEntry *ents, int n, int pbase,
+                                       void *stage, cudaStream_t st) {
   switch (dtype) {
-    case LBM_F16DEV: return upload_batch_pairs_f16(ents, n, pbase, stage, st);
-    case LBM_BF16DEV: return upload_batch_pairs_bf16(ents, n, pbase, stage, st);
+    case LBM_F32DEV: return upload_batch_consts_f32(ents, n, pbase, stage, st);
+    case LBM_F16DEV: return upload_batch_consts_f16(ents, n, pbase, stage, st);
+    case LBM_BF16DEV: return upload_batch_consts_bf16(ents, n, pbase, stage, st);
     default: return cudaSuccess;
   }
 }

@@ -1,4 +1,5 @@
 // Step kernels for one storage type (__half); see step_impl.cuh.
+#define LBM_TABLE_PAIRS  // this unit holds its type's constant table
 #include "step_impl.cuh"
 
 namespace lbm {
@@ -13,9 +14,9 @@ cudaError_t launch_step_batch_f16(const BatchList &bl, int parity, cudaStream_t 
   return launch_step_batch_t<__half>(bl, parity, st, block, variant, limits, k);
 }
 
-cudaError_t upload_batch_pairs_f16(const BatchEntry *ents, int n, int pbase, float *stage,
+cudaError_t upload_batch_consts_f16(const BatchEntry *ents, int n, int pbase, void *stage,
                                    cudaStream_t st) {
-  return upload_pairs_t<__half>(ents, n, pbase, stage, st);
+  return upload_consts_t<__half>(ents, n, pbase, stage, st);
 }
 
 cudaError_t launch_batch_resident_f16(const BatchEntry *ents, const int *idx, int nres,

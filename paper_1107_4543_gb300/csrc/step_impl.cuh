@@ -22,15 +22,28 @@ namespace lbm {
 template <typename T> struct ParamsOf { using type = DevParams; };
 template <> struct ParamsOf<double> { using type = DevParams64; };
 
-// The 16-bit batched step's per-lattice collision constants (PairConst
-// order, PC_COUNT per lattice) in constant memory: each batch owns a range
-// of kPairSlots lattice slots of its storage type's table (one table per
-// translation unit and device) and refreshes it from its entries before it
-// steps.  Read at a block-uniform index, the constants take the constant
-// cache's path instead of global loads held in registers across the task:
-// spills of k_step_batch<__half> at 80 registers 148 -> 84 bytes, the
-// 512-lattice FP16 batch 5.76 -> 6.14 TB/s.
-static __constant__ float c_pairs[kPairSlots * PC_COUNT];
+// The batched step's per-lattice collision constants in constant memory:
+// each batch owns a range of the slots of its storage type's table (one
+// table per translation unit and device) and refreshes it from its entries
+// before it steps.  The 16-bit types keep the PC_COUNT broadcast constants
+// of the pair collision (PairConst order).  Read at a block-uniform index,
+// the constants take the constant cache's path instead of global loads
+// held in registers across the task: spills of the FP16 step at 80
+// registers 148 -> 84 bytes, the 512-lattice FP16 batch 5.76 -> 6.14 TB/s.
+// FP32 keeps the lattice's DevParams itself (hi + lo constants, read by
+// collide_dev through a reference into the table).  A translation unit holds
+// one full-size table (the constant bank has 64 KB): step_f32.cu defines
+// LBM_TABLE_DEV, step_f16.cu and step_bf16.cu LBM_TABLE_PAIRS, before they
+// include this file; the other table shrinks to one element there.
+#if defined(LBM_TABLE_DEV)
+constexpr int kDevTable = kDevSlots, kPairTable = 1;
+#elif defined(LBM_TABLE_PAIRS)
+constexpr int kDevTable = 1, kPairTable = kPairSlots;
+#else
+constexpr int kDevTable = 1, kPairTable = 1;
+#endif
+static __constant__ float c_pairs[kPairTable * PC_COUNT];
+static __constant__ DevParams c_dev[kDevTable];
 
 struct ConstPairs {
   int base;  // first constant of the lattice: slot * PC_COUNT
@@ -159,9 +172,11 @@ __device__ __forceinline__ void batch_block(const BatchEntry *__restrict__ ents,
   const int from = parity ^ B.off;
   const T *src = static_cast<const T *>(B.buf[from]);
   T *dst = static_cast<T *>(B.buf[from ^ 1]);
-  if constexpr (CP) {
-    static_assert(sizeof(T) == 2, "the constant table holds the 16-bit collision's constants");
+  if constexpr (CP && sizeof(T) == 2) {
     step_task<T>(src, dst, B.g, ConstPairs{(pbase + B.lat) * PC_COUNT}, task, lane);
+  } else if constexpr (CP) {
+    static_assert(sizeof(T) == 4, "constant tables: FP32 and the 16-bit types");
+    step_task<T>(src, dst, B.g, c_dev[pbase + B.lat], task, lane);
   } else {
     step_task<T>(src, dst, B.g, ents[B.lat].dp, task, lane);
   }
@@ -174,16 +189,19 @@ k_step_batch(const BatchEntry *__restrict__ ents, const BlockRec *__restrict__ b
   batch_block<T, false>(ents, blocks, nents, parity, limits, k, -1);
 }
 
-// The 16-bit types with the constant table.  Register caps by variant: no
-// cap, 128, and 72 (28 warps per SM) where the plain kernel has 80 (24
-// warps): without the constants held in registers the task spills less at
-// 72 than at 80 (ptxas: FP16 64 / 56 bytes stored / loaded against 84 / 80,
-// BF16 100 / 88 against 104 / 104), and the 512-lattice batch streams at
-// 0.962 / 0.920 of the measured copy rate against 0.925 / 0.894 (FP16 /
-// BF16; 64 registers, 32 warps: 0.882 / 0.747).  The cap is written out in
-// the attribute: nvcc takes a plain expression of MINB there.
+// The batched step with the constant table.  Register caps by variant: no
+// cap, 128, and for variant 2 80 (FP32) or 72 (16-bit types; 28 warps per
+// SM instead of 24).  Without the constants held in registers the 16-bit
+// task spills less at 72 than at 80 (ptxas: FP16 64 / 56 bytes stored /
+// loaded against 84 / 80, BF16 100 / 88 against 104 / 104), and the
+// 512-lattice batch streams at 0.962 / 0.920 of the measured copy rate
+// against 0.925 / 0.894 (FP16 / BF16; 64 registers, 32 warps: 0.882 /
+// 0.747).  FP32 spills nothing at 80 (8 bytes with the constants from the
+// entries) and streams at 1.033 against 1.026 (72 registers: 1.030).  The
+// cap is written out in the attribute: nvcc takes a plain expression of
+// MINB and T there.
 template <typename T, int MINB>
-__global__ void __maxnreg__(MINB >= 3 ? 72 : (MINB == 2 ? 128 : 255))
+__global__ void __maxnreg__(MINB >= 3 ? (sizeof(T) == 4 ? 80 : 72) : (MINB == 2 ? 128 : 255))
 k_step_batch_table(const BatchEntry *__restrict__ ents, const BlockRec *__restrict__ blocks,
                    int nents, int parity, const int *__restrict__ limits, int k, int pbase) {
   batch_block<T, true>(ents, blocks, nents, parity, limits, k, pbase);
@@ -272,19 +290,39 @@ static __global__ void k_fill_pairs(const BatchEntry *__restrict__ ents, int n,
   if (i < n * PC_COUNT) stage[i] = pair_const(ents[i / PC_COUNT].dp, i % PC_COUNT);
 }
 
+static __global__ void k_fill_dev(const BatchEntry *__restrict__ ents, int n,
+                                  DevParams *__restrict__ stage) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) stage[i] = ents[i].dp;
+}
+
 template <typename T>
-cudaError_t upload_pairs_t(const BatchEntry *ents, int n, int pbase, float *stage,
-                           cudaStream_t st) {
-  static_assert(sizeof(T) == 2, "16-bit storage types only");
+cudaError_t upload_consts_t(const BatchEntry *ents, int n, int pbase, void *stage,
+                            cudaStream_t st) {
+  constexpr bool PAIRS = sizeof(T) == 2;
+  static_assert(PAIRS || sizeof(T) == 4, "constant tables: FP32 and the 16-bit types");
+  constexpr int slots = PAIRS ? kPairTable : kDevTable;
+  static_assert(slots == (PAIRS ? kPairSlots : kDevSlots),
+                "this translation unit does not hold the type's constant table");
   if (n < 1) return cudaSuccess;
-  if (pbase < 0 || n > kPairSlots - pbase || stage == nullptr) return cudaErrorInvalidValue;
-  const int nv = n * PC_COUNT;
-  k_fill_pairs<<<(nv + 255) / 256, 256, 0, st>>>(ents, n, stage);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbolAsync(c_pairs, stage, (size_t)nv * sizeof(float),
-                                 (size_t)pbase * PC_COUNT * sizeof(float),
-                                 cudaMemcpyDeviceToDevice, st);
+  if (pbase < 0 || n > slots - pbase || stage == nullptr) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if constexpr (PAIRS) {
+    const int nv = n * PC_COUNT;
+    k_fill_pairs<<<(nv + 255) / 256, 256, 0, st>>>(ents, n, static_cast<float *>(stage));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbolAsync(c_pairs, stage, (size_t)nv * sizeof(float),
+                                   (size_t)pbase * PC_COUNT * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, st);
+  } else {
+    k_fill_dev<<<(n + 255) / 256, 256, 0, st>>>(ents, n, static_cast<DevParams *>(stage));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbolAsync(c_dev, stage, (size_t)n * sizeof(DevParams),
+                                   (size_t)pbase * sizeof(DevParams), cudaMemcpyDeviceToDevice,
+                                   st);
+  }
 }
 
 template <typename T>
@@ -314,7 +352,7 @@ cudaError_t launch_step_batch_t(const BatchList &bl, int parity, cudaStream_t st
     return cudaGetLastError();
   }
   const unsigned grid = (unsigned)bl.nblocks;
-  if constexpr (sizeof(T) == 2) {
+  if constexpr (sizeof(T) <= 4) {
     if (bl.pbase >= 0) {
       switch (variant) {
         case 0:

@@ -156,10 +156,11 @@ def _scaled(fields, a):
 
 @pytest.mark.parametrize("mode", ["fallback", "reused", "off"])
 def test_const_table_slots_equal_alone(L, mode, monkeypatch):
-    """The 16-bit members' collision constants come from a constant-memory
-    table of 960 slots per storage type and device (lbm_batch_const_table
-    says whose).  A batch that finds no room (another batch holds the FP16
-    slots) or is made with LBM_CONST_TABLE=0 reads them from its entries;
+    """The members' collision constants come from a constant-memory table
+    per storage type and device (960 slots for FP16 and BF16, 640 for FP32;
+    lbm_batch_const_table says whose).  A batch that finds no room (another
+    batch holds the FP16 slots) or is made with LBM_CONST_TABLE=0 reads them
+    from its entries;
     slots a destroyed batch held are taken again.  Every member equals its
     standalone run bit for bit in each case, across a batch-level re-init
     between calls that changes the FP16 storage scales (the table is
@@ -187,7 +188,7 @@ def test_const_table_slots_equal_alone(L, mode, monkeypatch):
             L.lbm_batch_destroy(hb)
             hb = None
         b = L.lbm_batch_create(hs)
-        want_flags = [{"fallback": dt == "bf16", "reused": dt != "f32", "off": False}[mode]
+        want_flags = [{"fallback": dt != "f16", "reused": True, "off": False}[mode]
                       for dt in dtypes]
         assert list(L.lbm_batch_const_table(b)) == want_flags
         L.lbm_batch_step(b, 10)
@@ -215,8 +216,8 @@ def test_const_table_slots_equal_alone(L, mode, monkeypatch):
 
 
 def test_const_table_two_live_batches(L, monkeypatch):
-    """Two batches alive at once hold neighbouring ranges of the FP16 and
-    BF16 constant tables (the second one's start past slot 0) and step in
+    """Two batches alive at once hold neighbouring ranges of the FP32, FP16
+    and BF16 constant tables (the second one's start past slot 0) and step in
     turns, each call refreshing its own range: every member of both equals
     its standalone run bit for bit."""
     monkeypatch.setenv("LBM_RESIDENT_BYTES", "0")
@@ -233,7 +234,7 @@ def test_const_table_two_live_batches(L, monkeypatch):
             hs.append(h)
         for lo, hi in groups:
             bs.append(L.lbm_batch_create(hs[lo:hi]))
-            assert list(L.lbm_batch_const_table(bs[-1])) == [dt != "f32" for dt in dtypes[lo:hi]]
+            assert L.lbm_batch_const_table(bs[-1]).all()
         for c in range(3):
             for b, st in zip(bs, steps):
                 L.lbm_batch_step(b, st[c])
