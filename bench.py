@@ -387,6 +387,9 @@ def bench_batched(args, L, torch, rank, ws):
     res_classes = len({0 if rb <= optin // 3 else (1 if rb <= optin // 2 else 2)
                        for rb in (2 * 9 * s["nx"] * s["ny"] * esize
                                   for s, r in zip(specs, resident) if r)})
+    # one launch per call refreshes the batch's slots of the constant table
+    # (a single storage type here) when it holds any
+    table_fills = int(L.lbm_batch_const_table(b).any())
 
     def one_step():
         L.lbm_batch_step(b, lbm_steps)
@@ -419,8 +422,9 @@ def bench_batched(args, L, torch, rank, ws):
     lu_job = reduce_sum(lu_per_step * args.steps)  # every rank's lattice updates
     value = job_mlups(lu_job, total_ms * 1e-3)
     launch_ms = float(np.mean(step_ms)) / lbm_steps  # one batched kernel per time step
-    # batched steps, the resident launches and one drift launch pair
-    launches = args.steps * (lbm_steps + 2 + res_classes)
+    # batched steps, the resident launches, the constant-table refresh and
+    # one drift launch pair
+    launches = args.steps * (lbm_steps + 2 + res_classes + table_fills)
 
     # e2e: host fields in, moments out, through the public API: one
     # lbm_batch_solve_packed call per benchmark step (upload of the fields
