@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include "lbm_internal.h"
+#include "node_xy.cuh"
 
 namespace lbm {
 
@@ -119,7 +120,8 @@ __global__ void k_init_eq(AuxView a, const double *rho, const double *ux, const 
   unsigned int nbad = 0;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(n % a.g.nx), y = (int)(n / a.g.nx);
+    int x, y;
+    node_xy(n, a.g.nx, x, y);
     double r, u, v, f[9];
     field_at(a, rho, ux, uy, kind, ap.p, x, y, r, u, v);
     if (!(r > 0.0) || !isfinite(r) || !isfinite(u) || !isfinite(v)) ++nbad;
@@ -177,7 +179,8 @@ __global__ void k_maxdev_eq(AuxView a, const double *rho, const double *ux, cons
   float m = 0.0f;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(n % a.g.nx), y = (int)(n / a.g.nx);
+    int x, y;
+    node_xy(n, a.g.nx, x, y);
     double r, u, v, f[9];
     field_at(a, rho, ux, uy, kind, ap.p, x, y, r, u, v);
     feq_canonical(r, u, v, f);
@@ -200,7 +203,8 @@ __global__ void k_moments(AuxView a, double *rho, double *ux, double *uy) {
   const long long N = (long long)a.g.nx * a.g.ny;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(n % a.g.nx), y = (int)(n / a.g.nx);
+    int x, y;
+    node_xy(n, a.g.nx, x, y);
     double f[9];
     gather(a, x, y, f);
     double r = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
@@ -221,7 +225,8 @@ __global__ void k_get_pop(AuxView a, double *f) {
   const long long N = (long long)a.g.nx * a.g.ny;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(n % a.g.nx), y = (int)(n / a.g.nx);
+    int x, y;
+    node_xy(n, a.g.nx, x, y);
     double g[9];
     gather(a, x, y, g);
 #pragma unroll
@@ -233,7 +238,8 @@ __global__ void k_set_pop(AuxView a, const double *f) {
   const long long N = (long long)a.g.nx * a.g.ny;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(n % a.g.nx), y = (int)(n / a.g.nx);
+    int x, y;
+    node_xy(n, a.g.nx, x, y);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const int xs = wrapi(x - CXd(i), a.g.nx), ys = wrapi(y - CYd(i), a.g.nyw);
@@ -288,7 +294,7 @@ struct FF {
 // deviation types sum their FP32 values as float-float (GB300 runs FP32 at
 // many times its FP64 rate, and the 9-term sums keep ~48 bits).
 __device__ __forceinline__ void node_sums(const AuxView &a, long long off, double &r, double &jx,
-                                          double &jy, double &bad) {
+                                          double &jy, unsigned &bad) {
   if (a.dtype == LBM_F64 || a.dtype == LBM_F64DEV) {
     // deviations from the base populations first: f_i - f0_i is exact while
     // f_i stays within a factor two of f0_i (Sterbenz), so the node's sums
@@ -299,7 +305,7 @@ __device__ __forceinline__ void node_sums(const AuxView &a, long long off, doubl
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const double v = static_cast<const double *>(a.buf)[(long long)i * a.g.plane + off];
-      if (!isfinite(v)) { bad += 1.0; d[i] = 0.0; }
+      if (!isfinite(v)) { ++bad; d[i] = 0.0; }
       else d[i] = v - sub * a.f0[i];
     }
     r = d[0] + d[1] + d[2] + d[3] + d[4] + d[5] + d[6] + d[7] + d[8];
@@ -316,7 +322,7 @@ __device__ __forceinline__ void node_sums(const AuxView &a, long long off, doubl
     if (a.dtype == LBM_F32DEV) v = static_cast<const float *>(a.buf)[idx];
     else if (a.dtype == LBM_F16DEV) v = __half2float(static_cast<const __half *>(a.buf)[idx]) * inv;
     else v = __bfloat162float(static_cast<const __nv_bfloat16 *>(a.buf)[idx]);
-    if (!isfinite(v)) { bad += 1.0; v = 0.0f; }
+    if (!isfinite(v)) { ++bad; v = 0.0f; }
     f[i] = v;
   }
   FF s0{f[0], 0.0f}, s1{f[1], 0.0f}, s2{f[2], 0.0f};
@@ -332,16 +338,20 @@ __device__ __forceinline__ void node_sums(const AuxView &a, long long off, doubl
 __global__ void __launch_bounds__(DRIFT_THREADS) k_drift1(AuxView a, double *partials) {
   __shared__ double sh[4][DRIFT_THREADS];
   const long long N = (long long)a.g.nx * a.g.ny;
-  double s0 = 0, s1 = 0, s2 = 0, bad = 0;
-  for (long long n = blockIdx.x * (long long)DRIFT_THREADS + threadIdx.x; n < N;
-       n += (long long)DRIFT_BLOCKS * DRIFT_THREADS) {
-    const int x = (int)(n % a.g.nx), y = (int)(n / a.g.nx);
-    double r, jx, jy;
-    node_sums(a, (long long)y * a.g.rstride + x, r, jx, jy, bad);
-    s0 += r; s1 += jx; s2 += jy;
+  double s0 = 0, s1 = 0, s2 = 0;
+  unsigned bad = 0;
+  const long long n0 = blockIdx.x * (long long)DRIFT_THREADS + threadIdx.x;
+  const long long stride = (long long)DRIFT_BLOCKS * DRIFT_THREADS;
+  if (n0 < N) {
+    NodeWalk w(n0, stride, a.g.nx);
+    for (long long n = n0; n < N; n += stride, w.next()) {
+      double r, jx, jy;
+      node_sums(a, (long long)w.y * a.g.rstride + w.x, r, jx, jy, bad);
+      s0 += r; s1 += jx; s2 += jy;
+    }
   }
   sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = s1;
-  sh[2][threadIdx.x] = s2; sh[3][threadIdx.x] = bad;
+  sh[2][threadIdx.x] = s2; sh[3][threadIdx.x] = (double)bad;
   __syncthreads();
   for (int w = DRIFT_THREADS / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w)
@@ -375,16 +385,20 @@ k_batch_drift1(const AuxView *__restrict__ views, double *partials) {
   __shared__ double sh[4][DRIFT_THREADS];
   const AuxView &a = views[blockIdx.y];
   const long long N = (long long)a.g.nx * a.g.ny;
-  double s0 = 0, s1 = 0, s2 = 0, bad = 0;
-  for (long long n = blockIdx.x * (long long)DRIFT_THREADS + threadIdx.x; n < N;
-       n += (long long)BD_BLOCKS * DRIFT_THREADS) {
-    const int x = (int)(n % a.g.nx), y = (int)(n / a.g.nx);
-    double r, jx, jy;
-    node_sums(a, (long long)y * a.g.rstride + x, r, jx, jy, bad);
-    s0 += r; s1 += jx; s2 += jy;
+  double s0 = 0, s1 = 0, s2 = 0;
+  unsigned bad = 0;
+  const long long n0 = blockIdx.x * (long long)DRIFT_THREADS + threadIdx.x;
+  const long long stride = (long long)BD_BLOCKS * DRIFT_THREADS;
+  if (n0 < N) {
+    NodeWalk w(n0, stride, a.g.nx);
+    for (long long n = n0; n < N; n += stride, w.next()) {
+      double r, jx, jy;
+      node_sums(a, (long long)w.y * a.g.rstride + w.x, r, jx, jy, bad);
+      s0 += r; s1 += jx; s2 += jy;
+    }
   }
   sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = s1;
-  sh[2][threadIdx.x] = s2; sh[3][threadIdx.x] = bad;
+  sh[2][threadIdx.x] = s2; sh[3][threadIdx.x] = (double)bad;
   __syncthreads();
   for (int w = DRIFT_THREADS / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w)

@@ -18,6 +18,7 @@
 
 #include "bounds.cuh"
 #include "lbm_internal.h"
+#include "node_xy.cuh"
 
 namespace lbm {
 namespace {
@@ -134,7 +135,8 @@ __global__ void __launch_bounds__(256) k_init_dev(AuxView a, RefState R, const d
   unsigned int nbad = 0;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(n / nx), x = (int)(n - (long long)y * nx);
+    int x, y;
+    node_xy(n, nx, x, y);
     if (init_node<T>(a, R, x, y, rho[n], ux[n], uy[n])) ++nbad;
   }
   if (bad && nbad) atomicAdd(bad, nbad);
@@ -186,7 +188,8 @@ __global__ void __launch_bounds__(256) k_moments_dev(AuxView a, double *rho, dou
   const double inv_scale = 1.0 / a.scale;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(n / nx), x = (int)(n - (long long)y * nx);
+    int x, y;
+    node_xy(n, nx, x, y);
     moments_node<T>(a, x, y, inv_scale, rho[n], ux[n], uy[n]);
   }
 }
@@ -214,7 +217,8 @@ __device__ __forceinline__ void batch_init_block(const AuxView &a, const IoBlock
   unsigned int nbad = 0;
   for (int j = threadIdx.x; j < B.count; j += blockDim.x) {
     const long long n = B.start + j;
-    const int y = (int)(n / a.g.nx), x = (int)(n - (long long)y * a.g.nx);
+    int x, y;
+    node_xy(n, a.g.nx, x, y);
     if (init_node<T>(a, R, x, y, r_[n], u_[n], v_[n])) ++nbad;
   }
   if (nbad) atomicAdd(bad + B.member, nbad);
@@ -247,7 +251,8 @@ __device__ __forceinline__ void batch_moments_block(const AuxView &a, const IoBl
   const double inv_scale = 1.0 / a.scale;
   for (int j = threadIdx.x; j < B.count; j += blockDim.x) {
     const long long n = B.start + j;
-    const int y = (int)(n / a.g.nx), x = (int)(n - (long long)y * a.g.nx);
+    int x, y;
+    node_xy(n, a.g.nx, x, y);
     moments_node<T>(a, x, y, inv_scale, r_[n], u_[n], v_[n]);
   }
 }
