@@ -8,7 +8,7 @@
 
 namespace lbm {
 
-__device__ __forceinline__ void node_xy(long long n, int nx, int &x, int &y) {
+__host__ __device__ __forceinline__ void node_xy(long long n, int nx, int &x, int &y) {
   if (n < 0x7fffffffLL) {
     const unsigned q = (unsigned)n / (unsigned)nx;
     y = (int)q;
@@ -23,12 +23,12 @@ __device__ __forceinline__ void node_xy(long long n, int nx, int &x, int &y) {
 // (x, y) advanced by a fixed step instead of a division per node.
 struct NodeWalk {
   int x, y, dx, dy, nx;
-  __device__ __forceinline__ NodeWalk(long long n, long long stride, int nx_) : nx(nx_) {
+  __host__ __device__ __forceinline__ NodeWalk(long long n, long long stride, int nx_) : nx(nx_) {
     node_xy(n, nx, x, y);
     dy = (int)(stride / nx);
     dx = (int)(stride - (long long)dy * nx);
   }
-  __device__ __forceinline__ void next() {
+  __host__ __device__ __forceinline__ void next() {
     x += dx;
     y += dy;
     if (x >= nx) {
