@@ -157,8 +157,9 @@ __device__ __forceinline__ void batch_block(const BatchEntry *__restrict__ ents,
   // the block about one wave of resident blocks later (measured +1.7%
   // FP32, +2.9% FP16, +1.8% BF16 on the 512-lattice batch; any distance
   // from 1024 to 2048 blocks alike; 152 SMs hold 1824 of the 64-thread
-  // blocks at the 80-register cap; a compile-time distance keeps the
-  // register budget, a launch parameter cost 20 bytes more of spills)
+  // blocks at the 80-register cap, 2128 at 72; a compile-time distance
+  // keeps the register budget, a launch parameter cost 20 bytes more of
+  // spills)
   constexpr unsigned kPrefetch = 1536;
   if (threadIdx.x == 0 && blockIdx.x + kPrefetch < gridDim.x) {
     const char *q = reinterpret_cast<const char *>(blocks + blockIdx.x + kPrefetch);
