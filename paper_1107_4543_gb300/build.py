@@ -34,7 +34,7 @@ UNITS = {
     "optcost.cu": [],
 }
 HEADERS = ["lbm_internal.h", "d2q9_pull.cuh", "collide.cuh", "step_impl.cuh", "bounds.cuh",
-           "resident.cuh", "runtime.h", "node_xy.cuh"]
+           "resident.cuh", "runtime.h", "node_xy.cuh", "slots.h"]
 # the debug build: device-side index checks that record failures in a word
 # (lbm_debug_bounds) instead of trapping
 OUT_DEBUG = os.path.join(HERE, "_build_debug")

@@ -18,6 +18,7 @@
 
 #include "lbm_internal.h"
 #include "runtime.h"
+#include "slots.h"
 
 using namespace lbm;
 
@@ -29,31 +30,22 @@ using namespace lbm;
 // instead.
 namespace {
 std::mutex g_slot_mu;
-std::map<std::pair<int, int>, std::vector<char>> g_slot_used;  // (device, dtype) -> slot taken
+std::map<std::pair<int, int>, SlotRanges> g_slots;  // (device, dtype) -> its table's ranges
 
 int slots_reserve(int dev, int dtype, int n) {
   const char *env = getenv("LBM_CONST_TABLE");
   if (env != nullptr && strcmp(env, "0") == 0) return -1;
-  const int cap = const_slots(dtype);
-  if (n < 1 || n > cap) return -1;
   std::lock_guard<std::mutex> lk(g_slot_mu);
-  auto &used = g_slot_used[{dev, dtype}];
-  if (used.empty()) used.assign(cap, 0);
-  for (int s = 0, run = 0; s < cap; ++s) {
-    run = used[s] ? 0 : run + 1;
-    if (run == n) {
-      std::fill(used.begin() + (s - n + 1), used.begin() + (s + 1), 1);
-      return s - n + 1;
-    }
-  }
-  return -1;
+  auto it = g_slots.find({dev, dtype});
+  if (it == g_slots.end())
+    it = g_slots.emplace(std::make_pair(dev, dtype), SlotRanges(const_slots(dtype))).first;
+  return it->second.reserve(n);
 }
 
 void slots_release(int dev, int dtype, int base, int n) {
   std::lock_guard<std::mutex> lk(g_slot_mu);
-  auto &used = g_slot_used[{dev, dtype}];
-  if (base < 0 || base + n > (int)used.size()) return;
-  std::fill(used.begin() + base, used.begin() + base + n, 0);
+  auto it = g_slots.find({dev, dtype});
+  if (it != g_slots.end()) it->second.release(base, n);
 }
 }  // namespace
 
